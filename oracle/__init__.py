@@ -1,0 +1,167 @@
+"""CPU oracle for the learned indexed nested loop join.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the package smoke check
+and by the benchmark's CPU-baseline leg, never by the library itself.  It
+shares no code with the CUDA implementation and does not import it.
+
+The arithmetic lives in `ljoin_oracle.c` (plain C, built with gcc); this
+module compiles it on first use and wraps it for numpy arrays.  It also
+carries `brute_force_join`, the nested-loop definition of the join in pure
+Python, used only on tiny inputs to pin the C sort-merge.
+
+Functions and the passages they follow (Sabek and Kraska, "The Case for
+Learned In-Memory Joins"):
+  join_ranges / join_pairs   Section 2.A (indexed nested loop join) and
+                             Section 6.B (duplicates return all matches)
+  rmi_fit / rmi_lookup       Section 2.D (two-level RMI with per-leaf
+                             min/max error bounds and a bounded search)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ljoin_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libljoin_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            U64 = ctypes.c_uint64
+            lib.lj_oracle_is_sorted.argtypes = [P, U64]
+            lib.lj_oracle_is_sorted.restype = ctypes.c_int
+            lib.lj_oracle_join_ranges.argtypes = [P, U64, P, U64, P, P]
+            lib.lj_oracle_join_ranges.restype = ctypes.c_int64
+            lib.lj_oracle_join_pairs.argtypes = [P, U64, P, U64, P, U64]
+            lib.lj_oracle_join_pairs.restype = ctypes.c_int64
+            lib.lj_oracle_rmi_fit.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int,
+                                              P, P, P, P, P, P]
+            lib.lj_oracle_rmi_fit.restype = ctypes.c_int
+            lib.lj_oracle_rmi_lookup.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int,
+                                                 P, P, P, P, U64, P, P, P, P]
+            lib.lj_oracle_rmi_lookup.restype = ctypes.c_uint32
+            _lib = lib
+    return _lib
+
+
+def _u64(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+class OracleError(ValueError):
+    pass
+
+
+def is_sorted(R) -> bool:
+    R = _u64(R)
+    return bool(_load().lj_oracle_is_sorted(_ptr(R), R.size))
+
+
+def join_ranges(R, S) -> tuple[np.ndarray, np.ndarray, int]:
+    """Per-probe match ranges [lo_j, hi_j) into sorted R, and |J|."""
+    R, S = _u64(R), _u64(S)
+    lo = np.zeros(S.size, dtype=np.uint64)
+    hi = np.zeros(S.size, dtype=np.uint64)
+    total = _load().lj_oracle_join_ranges(_ptr(R), R.size, _ptr(S), S.size,
+                                          _ptr(lo), _ptr(hi))
+    if total == -1:
+        raise OracleError("R is not sorted non-decreasing")
+    if total < 0:
+        raise MemoryError("oracle ran out of memory")
+    return lo, hi, int(total)
+
+
+def join_pairs(R, S, cap: int | None = None) -> np.ndarray:
+    """All (r_idx, s_idx) pairs, s ascending then r ascending, as (k, 2) uint32."""
+    R, S = _u64(R), _u64(S)
+    lib = _load()
+    if cap is None:
+        _, _, cap = join_ranges(R, S)
+    out = np.zeros((max(cap, 1), 2), dtype=np.uint32)
+    total = lib.lj_oracle_join_pairs(_ptr(R), R.size, _ptr(S), S.size, _ptr(out), cap)
+    if total == -1:
+        raise OracleError("R is not sorted non-decreasing")
+    if total < 0:
+        raise MemoryError("oracle ran out of memory")
+    return out[: min(total, cap)]
+
+
+def brute_force_join(R, S) -> list[tuple[int, int]]:
+    """Nested loops over every (i, j): the definition of J(R, S). Tiny inputs."""
+    R = [int(v) for v in R]
+    S = [int(v) for v in S]
+    return [(i, j) for j in range(len(S)) for i in range(len(R)) if R[i] == S[j]]
+
+
+@dataclass
+class RMI:
+    """A fitted two-level linear RMI (oracle side)."""
+    L: int
+    fp64: bool
+    root_fit: np.ndarray   # (2,) float64: least-squares (a0, b0)
+    root_dep: np.ndarray   # (2,) deployed (a0, b0)
+    leaf_lo: np.ndarray    # (L+1,) uint64
+    leaf_fit: np.ndarray   # (L, 2) float64
+    leaf_dep: np.ndarray   # (L, 2) deployed
+    err: np.ndarray        # (L, 2) int64: (e_lo, e_hi)
+
+
+def rmi_fit(R, L: int, fp64: bool = False) -> RMI:
+    R = _u64(R)
+    root_fit = np.zeros(2)
+    root_dep = np.zeros(2)
+    leaf_lo = np.zeros(L + 1, dtype=np.uint64)
+    leaf_fit = np.zeros((L, 2))
+    leaf_dep = np.zeros((L, 2))
+    err = np.zeros((L, 2), dtype=np.int64)
+    rc = _load().lj_oracle_rmi_fit(_ptr(R), R.size, L, int(fp64), _ptr(root_fit),
+                                   _ptr(root_dep), _ptr(leaf_lo), _ptr(leaf_fit),
+                                   _ptr(leaf_dep), _ptr(err))
+    if rc == -1:
+        raise OracleError("R is not sorted or L == 0")
+    if rc < 0:
+        raise MemoryError("oracle ran out of memory")
+    return RMI(L, fp64, root_fit, root_dep, leaf_lo, leaf_fit, leaf_dep, err)
+
+
+def rmi_lookup(R, rmi: RMI, x: int) -> dict:
+    """Learned lookup of one key: leaf, window [w_lo, w_hi) and [lb, ub)."""
+    R = _u64(R)
+    out = [ctypes.c_uint64() for _ in range(4)]
+    leaf = _load().lj_oracle_rmi_lookup(
+        _ptr(R), R.size, rmi.L, int(rmi.fp64), _ptr(rmi.root_dep), _ptr(rmi.leaf_lo),
+        _ptr(rmi.leaf_dep), _ptr(rmi.err), int(x), *[ctypes.byref(o) for o in out])
+    lb, ub, wl, wh = (o.value for o in out)
+    return {"leaf": int(leaf), "lb": lb, "ub": ub, "w_lo": wl, "w_hi": wh}

@@ -1,0 +1,322 @@
+/*
+ * CPU oracle for the learned indexed nested loop join (RMI-INLJ).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path links,
+ * loads or calls this file; only the tests, the package's smoke check and
+ * the benchmark's CPU baseline do.  It shares no code, header, table or
+ * constant with the CUDA implementation.
+ *
+ * Plain, slow and written to be checked by eye against the paper
+ * ("The Case for Learned In-Memory Joins", Sabek and Kraska):
+ *
+ *  1. lj_oracle_join_ranges / lj_oracle_join_pairs: the join result itself.
+ *     Section 2.A defines the indexed nested loop join: for every tuple s of
+ *     S, fetch the tuples of R with the same join key.  Section 6.B (the
+ *     duplicates experiment) returns every match, so the result is the set
+ *       J(R, S) = { (i, j) : R[i] == S[j] }.
+ *     Computed by a sort-merge equi-join (sort S by (key, j), merge with the
+ *     sorted R).  Because R is sorted, the matches of one probe j form one
+ *     contiguous range [lo_j, hi_j) of R's positions.
+ *
+ *  2. lj_oracle_rmi_fit / lj_oracle_rmi_lookup: the two-level linear
+ *     Recursive Model Index of Section 2.D ("Recursive Model Index"): a root
+ *     linear model picks a leaf model, the leaf's linear model predicts a
+ *     position, each leaf keeps the minimum and maximum error of its keys and
+ *     a lookup binary-searches between those bounds.  The paper gives no
+ *     formulas; the readings taken here are:
+ *       root:  leaf(x) = clamp(floor(a0 * X + b0), 0, L-1), X = x rounded to
+ *              the model's precision, (a0, b0) the least-squares line of
+ *              i * L / n on R[i] (fit in double precision);
+ *       leaf l owns the contiguous positions [lo_l, hi_l) of the keys the
+ *              root sends to it; base key k_l = R[lo_l];
+ *       leaf:  pred(x) = lo_l + floor(a_l * D + b_l), D = x - k_l as a signed
+ *              quantity rounded to the model's precision, (a_l, b_l) the
+ *              least-squares line of (i - lo_l) on (R[i] - k_l) over the
+ *              leaf's keys (fit in double precision, slope kept >= 0);
+ *       a*X+b is one fused multiply-add in the model's precision (fmaf for
+ *              the single-precision model, fma for the double one);
+ *       errors: err_i = i - pred(R[i]); e_lo = min, e_hi = max over the leaf;
+ *       window: [clamp(pred+e_lo), clamp(pred+e_hi+1)] within [lo_l, hi_l].
+ *
+ * Compile with -ffp-contract=off so that no a*b+c outside the explicit
+ * fma/fmaf calls is fused (the results must not depend on the host CPU).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- join -- */
+
+typedef struct {
+  uint64_t key;
+  uint64_t j;
+} probe_t;
+
+static int cmp_probe(const void* a, const void* b) {
+  const probe_t* x = (const probe_t*)a;
+  const probe_t* y = (const probe_t*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->j != y->j) return x->j < y->j ? -1 : 1;
+  return 0;
+}
+
+/* 1 if R is sorted non-decreasing, else 0. */
+int lj_oracle_is_sorted(const uint64_t* R, uint64_t n) {
+  for (uint64_t i = 1; i < n; ++i)
+    if (R[i - 1] > R[i]) return 0;
+  return 1;
+}
+
+/*
+ * For every probe j, the range [lo[j], hi[j]) of positions i with
+ * R[i] == S[j] (lo[j] == hi[j] when S[j] has no match; the value is then
+ * the number of keys of R below S[j]).  Returns |J| = sum (hi - lo), -1 if R
+ * is not sorted, -2 if memory runs out.
+ */
+int64_t lj_oracle_join_ranges(const uint64_t* R, uint64_t n, const uint64_t* S,
+                              uint64_t m, uint64_t* lo, uint64_t* hi) {
+  if (!lj_oracle_is_sorted(R, n)) return -1;
+  if (m == 0) return 0;
+  probe_t* P = (probe_t*)malloc(sizeof(probe_t) * m);
+  if (!P) return -2;
+  for (uint64_t j = 0; j < m; ++j) {
+    P[j].key = S[j];
+    P[j].j = j;
+  }
+  qsort(P, m, sizeof(probe_t), cmp_probe);
+
+  int64_t total = 0;
+  uint64_t i = 0; /* first position of R whose key is >= the current probe key */
+  uint64_t k = 0;
+  while (k < m) {
+    uint64_t key = P[k].key;
+    while (i < n && R[i] < key) ++i;
+    uint64_t a = i, b = i;
+    while (b < n && R[b] == key) ++b;
+    /* every probe carrying this key gets the whole run [a, b) */
+    while (k < m && P[k].key == key) {
+      lo[P[k].j] = a;
+      hi[P[k].j] = b;
+      total += (int64_t)(b - a);
+      ++k;
+    }
+  }
+  free(P);
+  return total;
+}
+
+/*
+ * The join as (r_idx, s_idx) pairs in canonical order: s_idx ascending,
+ * r_idx ascending within one probe.  pairs holds 2*cap uint32 values
+ * (r, s interleaved).  Returns |J| (which may exceed cap: only the first cap
+ * pairs are written), -1 if R is not sorted, -2 if memory runs out.
+ */
+int64_t lj_oracle_join_pairs(const uint64_t* R, uint64_t n, const uint64_t* S,
+                             uint64_t m, uint32_t* pairs, uint64_t cap) {
+  if (m == 0) return lj_oracle_is_sorted(R, n) ? 0 : -1;
+  uint64_t* lo = (uint64_t*)malloc(sizeof(uint64_t) * m);
+  uint64_t* hi = (uint64_t*)malloc(sizeof(uint64_t) * m);
+  if (!lo || !hi) {
+    free(lo);
+    free(hi);
+    return -2;
+  }
+  int64_t total = lj_oracle_join_ranges(R, n, S, m, lo, hi);
+  if (total >= 0) {
+    uint64_t q = 0;
+    for (uint64_t j = 0; j < m && q < cap; ++j)
+      for (uint64_t r = lo[j]; r < hi[j] && q < cap; ++r, ++q) {
+        pairs[2 * q] = (uint32_t)r;
+        pairs[2 * q + 1] = (uint32_t)j;
+      }
+  }
+  free(lo);
+  free(hi);
+  return total;
+}
+
+/* ----------------------------------------------------------------- RMI -- */
+
+/* Least-squares line y = a*x + b by centred two-pass sums (double). */
+static void lsq_fit(const double* x, const double* y, uint64_t k, double* a,
+                    double* b) {
+  if (k == 0) {
+    *a = 0.0;
+    *b = 0.0;
+    return;
+  }
+  double sx = 0.0, sy = 0.0;
+  for (uint64_t t = 0; t < k; ++t) {
+    sx += x[t];
+    sy += y[t];
+  }
+  double mx = sx / (double)k, my = sy / (double)k;
+  double sxy = 0.0, sxx = 0.0;
+  for (uint64_t t = 0; t < k; ++t) {
+    double dx = x[t] - mx, dy = y[t] - my;
+    sxy += dx * dy;
+    sxx += dx * dx;
+  }
+  double slope = sxx > 0.0 ? sxy / sxx : 0.0;
+  if (!(slope > 0.0)) slope = 0.0; /* sorted keys: the slope is never negative */
+  *a = slope;
+  *b = my - slope * mx;
+}
+
+/* Deployed parameter: rounded to float for the single-precision model. */
+static double deploy(double v, int fp64) { return fp64 ? v : (double)(float)v; }
+
+/* floor of the model output clamped to [-2^40, 2^40], as an integer. */
+static int64_t clamp_floor(double v) {
+  v = floor(v);
+  if (v < -1099511627776.0) v = -1099511627776.0;
+  if (v > 1099511627776.0) v = 1099511627776.0;
+  return (int64_t)v;
+}
+
+/* Root model: which leaf serves key x. */
+static uint32_t root_leaf(uint64_t x, double a0, double b0, uint32_t L, int fp64) {
+  double v;
+  if (fp64)
+    v = fma(a0, (double)x, b0);
+  else
+    v = (double)fmaf((float)a0, (float)x, (float)b0);
+  v = floor(v);
+  if (!(v >= 0.0)) return 0; /* also catches NaN */
+  if (v >= (double)(L - 1)) return L - 1;
+  return (uint32_t)v;
+}
+
+/* Leaf model: predicted offset of key x from the leaf's first position. */
+static int64_t leaf_pred(uint64_t x, uint64_t base, double a, double b, int fp64) {
+  double v;
+  if (fp64) {
+    double d = x >= base ? (double)(x - base) : -(double)(base - x);
+    v = fma(a, d, b);
+  } else {
+    float d = x >= base ? (float)(x - base) : -(float)(base - x);
+    v = (double)fmaf((float)a, d, (float)b);
+  }
+  return clamp_floor(v);
+}
+
+/*
+ * Fit the two-level RMI over sorted R (n keys) with L leaves.
+ *   root_fit[2]  = (a0, b0) least-squares fit (double)
+ *   root_dep[2]  = deployed (a0, b0) (float-rounded for fp64 == 0)
+ *   leaf_lo[L+1] = first position of each leaf; leaf_lo[L] = n
+ *   leaf_fit[2L] = per-leaf (a, b) least-squares fit (double)
+ *   leaf_dep[2L] = deployed per-leaf (a, b)
+ *   err[2L]      = per-leaf (e_lo, e_hi); (0, 0) for an empty leaf
+ * Returns 0, -1 if R is not sorted or L == 0, -2 if memory runs out.
+ */
+int lj_oracle_rmi_fit(const uint64_t* R, uint64_t n, uint32_t L, int fp64,
+                      double* root_fit, double* root_dep, uint64_t* leaf_lo,
+                      double* leaf_fit, double* leaf_dep, int64_t* err) {
+  if (L == 0 || !lj_oracle_is_sorted(R, n)) return -1;
+  double* x = (double*)malloc(sizeof(double) * (n ? n : 1));
+  double* y = (double*)malloc(sizeof(double) * (n ? n : 1));
+  if (!x || !y) {
+    free(x);
+    free(y);
+    return -2;
+  }
+  /* root: least squares of the scaled position i*L/n on the key */
+  for (uint64_t i = 0; i < n; ++i) {
+    x[i] = (double)R[i];
+    y[i] = (double)i * (double)L / (double)n;
+  }
+  lsq_fit(x, y, n, &root_fit[0], &root_fit[1]);
+  root_dep[0] = deploy(root_fit[0], fp64);
+  root_dep[1] = deploy(root_fit[1], fp64);
+
+  /* leaf of every key; the root is monotone, so each leaf is one range */
+  for (uint32_t l = 0; l <= L; ++l) leaf_lo[l] = n;
+  for (uint64_t i = n; i-- > 0;) {
+    uint32_t l = root_leaf(R[i], root_dep[0], root_dep[1], L, fp64);
+    leaf_lo[l] = i;
+  }
+  for (uint32_t l = L; l-- > 0;)
+    if (leaf_lo[l] > leaf_lo[l + 1]) leaf_lo[l] = leaf_lo[l + 1];
+
+  /* leaves: least squares of (i - lo) on (R[i] - base), then the errors */
+  for (uint32_t l = 0; l < L; ++l) {
+    uint64_t lo = leaf_lo[l], hi = leaf_lo[l + 1];
+    double a = 0.0, b = 0.0;
+    if (hi > lo) {
+      uint64_t base = R[lo];
+      for (uint64_t i = lo; i < hi; ++i) {
+        x[i - lo] = (double)(R[i] - base);
+        y[i - lo] = (double)(i - lo);
+      }
+      lsq_fit(x, y, hi - lo, &a, &b);
+    }
+    leaf_fit[2 * l] = a;
+    leaf_fit[2 * l + 1] = b;
+    leaf_dep[2 * l] = deploy(a, fp64);
+    leaf_dep[2 * l + 1] = deploy(b, fp64);
+    int64_t elo = 0, ehi = 0;
+    for (uint64_t i = lo; i < hi; ++i) {
+      int64_t e = (int64_t)(i - lo) -
+                  leaf_pred(R[i], R[lo], leaf_dep[2 * l], leaf_dep[2 * l + 1], fp64);
+      if (i == lo || e < elo) elo = e;
+      if (i == lo || e > ehi) ehi = e;
+    }
+    err[2 * l] = elo;
+    err[2 * l + 1] = ehi;
+  }
+  free(x);
+  free(y);
+  return 0;
+}
+
+/*
+ * Learned lookup of key x through a fitted RMI (Section 2.D): root picks the
+ * leaf, the leaf predicts a position, and a binary search between the error
+ * bounds finds the first position whose key is >= x (lower bound) and the
+ * first whose key is > x (upper bound).  Writes [lb, ub) and the searched
+ * window [w_lo, w_hi); returns the leaf.
+ */
+uint32_t lj_oracle_rmi_lookup(const uint64_t* R, uint64_t n, uint32_t L, int fp64,
+                              const double* root_dep, const uint64_t* leaf_lo,
+                              const double* leaf_dep, const int64_t* err,
+                              uint64_t x, uint64_t* lb, uint64_t* ub,
+                              uint64_t* w_lo, uint64_t* w_hi) {
+  uint32_t l = root_leaf(x, root_dep[0], root_dep[1], L, fp64);
+  int64_t lo = (int64_t)leaf_lo[l], hi = (int64_t)leaf_lo[l + 1];
+  int64_t wl = lo, wh = lo;
+  if (hi > lo) {
+    int64_t p = lo + leaf_pred(x, R[lo], leaf_dep[2 * l], leaf_dep[2 * l + 1], fp64);
+    wl = p + err[2 * l];
+    wh = p + err[2 * l + 1] + 1;
+    if (wl < lo) wl = lo;
+    if (wl > hi) wl = hi;
+    if (wh < lo) wh = lo;
+    if (wh > hi) wh = hi;
+  }
+  /* binary search for the lower bound inside [wl, wh) */
+  int64_t a = wl, b = wh;
+  while (a < b) {
+    int64_t mid = a + (b - a) / 2;
+    if (R[mid] < x)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  *lb = (uint64_t)a;
+  /* and for the upper bound */
+  b = wh;
+  while (a < b) {
+    int64_t mid = a + (b - a) / 2;
+    if (R[mid] <= x)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  *ub = (uint64_t)a;
+  *w_lo = (uint64_t)wl;
+  *w_hi = (uint64_t)wh;
+  (void)n;
+  return l;
+}
