@@ -1,0 +1,304 @@
+#!/usr/bin/env python3
+"""Benchmark of the learned indexed nested loop join (RMI-INLJ) on GB300.
+
+One step = one pass of the probe path over the whole outer relation S with
+the learned index of R resident on the device (the index is built before
+the timed region, as the paper measures joins: Section 3.A / 6.A); the
+build is timed separately and reported as build_ms.
+
+Default workload (lognormal_100m): R = 100M unique keys
+round(1e9 * LogNormal(0, 2)), sorted; S = 400M keys, half Zipf(0.99) hits
+over R's ranks, half true misses uniform in [min R, max R]; two-level
+linear RMI with 2^20 leaves, single-precision model evaluation.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+(sort-merge join) on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+WORKLOADS = {
+    "lognormal_100m": dict(fn=datagen.lognormal_100m, kw={}),
+    "uniform_1m": dict(fn=datagen.uniform_1m, kw={}),
+    "dup_seqh_50m": dict(fn=datagen.dup_seqh_50m, kw={}),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu, self.proc, self.path = gpu_index, None, None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("LJ_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def run_reference(args, rank, world):
+    """CPU oracle (sort-merge) on bounded samples of the same workload."""
+    import oracle
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    wl = w["fn"](seed=args.seed, **w["kw"])
+    m_s = min(wl.S.size, args.ref_sample)
+    oracle.build()
+    times = []
+    for step in range(args.warmup + args.steps):
+        off = (step * m_s) % max(1, wl.S.size - m_s + 1)
+        S = wl.S[off:off + m_s]
+        t0 = time.perf_counter()
+        _, _, total = oracle.join_ranges(wl.R, S)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = m_s * args.steps / t
+    line = {
+        "impl": "reference", "metric": "probe_keys_per_s", "value": value, "unit": "keys/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": _config(args, wl),
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{m_s} probes of S per step against the full R"},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, wl):
+    return {"workload": wl.name, "n": int(wl.R.size), "m": int(wl.S.size),
+            "leaves": int(wl.leaves), "precision": wl.precision, "seed": args.seed,
+            "l2": "inputs larger than L2 (S = %.1f GB, R = %.1f GB)" % (
+                wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
+
+
+def cpu_baseline(wl, sample: int) -> dict:
+    import oracle
+    oracle.build()
+    m_s = min(sample, wl.S.size)
+    S = wl.S[:m_s]
+    t0 = time.perf_counter()
+    oracle.join_ranges(wl.R, S)
+    dt = time.perf_counter() - t0
+    return {"value": m_s / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m_s} probes of S against the full R ({dt:.1f} s, single thread)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lognormal_100m", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 25)
+    ap.add_argument("--ref-sample", type=int, default=1 << 23)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import torch
+
+    import paper_2111_08824_gb300 as lj
+    torch.cuda.set_device(local)
+    w = WORKLOADS[args.workload]
+    # weak scaling: every rank probes its own S (seeded by rank) against the
+    # replicated R; no collective on the data path.
+    wl = w["fn"](seed=args.seed + 1000 * rank, **w["kw"]) if rank else w["fn"](seed=args.seed, **w["kw"])
+    n, m, L = wl.R.size, wl.S.size, wl.leaves
+
+    Rd = torch.from_numpy(wl.R.view(np.int64)).cuda()
+    Sd = torch.from_numpy(wl.S.view(np.int64)).cuda()
+    idx = lj.rmi_build(Rd, L, wl.precision)
+    st = idx.stats()
+    unique = bool(st["unique"])
+    stream = torch.cuda.current_stream()
+
+    if unique:
+        pairs = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+        written = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+        def step():
+            lj.join_emit(idx, Sd, pairs, written=written, want_total=False)
+        launches_per_step = 1
+    else:
+        offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+        total0 = lj.join_count(idx, Sd, offsets=offsets)
+        pairs = torch.empty((max(total0, 1), 2), dtype=torch.int32, device="cuda")
+
+        def step():
+            lj.join_count(idx, Sd, offsets=offsets, want_total=False)
+            lj.join_emit(idx, Sd, pairs, offsets=offsets, want_total=False)
+        launches_per_step = 2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    total = lj.join_emit(idx, Sd, pairs) if unique else lj.join_count(idx, Sd)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    per_launch = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * m / (ms_per_step / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    S_host = torch.from_numpy(wl.S.view(np.int64)).pin_memory()
+    P_host = torch.empty((max(total, 1), 2), dtype=torch.int32).pin_memory()
+    S_np = S_host.numpy().view(np.uint64)
+    P_np = P_host.numpy().view(np.uint32)
+    lj.join_host(idx, S_np, P_np)          # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        got = lj.join_host(idx, S_np, P_np)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    assert got == total
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = _peaks()
+    alg_bytes = 8 * m + 8 * n + 8 * total + 32 * L
+    launch_ms = statistics.mean(per_launch) / launches_per_step if unique else statistics.mean(per_launch)
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    line = {
+        "metric": "probe_keys_per_s", "value": value, "unit": "keys/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 keys, f32 model" if wl.precision == "fp32" else "u64 keys, f64 model",
+        "data": "synthetic", "config": _config(args, wl),
+        "pairs": int(total), "pairs_per_s": world * total / (ms_per_step / 1e3),
+        "paper_metric_tuples_per_s": world * (n + m) / (ms_per_step / 1e3),
+        "build_ms": st["build_ms"], "mean_window": st["mean_window"],
+        "max_window": st["max_window"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "kernel": "probe_tile_kernel" if unique else "probe_tile_kernel+emit_kernel",
+                     "alg_bytes_per_launch": alg_bytes},
+        "e2e": {"value": world * m / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * m,
+                "d2h_bytes_per_step": 8 * total},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

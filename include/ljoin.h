@@ -1,0 +1,183 @@
+/*
+ * ljoin.h -- C ABI of the GB300 learned indexed nested loop join (RMI-INLJ).
+ *
+ * Method: Sabek and Kraska, "The Case for Learned In-Memory Joins".
+ *   Section 2.A  indexed nested loop join: R carries an index on the join
+ *                key; every tuple s of S fetches the R tuples with equal key.
+ *   Section 2.D  two-level linear Recursive Model Index (RMI): a root linear
+ *                model picks a leaf model, the leaf's linear model predicts
+ *                a position, per-leaf min/max error bounds delimit a binary
+ *                search.
+ *   Section 3    RMI-INLJ: index R with an RMI, probe it with every s.
+ *   Section 6.A  the index is built before the join; its build time is not
+ *                part of the join (Section 3.A).
+ *   Section 6.B  duplicate keys: a range scan between the error bounds
+ *                returns every match (1-to-m and n-to-m joins).
+ *
+ * Result of a join: J(R, S) = { (i, j) : R[i] == S[j] } as (r_idx, s_idx)
+ * pairs, r_idx a position in the sorted R as passed, s_idx a position in S.
+ * The library writes them s-major, r-ascending (deterministic).
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (LJ_OK) or a negative LJ_E_* code; lj_last_error() then gives
+ *     a thread-local message.  No entry point aborts or exits the process.
+ *   - Pointers named *_dev are CUDA device pointers (or managed memory) on
+ *     the current device; *_host are host pointers.  Keys are uint64.
+ *   - R is BORROWED by the index: device memory, sorted non-decreasing, left
+ *     unchanged and alive until rmi_free.  S and every output buffer belong
+ *     to the caller.
+ *   - n = |R| and m = |S| are below 2^32 (indices are uint32); pair totals
+ *     and offsets are uint64.
+ *   - Work is ordered on `stream` (NULL = the legacy default stream) and is
+ *     asynchronous, except where the call fills a *_host result: such a call
+ *     synchronises `stream` before returning.
+ *   - Empty R or empty S are valid and give zero pairs.
+ *   - Device code never traps: a bounded wait that runs out or a capacity
+ *     overflow sets an error word that the next synchronising call reports.
+ */
+#ifndef LJOIN_H
+#define LJOIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                     /* cudaStream_t == struct CUstream_st* */
+typedef struct CUstream_st* lj_stream_t;
+
+enum {
+  LJ_OK = 0,
+  LJ_E_INVAL = -1,      /* bad argument (NULL pointer, size out of range) */
+  LJ_E_NOMEM = -2,      /* device or host allocation failed */
+  LJ_E_CUDA = -3,       /* a CUDA runtime call failed (message has details) */
+  LJ_E_UNSORTED = -4,   /* R is not sorted non-decreasing */
+  LJ_E_CAPACITY = -5,   /* output buffer smaller than the join result */
+  LJ_E_TIMEOUT = -6,    /* a bounded device wait or a host wait ran out */
+  LJ_E_BUDGET = -7,     /* request larger than the server's memory budget */
+  LJ_E_NOTUNIQUE = -8,  /* single-pass path asked for on an R with duplicates */
+  LJ_E_STATE = -9       /* object used in a state that does not allow it */
+};
+
+enum { LJ_FP32 = 0, LJ_FP64 = 1 };     /* precision of the model evaluation */
+
+typedef struct lj_index lj_index;       /* opaque, owned by the library */
+
+typedef struct {
+  uint32_t r_idx;
+  uint32_t s_idx;
+} lj_pair;                              /* 8 bytes, array of structs */
+
+typedef struct {
+  uint64_t n;               /* |R| */
+  uint32_t leaves;          /* L */
+  int32_t precision;        /* LJ_FP32 | LJ_FP64 */
+  int32_t unique;           /* 1 if no key of R repeats */
+  uint32_t nonempty_leaves;
+  uint32_t max_leaf_size;
+  uint32_t max_window;      /* max over leaves of min(e_hi - e_lo + 1, size) */
+  double mean_window;       /* key-weighted mean of that width */
+  double root_a, root_b;    /* deployed root parameters (widened) */
+  double build_ms;          /* device time of the build, CUDA events */
+} lj_index_stats;
+
+/* ------------------------------------------------------------- index ---- */
+
+/*
+ * rmi_build -- fit a two-level linear RMI over the sorted R (Section 2.D).
+ *   R_dev      n sorted keys (device, borrowed for the index's lifetime)
+ *   leaves     L, number of leaf models, 1 .. 2^24
+ *   precision  LJ_FP32: models evaluated in single precision (fused
+ *              multiply-add), fits in double; LJ_FP64: double throughout.
+ *              Error bounds are always measured with the deployed arithmetic,
+ *              so the join is exact at either precision.
+ *   out        receives the index; free with rmi_free.
+ * Root: leaf(x) = clamp(floor(a0*X + b0), 0, L-1), (a0, b0) the least-squares
+ * line of i*L/n on R[i].  Leaf l owns positions [lo_l, hi_l); with base key
+ * k_l = R[lo_l]: pred(x) = lo_l + floor(a_l*(x - k_l) + b_l), (a_l, b_l) the
+ * least-squares line of (i - lo_l) on (R[i] - k_l), slope >= 0; e_lo/e_hi the
+ * min/max of i - pred(R[i]) over the leaf.
+ * Synchronises `stream`.  Errors: LJ_E_INVAL, LJ_E_UNSORTED, LJ_E_NOMEM,
+ * LJ_E_CUDA.
+ */
+int rmi_build(const uint64_t* R_dev, uint64_t n, uint32_t leaves, int precision,
+              lj_stream_t stream, lj_index** out);
+
+/* Release an index (its device memory; R itself is not touched). NULL is ok. */
+void rmi_free(lj_index* index);
+
+/* Summary statistics of a built index.  Host-only, no device work. */
+int rmi_stats(const lj_index* index, lj_index_stats* out);
+
+/*
+ * rmi_export -- copy the index to host memory for inspection.
+ *   root_host   2 doubles: deployed (a0, b0), widened to double
+ *   leaf_lo     L+1 uint64: first position of each leaf, leaf_lo[L] = n
+ *   leaf_ab     2L doubles: deployed (a_l, b_l) per leaf, widened
+ *   leaf_err    2L int64: (e_lo, e_hi) per leaf
+ * Any pointer may be NULL.  Synchronises.  Section 2.D, as rmi_build.
+ */
+int rmi_export(const lj_index* index, double* root_host, uint64_t* leaf_lo,
+               double* leaf_ab, int64_t* leaf_err);
+
+/* ------------------------------------------------------------- join ----- */
+
+/*
+ * join_count -- number of matches of every probe, and their offsets
+ * (Section 2.A probe of every s; Section 6.B all duplicates).
+ *   S_dev        m probe keys (device)
+ *   counts_dev   optional, m uint32: c_j = |{ i : R[i] == S[j] }|
+ *   offsets_dev  optional, m+1 uint64: exclusive prefix sum of c,
+ *                offsets[m] = |J|
+ *   total_host   optional: |J|; if given the call synchronises.
+ * One fused kernel: learned lookup (root, leaf, bounded lower/upper-bound
+ * search) + single-pass decoupled look-back scan.
+ * Errors: LJ_E_INVAL, LJ_E_NOMEM, LJ_E_CUDA, LJ_E_TIMEOUT.
+ */
+int join_count(const lj_index* index, const uint64_t* S_dev, uint64_t m,
+               uint32_t* counts_dev, uint64_t* offsets_dev, uint64_t* total_host,
+               lj_stream_t stream);
+
+/*
+ * join_emit -- write the join pairs (Section 2.A; Section 6.B).
+ *   offsets_dev   m+1 offsets from join_count (two-pass path), or NULL for the
+ *                 single-pass path (lookup + in-kernel scan + emit in one
+ *                 kernel), which needs an index whose R has no duplicate key
+ *                 (else LJ_E_NOTUNIQUE).
+ *   pairs_dev     capacity pairs; pairs beyond capacity are not written.
+ *   written_dev   optional device uint64: |J| (stream-ordered, no sync)
+ *   written_host  optional host uint64: |J|; if given the call synchronises
+ *                 and returns LJ_E_CAPACITY when |J| > capacity.
+ * Errors: LJ_E_INVAL, LJ_E_NOTUNIQUE, LJ_E_NOMEM, LJ_E_CUDA, LJ_E_CAPACITY,
+ * LJ_E_TIMEOUT.
+ */
+int join_emit(const lj_index* index, const uint64_t* S_dev, uint64_t m,
+              const uint64_t* offsets_dev, lj_pair* pairs_dev, uint64_t capacity,
+              uint64_t* written_dev, uint64_t* written_host, lj_stream_t stream);
+
+/*
+ * join_host -- the whole join from host buffers: copies S (host, ideally
+ * pinned) to the device in chunks, runs the lookup on each chunk while the
+ * next one is in flight, and copies the pairs back into pairs_host
+ * (capacity pairs).  s_idx values are positions in the whole S.  Uses the
+ * single-pass path when R is unique, else count + emit per chunk.
+ * Synchronises.  Errors: as join_emit.
+ */
+int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
+              lj_pair* pairs_host, uint64_t capacity, uint64_t* written_host,
+              lj_stream_t stream);
+
+/* ------------------------------------------------------ diagnostics ----- */
+
+/* Thread-local message describing the last error of this thread. */
+const char* lj_last_error(void);
+
+/* Library version string. */
+const char* lj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LJOIN_H */

@@ -1,0 +1,17 @@
+"""GB300-native learned indexed nested loop join (RMI-INLJ).
+
+Sabek and Kraska, "The Case for Learned In-Memory Joins": a two-level linear
+Recursive Model Index is fitted over the sorted inner relation R, then every
+outer key of S predicts a position, searches the model's error window and
+emits all matching (r_idx, s_idx) pairs.  The computation runs in the CUDA
+library `libljoin` (hand-written sm_103a kernels, C ABI in include/ljoin.h);
+this package is its thin Python binding.  The library is loaded on first
+use; there is no CPU fallback.
+"""
+from ._native import (LJ_FP32, LJ_FP64, Index, LJoinError, join_count, join_emit, join_host,
+                      library_path, lj_last_error, lj_version, load, rmi_build, rmi_export,
+                      rmi_free, rmi_stats)
+
+__all__ = ["LJ_FP32", "LJ_FP64", "Index", "LJoinError", "join_count", "join_emit", "join_host",
+           "library_path", "lj_last_error", "lj_version", "load", "rmi_build", "rmi_export",
+           "rmi_free", "rmi_stats"]

@@ -1,0 +1,202 @@
+"""ctypes binding of libljoin (include/ljoin.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  There is no CPU fallback: if
+the library cannot be loaded (not built, or built for another machine) the
+first call raises.  torch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+LJ_FP32, LJ_FP64 = 0, 1
+_ERR_NAMES = {
+    -1: "LJ_E_INVAL", -2: "LJ_E_NOMEM", -3: "LJ_E_CUDA", -4: "LJ_E_UNSORTED",
+    -5: "LJ_E_CAPACITY", -6: "LJ_E_TIMEOUT", -7: "LJ_E_BUDGET", -8: "LJ_E_NOTUNIQUE",
+    -9: "LJ_E_STATE",
+}
+
+
+class LJoinError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lj_index_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("leaves", ctypes.c_uint32),
+                ("precision", ctypes.c_int32), ("unique", ctypes.c_int32),
+                ("nonempty_leaves", ctypes.c_uint32), ("max_leaf_size", ctypes.c_uint32),
+                ("max_window", ctypes.c_uint32), ("mean_window", ctypes.c_double),
+                ("root_a", ctypes.c_double), ("root_b", ctypes.c_double),
+                ("build_ms", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# every function declared in include/ljoin.h, with its ctypes signature
+_P, _U64, _U32, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+SIGNATURES = {
+    "rmi_build": ([_P, _U64, _U32, _I, _P, _P], _I),
+    "rmi_free": ([_P], None),
+    "rmi_stats": ([_P, _P], _I),
+    "rmi_export": ([_P, _P, _P, _P, _P], _I),
+    "join_count": ([_P, _P, _U64, _P, _P, _P, _P], _I),
+    "join_emit": ([_P, _P, _U64, _P, _P, _U64, _P, _P, _P], _I),
+    "join_host": ([_P, _P, _U64, _P, _U64, _P, _P], _I),
+    "lj_last_error": ([], ctypes.c_char_p),
+    "lj_version": ([], ctypes.c_char_p),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libljoin.so (building it in-tree first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libljoin is not built ({path}); run build() first")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load().lj_last_error().decode(errors="replace")
+        raise LJoinError(rc, msg)
+
+
+def _stream_ptr(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data if t.size else None
+    return t.data_ptr() if t.numel() else None
+
+
+def _require_cuda_u64(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in (torch.int64, torch.uint64) or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous 64-bit integer tensor")
+
+
+@dataclass
+class Index:
+    """A learned index over R (keeps R alive: the library borrows it)."""
+    handle: int
+    R: object
+    leaves: int
+    precision: int
+
+    def stats(self) -> dict:
+        st = lj_index_stats()
+        _check(load().rmi_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.rmi_free(h)
+
+
+def rmi_build(R, leaves: int, precision: str | int = "fp32", stream=None) -> Index:
+    """Fit the two-level linear RMI over the sorted device tensor R."""
+    _require_cuda_u64(R, "R")
+    prec = {"fp32": LJ_FP32, "fp64": LJ_FP64}.get(precision, precision)
+    out = ctypes.c_void_p()
+    _check(load().rmi_build(_ptr(R), R.numel(), leaves, prec, _stream_ptr(stream),
+                            ctypes.byref(out)))
+    return Index(out.value, R, leaves, prec)
+
+
+def rmi_free(index: Index):
+    h, index.handle = index.handle, None
+    if h:
+        load().rmi_free(h)
+
+
+def rmi_stats(index: Index) -> dict:
+    return index.stats()
+
+
+def rmi_export(index: Index) -> dict:
+    L = index.leaves
+    root = np.zeros(2)
+    lo = np.zeros(L + 1, dtype=np.uint64)
+    ab = np.zeros((L, 2))
+    err = np.zeros((L, 2), dtype=np.int64)
+    _check(load().rmi_export(index.handle, _ptr(root), _ptr(lo), _ptr(ab), _ptr(err)))
+    return {"root": root, "leaf_lo": lo, "leaf_ab": ab, "err": err}
+
+
+def join_count(index: Index, S, counts=None, offsets=None, want_total: bool = True,
+               stream=None) -> int | None:
+    """Match counts (uint32 tensor, optional) and offsets (m+1 int64 tensor,
+    optional) of every probe of S; returns |J| when want_total (synchronises)."""
+    _require_cuda_u64(S, "S")
+    total = ctypes.c_uint64()
+    _check(load().join_count(index.handle, _ptr(S), S.numel(), _ptr(counts), _ptr(offsets),
+                             ctypes.byref(total) if want_total else None,
+                             _stream_ptr(stream)))
+    return total.value if want_total else None
+
+
+def join_emit(index: Index, S, pairs, offsets=None, written=None, want_total: bool = True,
+              stream=None) -> int | None:
+    """Write the join pairs into `pairs` (int32 tensor of shape (cap, 2)).
+    offsets=None selects the single-pass path (R unique).  `written` is an
+    optional 1-element 64-bit device tensor receiving |J| without a sync."""
+    _require_cuda_u64(S, "S")
+    cap = pairs.shape[0] if pairs is not None else 0
+    total = ctypes.c_uint64()
+    _check(load().join_emit(index.handle, _ptr(S), S.numel(), _ptr(offsets), _ptr(pairs), cap,
+                            _ptr(written), ctypes.byref(total) if want_total else None,
+                            _stream_ptr(stream)))
+    return total.value if want_total else None
+
+
+def join_host(index: Index, S_host: np.ndarray, pairs_host: np.ndarray, stream=None) -> int:
+    """The whole join from host arrays (S uint64; pairs (cap, 2) uint32)."""
+    assert S_host.dtype == np.uint64 and S_host.flags.c_contiguous
+    assert pairs_host.dtype == np.uint32 and pairs_host.flags.c_contiguous
+    total = ctypes.c_uint64()
+    _check(load().join_host(index.handle, _ptr(S_host), S_host.size, _ptr(pairs_host),
+                            pairs_host.shape[0], ctypes.byref(total), _stream_ptr(stream)))
+    return total.value
+
+
+def lj_last_error() -> str:
+    return load().lj_last_error().decode(errors="replace")
+
+
+def lj_version() -> str:
+    return load().lj_version().decode()

@@ -1,0 +1,164 @@
+// Error reporting, scratch memory, and the host-only index entry points.
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace lj {
+
+static thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int fail_cuda(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? LJ_E_NOMEM : LJ_E_CUDA, "%s: %s (%s)",
+              what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+namespace {
+std::mutex g_mu;
+std::vector<cudaMemPool_t> g_pools;
+std::vector<uint32_t*> g_err_words;
+}  // namespace
+
+static cudaMemPool_t pool_for(int dev) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pools[dev] = p;
+  }
+  return g_pools[dev];
+}
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  cudaMemPool_t pool = pool_for(current_device());
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t scratch_free(void* p, cudaStream_t s) {
+  if (!p) return cudaSuccess;
+  return cudaFreeAsync(p, s);
+}
+
+uint32_t* device_error_word(int dev) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if ((int)g_err_words.size() <= dev) g_err_words.resize(dev + 1, nullptr);
+  if (!g_err_words[dev]) {
+    uint32_t* p = nullptr;
+    if (cudaMalloc(&p, 256) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, 256) != cudaSuccess) return nullptr;
+    g_err_words[dev] = p;
+  }
+  return g_err_words[dev];
+}
+
+int take_device_errors(int dev, cudaStream_t s) {
+  uint32_t* w = device_error_word(dev);
+  if (!w) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
+  uint32_t v = 0;
+  LJ_CUDA(cudaMemcpyAsync(&v, w, sizeof(v), cudaMemcpyDeviceToHost, s));
+  LJ_CUDA(cudaStreamSynchronize(s));
+  if (v) {
+    LJ_CUDA(cudaMemsetAsync(w, 0, sizeof(uint32_t), s));
+    LJ_CUDA(cudaStreamSynchronize(s));
+  }
+  if (v & kErrLookbackTimeout)
+    return fail(LJ_E_TIMEOUT, "a device-side look-back wait ran out (error word 0x%x)", v);
+  if (v & kErrCapacity) return fail(LJ_E_CAPACITY, "output capacity exceeded on the device");
+  return 0;
+}
+
+}  // namespace lj
+
+extern "C" {
+
+const char* lj_last_error(void) { return lj::g_err; }
+
+const char* lj_version(void) { return "ljoin-gb300 0.1 (sm_103a)"; }
+
+void rmi_free(lj_index* index) {
+  if (!index) return;
+  if (index->leaves) cudaFree(index->leaves);
+  delete index;
+}
+
+int rmi_stats(const lj_index* index, lj_index_stats* out) {
+  if (!index || !out) return lj::fail(LJ_E_INVAL, "rmi_stats: NULL argument");
+  *out = index->stats;
+  return LJ_OK;
+}
+
+int rmi_export(const lj_index* index, double* root_host, uint64_t* leaf_lo, double* leaf_ab,
+               int64_t* leaf_err) {
+  if (!index) return lj::fail(LJ_E_INVAL, "rmi_export: NULL index");
+  const uint32_t L = index->L;
+  if (root_host) {
+    if (index->precision == LJ_FP64) {
+      root_host[0] = index->root_f64[0];
+      root_host[1] = index->root_f64[1];
+    } else {
+      root_host[0] = index->root_f32[0];
+      root_host[1] = index->root_f32[1];
+    }
+  }
+  if (!leaf_lo && !leaf_ab && !leaf_err) return LJ_OK;
+  if (index->precision == LJ_FP64) {
+    std::vector<lj::LeafF64> h(L);
+    LJ_CUDA(cudaMemcpy(h.data(), index->leaves, sizeof(lj::LeafF64) * L, cudaMemcpyDeviceToHost));
+    for (uint32_t l = 0; l < L; ++l) {
+      if (leaf_lo) leaf_lo[l] = h[l].lo;
+      if (leaf_ab) {
+        leaf_ab[2 * l] = h[l].a;
+        leaf_ab[2 * l + 1] = h[l].b;
+      }
+      if (leaf_err) {
+        leaf_err[2 * l] = h[l].e_lo;
+        leaf_err[2 * l + 1] = h[l].e_hi;
+      }
+    }
+  } else {
+    std::vector<lj::LeafF32> h(L);
+    LJ_CUDA(cudaMemcpy(h.data(), index->leaves, sizeof(lj::LeafF32) * L, cudaMemcpyDeviceToHost));
+    for (uint32_t l = 0; l < L; ++l) {
+      if (leaf_lo) leaf_lo[l] = h[l].lo;
+      if (leaf_ab) {
+        leaf_ab[2 * l] = h[l].a;
+        leaf_ab[2 * l + 1] = h[l].b;
+      }
+      if (leaf_err) {
+        leaf_err[2 * l] = h[l].e_lo;
+        leaf_err[2 * l + 1] = h[l].e_hi;
+      }
+    }
+  }
+  if (leaf_lo) leaf_lo[L] = index->n;
+  return LJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// join_host: the whole join from host buffers, pipelined in chunks.
+//
+// Unique R (single-pass path): two device buffers for S chunks and two for
+// pair chunks.  While chunk c is probed on the caller's stream, chunk c+1 is
+// copied in on a copy stream and chunk c-1's pairs are copied out on another,
+// so host<->device transfers overlap the lookups.  The host waits only for
+// each chunk's pair count (8 bytes) before issuing its copy-out.
+// R with duplicates: per chunk, count (offsets) -> emit -> copy out.
+#include <algorithm>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace lj {
+int probe_count_impl(const lj_index* idx, const uint64_t* S, uint64_t m, uint32_t* counts,
+                     uint64_t* offsets, uint64_t* total_dev, uint64_t* total_host,
+                     cudaStream_t s);
+int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const uint64_t* offsets,
+                    lj_pair* pairs, uint64_t cap, uint64_t* total_dev, uint64_t* total_host,
+                    uint32_t s_base, cudaStream_t s);
+}  // namespace lj
+
+namespace {
+
+struct Streams {
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t ev[8] = {};
+  ~Streams() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (in) cudaStreamDestroy(in);
+    if (out) cudaStreamDestroy(out);
+  }
+};
+
+constexpr uint64_t kHostChunk = 1ull << 25;   // 32M keys = 256 MB per chunk
+
+}  // namespace
+
+extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m,
+                         lj_pair* pairs_host, uint64_t capacity, uint64_t* written_host,
+                         lj_stream_t stream) {
+  using namespace lj;
+  if (!idx) return fail(LJ_E_INVAL, "join_host: index is NULL");
+  if (m >= (1ull << 32)) return fail(LJ_E_INVAL, "join_host: m must be below 2^32");
+  if (m > 0 && !S_host) return fail(LJ_E_INVAL, "join_host: S is NULL");
+  if (capacity > 0 && !pairs_host) return fail(LJ_E_INVAL, "join_host: pairs is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m == 0) {
+    if (written_host) *written_host = 0;
+    return LJ_OK;
+  }
+  Streams st;
+  LJ_CUDA(cudaStreamCreateWithFlags(&st.in, cudaStreamNonBlocking));
+  LJ_CUDA(cudaStreamCreateWithFlags(&st.out, cudaStreamNonBlocking));
+  for (auto& e : st.ev) LJ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t* in_done = st.ev;        // [2]
+  cudaEvent_t* comp_done = st.ev + 2;  // [2]
+  cudaEvent_t* out_done = st.ev + 4;   // [2]
+  const uint64_t chunk = std::min<uint64_t>(m, kHostChunk);
+  const uint64_t nchunks = (m + chunk - 1) / chunk;
+  uint64_t written = 0;
+
+  if (idx->unique) {
+    char* ws = nullptr;
+    const size_t bytes = 4 * chunk * 8 + 256;
+    LJ_CUDA(scratch_alloc((void**)&ws, bytes, s));
+    uint64_t* Sd[2] = {(uint64_t*)ws, (uint64_t*)(ws + chunk * 8)};
+    lj_pair* Pd[2] = {(lj_pair*)(ws + 2 * chunk * 8), (lj_pair*)(ws + 3 * chunk * 8)};
+    uint64_t* tot_d = (uint64_t*)(ws + 4 * chunk * 8);
+    uint64_t* tot_h = nullptr;
+    LJ_CUDA(cudaMallocHost(&tot_h, 2 * sizeof(uint64_t)));
+    int rc = 0;
+    auto issue = [&](uint64_t c) -> int {
+      const int b = (int)(c & 1);
+      const uint64_t off = c * chunk, len = std::min(chunk, m - off);
+      // S buffer b was last read by compute(c-2)
+      LJ_CUDA(cudaStreamWaitEvent(st.in, comp_done[b], 0));
+      LJ_CUDA(cudaMemcpyAsync(Sd[b], S_host + off, len * 8, cudaMemcpyHostToDevice, st.in));
+      LJ_CUDA(cudaEventRecord(in_done[b], st.in));
+      LJ_CUDA(cudaStreamWaitEvent(s, in_done[b], 0));
+      LJ_CUDA(cudaStreamWaitEvent(s, out_done[b], 0));   // pair buffer b drained
+      if (int r = probe_emit_impl(idx, Sd[b], len, nullptr, Pd[b], len, tot_d + b, nullptr,
+                                  (uint32_t)off, s))
+        return r;
+      LJ_CUDA(cudaMemcpyAsync(tot_h + b, tot_d + b, 8, cudaMemcpyDeviceToHost, s));
+      LJ_CUDA(cudaEventRecord(comp_done[b], s));
+      return 0;
+    };
+    rc = issue(0);
+    for (uint64_t c = 0; c < nchunks && !rc; ++c) {
+      if (c + 1 < nchunks && (rc = issue(c + 1))) break;
+      const int b = (int)(c & 1);
+      if (cudaEventSynchronize(comp_done[b]) != cudaSuccess) {
+        rc = fail(LJ_E_CUDA, "join_host: chunk %llu failed", (unsigned long long)c);
+        break;
+      }
+      const uint64_t cnt = tot_h[b];
+      const uint64_t room = capacity > written ? capacity - written : 0;
+      const uint64_t take = std::min(cnt, room);
+      cudaStreamWaitEvent(st.out, comp_done[b], 0);
+      if (take)
+        cudaMemcpyAsync(pairs_host + written, Pd[b], take * 8, cudaMemcpyDeviceToHost, st.out);
+      cudaEventRecord(out_done[b], st.out);
+      written += cnt;
+    }
+    cudaStreamSynchronize(st.out);
+    cudaStreamSynchronize(s);
+    cudaFreeHost(tot_h);
+    scratch_free(ws, s);
+    cudaStreamSynchronize(s);
+    if (rc) return rc;
+  } else {
+    char* ws = nullptr;
+    LJ_CUDA(scratch_alloc((void**)&ws, chunk * 8 + (chunk + 1) * 8 + 256, s));
+    uint64_t* Sd = (uint64_t*)ws;
+    uint64_t* off_d = (uint64_t*)(ws + chunk * 8);
+    int rc = 0;
+    for (uint64_t c = 0; c < nchunks && !rc; ++c) {
+      const uint64_t off = c * chunk, len = std::min(chunk, m - off);
+      if (cudaMemcpyAsync(Sd, S_host + off, len * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        rc = fail(LJ_E_CUDA, "join_host: copy-in failed");
+        break;
+      }
+      uint64_t cnt = 0;
+      if ((rc = probe_count_impl(idx, Sd, len, nullptr, off_d, nullptr, &cnt, s))) break;
+      const uint64_t room = capacity > written ? capacity - written : 0;
+      const uint64_t take = std::min(cnt, room);
+      if (take) {
+        lj_pair* Pd = nullptr;
+        if (scratch_alloc((void**)&Pd, take * 8, s) != cudaSuccess) {
+          rc = fail(LJ_E_NOMEM, "join_host: no room for %llu pairs", (unsigned long long)take);
+          break;
+        }
+        if ((rc = probe_emit_impl(idx, Sd, len, off_d, Pd, take, nullptr, nullptr, (uint32_t)off,
+                                  s)))
+          break;
+        cudaMemcpyAsync(pairs_host + written, Pd, take * 8, cudaMemcpyDeviceToHost, s);
+        scratch_free(Pd, s);
+      }
+      written += cnt;
+    }
+    cudaStreamSynchronize(s);
+    scratch_free(ws, s);
+    cudaStreamSynchronize(s);
+    if (rc) return rc;
+  }
+  if (written_host) *written_host = written;
+  // a capacity overflow inside a chunk (take < cnt) also sets the device word
+  const int dev_rc = take_device_errors(idx->device, s);
+  if (written > capacity)
+    return fail(LJ_E_CAPACITY, "join_host: %llu pairs do not fit the capacity of %llu",
+                (unsigned long long)written, (unsigned long long)capacity);
+  return dev_rc;
+}

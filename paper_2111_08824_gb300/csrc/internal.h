@@ -1,0 +1,51 @@
+// Host-side internals shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/ljoin.h"
+
+struct lj_index {
+  const uint64_t* R = nullptr;   // borrowed, sorted
+  uint64_t n = 0;
+  uint32_t L = 0;
+  int precision = LJ_FP32;
+  int device = 0;
+  void* leaves = nullptr;        // L records (LeafF32 or LeafF64), device
+  double root_fit[2] = {0, 0};   // least-squares root (double)
+  float root_f32[2] = {0, 0};    // deployed single-precision root
+  double root_f64[2] = {0, 0};   // deployed double-precision root
+  int unique = 1;
+  lj_index_stats stats{};
+};
+
+namespace lj {
+
+// Thread-local error message; returns `code` for convenient `return fail(...)`.
+int fail(int code, const char* fmt, ...);
+int fail_cuda(cudaError_t e, const char* what);
+
+#define LJ_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ::lj::fail_cuda(e_, #call); \
+  } while (0)
+
+// Stream-ordered scratch memory from a library-owned pool (one per device,
+// release threshold = unlimited, so repeated calls reuse the same memory).
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+cudaError_t scratch_free(void* p, cudaStream_t s);
+
+// Sticky per-device error word that kernels OR bits into (kErr*).
+uint32_t* device_error_word(int device);
+// Read and clear the error word after `s` has been synchronised; maps bits to
+// an LJ_E_* code (0 if clean).
+int take_device_errors(int device, cudaStream_t s);
+
+int current_device();
+
+}  // namespace lj

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element.
+
+Join results are compared exactly (the pairs are a set, and both sides write
+them in the same canonical order: s_idx ascending, r_idx ascending).  Index
+builds are compared through tests/_validate.py.  Sizes span several probe
+tiles (2048 probes each) plus a ragged tail, and cover the degenerate cases
+of the method: empty inputs, one key, one leaf, more leaves than keys, all
+keys equal, keys 0 and 2^64-1, float32-collapsing clusters, misses below
+the minimum and above the maximum, misaligned S.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import _validate
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOP = np.uint64(2**64 - 1)
+
+
+def _lj():
+    import paper_2111_08824_gb300 as lj
+    return lj
+
+
+def dev(a: np.ndarray):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return torch.from_numpy(a.view(np.int64)).cuda()
+
+
+def gpu_join(R, S, L, prec="fp32", path="auto", misalign=False):
+    lj = _lj()
+    Rd = dev(R)
+    if misalign:
+        Sfull = dev(np.concatenate([np.zeros(1, np.uint64), S]))
+        Sd = Sfull[1:]
+    else:
+        Sd = dev(S)
+    idx = lj.rmi_build(Rd, L, prec)
+    unique = bool(idx.stats()["unique"])
+    if path == "auto":
+        path = "fused" if unique else "two_pass"
+    m = S.size
+    if path == "fused":
+        pairs = torch.full((max(m, 1), 2), -1, dtype=torch.int32, device="cuda")
+        total = lj.join_emit(idx, Sd, pairs)
+        counts = offsets = None
+    else:
+        offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+        counts = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+        total = lj.join_count(idx, Sd, counts, offsets)
+        pairs = torch.full((max(total, 1), 2), -1, dtype=torch.int32, device="cuda")
+        written = lj.join_emit(idx, Sd, pairs, offsets=offsets)
+        assert written == total
+        counts = counts[:m].cpu().numpy().view(np.uint32)
+        offsets = offsets.cpu().numpy().view(np.uint64)
+    torch.cuda.synchronize()
+    out = pairs[:total].cpu().numpy().view(np.uint32)
+    return out, total, counts, offsets, idx
+
+
+def check_against_oracle(R, S, L, prec="fp32", path="auto", misalign=False):
+    got, total, counts, offsets, idx = gpu_join(R, S, L, prec, path, misalign)
+    lo, hi, want_total = oracle.join_ranges(R, S)
+    assert total == want_total
+    want = oracle.join_pairs(R, S)
+    assert np.array_equal(got, want)
+    if counts is not None:
+        assert np.array_equal(counts.astype(np.uint64), hi - lo)
+        assert offsets[0] == 0 and np.array_equal(np.diff(offsets.astype(np.int64)),
+                                                  (hi - lo).astype(np.int64))
+    return idx
+
+
+def _probe_mix(rng, R, m):
+    """Hits, near misses, misses below/above the range, extremes."""
+    parts = []
+    if R.size:
+        parts.append(R[rng.integers(0, R.size, m // 2)])
+        near = R[rng.integers(0, R.size, m // 4)]
+        parts.append(near + np.uint64(1))
+    parts.append(rng.integers(0, 2**64 - 1, m - sum(p.size for p in parts), dtype=np.uint64,
+                              endpoint=True))
+    S = np.concatenate(parts + [np.array([0, 1, TOP, TOP - np.uint64(1)], np.uint64)])
+    rng.shuffle(S)
+    return S
+
+
+def _relation(kind, rng, n):
+    if kind == "uniform":
+        return np.unique(rng.integers(0, 2**63, n, dtype=np.uint64))
+    if kind == "lognormal":
+        return np.unique(np.rint(1e9 * np.exp(2 * rng.standard_normal(n))).astype(np.uint64))
+    if kind == "clusters":   # tight clusters far apart: collapse under float32
+        c = rng.integers(0, 2**62, 16, dtype=np.uint64)
+        return np.unique(c[rng.integers(0, 16, n)] + rng.integers(0, 5000, n).astype(np.uint64))
+    if kind == "extremes":
+        return np.unique(np.concatenate([rng.integers(0, 2**64 - 1, n, dtype=np.uint64,
+                                                      endpoint=True), [0, TOP]]).astype(np.uint64))
+    raise ValueError(kind)
+
+
+# ------------------------------------------------------------ index build --
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("kind", ["uniform", "lognormal", "clusters", "extremes"])
+@pytest.mark.parametrize("L", [1, 7, 4096, 300000])
+def test_rmi_build_parity(kind, L, prec):
+    rng = np.random.default_rng(zlib.crc32(f"{kind}{L}{prec}".encode()))
+    R = _relation(kind, rng, 100000)
+    lj = _lj()
+    idx = lj.rmi_build(dev(R), L, prec)
+    gpu = lj.rmi_export(idx)
+    ora = oracle.rmi_fit(R, L, fp64=(prec == "fp64"))
+    _validate.compare_index(R, gpu, ora, fp64=(prec == "fp64"))
+    st = idx.stats()
+    assert st["unique"] == 1 and st["n"] == R.size and st["leaves"] == L
+
+
+def test_rmi_build_with_duplicates_parity():
+    rng = np.random.default_rng(5)
+    R = np.sort(rng.integers(0, 3000, 200000, dtype=np.uint64))
+    lj = _lj()
+    for prec in ("fp32", "fp64"):
+        idx = lj.rmi_build(dev(R), 1000, prec)
+        assert idx.stats()["unique"] == 0
+        _validate.compare_index(R, lj.rmi_export(idx), oracle.rmi_fit(R, 1000, prec == "fp64"),
+                                prec == "fp64")
+
+
+def test_rmi_build_is_deterministic():
+    rng = np.random.default_rng(6)
+    R = _relation("lognormal", rng, 300000)
+    lj = _lj()
+    a = lj.rmi_export(lj.rmi_build(dev(R), 5000, "fp32"))
+    b = lj.rmi_export(lj.rmi_build(dev(R), 5000, "fp32"))
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+
+
+# ------------------------------------------------------------------ joins --
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("kind", ["uniform", "lognormal", "clusters", "extremes"])
+@pytest.mark.parametrize("path", ["fused", "two_pass"])
+def test_join_unique_parity(kind, path, prec):
+    rng = np.random.default_rng(zlib.crc32(f"{kind}{path}{prec}".encode()))
+    R = _relation(kind, rng, 60000)
+    S = _probe_mix(rng, R, 2048 * 5 + 37)
+    for L in (1, 512, 100000):
+        check_against_oracle(R, S, L, prec, path)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_join_duplicates_parity(prec):
+    rng = np.random.default_rng(21)
+    R = np.sort(np.concatenate([rng.integers(0, 5000, 40000, dtype=np.uint64),
+                                np.full(300, 777, np.uint64), [0, 0, TOP, TOP]]).astype(np.uint64))
+    S = np.concatenate([R[rng.integers(0, R.size, 6000)],
+                        rng.integers(0, 6000, 4000, dtype=np.uint64), [TOP, 0, 777]])
+    for L in (1, 64, 5000, 100000):
+        check_against_oracle(R, S, L, prec, "two_pass")
+
+
+def test_join_misaligned_S_uses_scalar_loads():
+    rng = np.random.default_rng(22)
+    R = _relation("uniform", rng, 30000)
+    S = _probe_mix(rng, R, 2048 * 3 + 5)
+    for path in ("fused", "two_pass"):
+        check_against_oracle(R, S, 2048, "fp32", path, misalign=True)
+
+
+@pytest.mark.parametrize("case", ["empty_R", "empty_S", "both_empty", "one_key", "all_equal",
+                                  "leaves_gg_n", "self_join", "below_above"])
+def test_join_degenerate(case):
+    rng = np.random.default_rng(23)
+    if case == "empty_R":
+        R, S, L = np.zeros(0, np.uint64), rng.integers(0, 100, 5000, dtype=np.uint64), 16
+    elif case == "empty_S":
+        R, S, L = np.arange(100, dtype=np.uint64), np.zeros(0, np.uint64), 16
+    elif case == "both_empty":
+        R, S, L = np.zeros(0, np.uint64), np.zeros(0, np.uint64), 1
+    elif case == "one_key":
+        R, S, L = np.array([42], np.uint64), np.array([41, 42, 43, 42], np.uint64), 4
+    elif case == "all_equal":
+        R, S, L = np.full(3000, 9, np.uint64), np.array([9, 8, 9, 10] * 500, np.uint64), 64
+    elif case == "leaves_gg_n":
+        R = np.unique(rng.integers(0, 2**40, 500, dtype=np.uint64))
+        S, L = _probe_mix(rng, R, 3000), 1 << 20
+    elif case == "self_join":
+        R = _relation("lognormal", rng, 50000)
+        S, L = R.copy(), 3000
+    else:
+        R = np.arange(1000, 2000, dtype=np.uint64) * np.uint64(7)
+        S, L = np.array([0, 6999, 14000, TOP, 7000, 13993], np.uint64), 10
+    for path in ("auto", "two_pass"):
+        for prec in ("fp32", "fp64"):
+            check_against_oracle(R, S, L, prec, path)
+
+
+def test_error_codes():
+    lj = _lj()
+    with pytest.raises(lj.LJoinError) as e:
+        lj.rmi_build(dev(np.array([3, 2, 1], np.uint64)), 4)
+    assert e.value.code == -4                     # LJ_E_UNSORTED
+    with pytest.raises(lj.LJoinError) as e:
+        lj.rmi_build(dev(np.array([1, 2], np.uint64)), 0)
+    assert e.value.code == -1                     # LJ_E_INVAL
+    R = np.array([1, 1, 2], np.uint64)
+    idx = lj.rmi_build(dev(R), 2)
+    pairs = torch.empty((8, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(lj.LJoinError) as e:
+        lj.join_emit(idx, dev(np.array([1], np.uint64)), pairs)
+    assert e.value.code == -8                     # LJ_E_NOTUNIQUE
+    # capacity overflow is reported, the first `capacity` pairs are written
+    R = np.arange(100, dtype=np.uint64)
+    idx = lj.rmi_build(dev(R), 8)
+    small = torch.full((10, 2), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(lj.LJoinError) as e:
+        lj.join_emit(idx, dev(R), small)
+    assert e.value.code == -5                     # LJ_E_CAPACITY
+    got = small.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, np.stack([np.arange(10), np.arange(10)], 1).astype(np.uint32))
+    # the error word is cleared: the next call succeeds
+    full = torch.empty((100, 2), dtype=torch.int32, device="cuda")
+    assert lj.join_emit(idx, dev(R), full) == 100
+
+
+def test_join_host_matches_device_path():
+    lj = _lj()
+    rng = np.random.default_rng(24)
+    R = _relation("lognormal", rng, 80000)
+    S = _probe_mix(rng, R, 50000)
+    idx = lj.rmi_build(dev(R), 4096, "fp32")
+    want = oracle.join_pairs(R, S)
+    pairs = np.zeros((S.size, 2), np.uint32)
+    total = lj.join_host(idx, S, pairs)
+    assert total == want.shape[0] and np.array_equal(pairs[:total], want)
+    Rd = np.sort(np.concatenate([R, R[::3]]))
+    idx2 = lj.rmi_build(dev(Rd), 4096, "fp32")
+    want2 = oracle.join_pairs(Rd, S)
+    pairs2 = np.zeros((want2.shape[0], 2), np.uint32)
+    total2 = lj.join_host(idx2, S, pairs2)
+    assert total2 == want2.shape[0] and np.array_equal(pairs2, want2)
