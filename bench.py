@@ -117,7 +117,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
-    wl = w["fn"](seed=args.seed, **w["kw"])
+    wl = w["fn"](seed=args.seed, **_overrides(args))
     m_s = min(wl.S.size, args.ref_sample)
     oracle.build()
     times = []
@@ -143,6 +143,17 @@ def run_reference(args, rank, world):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _overrides(args) -> dict:
+    kw = dict(WORKLOADS[args.workload]["kw"])
+    if args.n is not None:
+        kw["rows" if args.workload == "dup_seqh_50m" else "n"] = args.n
+    if args.m is not None:
+        kw["m"] = args.m
+    if args.leaves is not None:
+        kw["leaves"] = args.leaves
+    return kw
 
 
 def _config(args, wl):
@@ -176,6 +187,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
     ap.add_argument("--ref-sample", type=int, default=1 << 23)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override |R| (profiling runs)")
+    ap.add_argument("--m", type=int, default=None, help="override |S| (profiling runs)")
+    ap.add_argument("--leaves", type=int, default=None, help="override L (profiling runs)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -193,7 +207,7 @@ def main():
     w = WORKLOADS[args.workload]
     # weak scaling: every rank probes its own S (seeded by rank) against the
     # replicated R; no collective on the data path.
-    wl = w["fn"](seed=args.seed + 1000 * rank, **w["kw"]) if rank else w["fn"](seed=args.seed, **w["kw"])
+    wl = w["fn"](seed=args.seed + 1000 * rank, **_overrides(args))
     n, m, L = wl.R.size, wl.S.size, wl.leaves
 
     Rd = torch.from_numpy(wl.R.view(np.int64)).cuda()
@@ -259,13 +273,15 @@ def main():
     P_host = torch.empty((max(total, 1), 2), dtype=torch.int32).pin_memory()
     S_np = S_host.numpy().view(np.uint64)
     P_np = P_host.numpy().view(np.uint32)
-    lj.join_host(idx, S_np, P_np)          # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        got = lj.join_host(idx, S_np, P_np)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    assert got == total
+    e2e_s = None
+    if args.e2e_steps > 0:
+        lj.join_host(idx, S_np, P_np)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            got = lj.join_host(idx, S_np, P_np)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        assert got == total
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = _peaks()
@@ -287,8 +303,9 @@ def main():
                      "peak_kind": peak_kind,
                      "kernel": "probe_tile_kernel" if unique else "probe_tile_kernel+emit_kernel",
                      "alg_bytes_per_launch": alg_bytes},
-        "e2e": {"value": world * m / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * m,
-                "d2h_bytes_per_step": 8 * total},
+        "e2e": None if e2e_s is None else {
+            "value": world * m / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * m,
+            "d2h_bytes_per_step": 8 * total},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

@@ -132,8 +132,9 @@ int rmi_export(const lj_index* index, double* root_host, uint64_t* leaf_lo,
  *   offsets_dev  optional, m+1 uint64: exclusive prefix sum of c,
  *                offsets[m] = |J|
  *   total_host   optional: |J|; if given the call synchronises.
- * One fused kernel: learned lookup (root, leaf, bounded lower/upper-bound
- * search) + single-pass decoupled look-back scan.
+ * Learned lookup (root, leaf, bounded lower/upper-bound search) and a scan:
+ * one kernel with a decoupled look-back for batches up to "single_pass_max"
+ * keys (lj_set_option), else a search kernel followed by a streaming scan.
  * Errors: LJ_E_INVAL, LJ_E_NOMEM, LJ_E_CUDA, LJ_E_TIMEOUT.
  */
 int join_count(const lj_index* index, const uint64_t* S_dev, uint64_t m,
@@ -142,10 +143,12 @@ int join_count(const lj_index* index, const uint64_t* S_dev, uint64_t m,
 
 /*
  * join_emit -- write the join pairs (Section 2.A; Section 6.B).
- *   offsets_dev   m+1 offsets from join_count (two-pass path), or NULL for the
- *                 single-pass path (lookup + in-kernel scan + emit in one
- *                 kernel), which needs an index whose R has no duplicate key
- *                 (else LJ_E_NOTUNIQUE).
+ *   offsets_dev   m+1 offsets from join_count (two-pass path), or NULL for
+ *                 the direct path, which needs an index whose R has no
+ *                 duplicate key (else LJ_E_NOTUNIQUE): lookup, scan and
+ *                 write in one kernel for batches up to "single_pass_max"
+ *                 keys, else a search kernel and a scan kernel that writes
+ *                 the pairs.
  *   pairs_dev     capacity pairs; pairs beyond capacity are not written.
  *   written_dev   optional device uint64: |J| (stream-ordered, no sync)
  *   written_host  optional host uint64: |J|; if given the call synchronises
@@ -170,6 +173,19 @@ int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
               lj_stream_t stream);
 
 /* ------------------------------------------------------ diagnostics ----- */
+
+/*
+ * lj_set_option / lj_get_option -- process-wide tuning knobs.
+ *   "single_pass_max"  probe batches of at most this many keys use the
+ *                      single-pass kernel (lookup + scan + write in one
+ *                      launch); larger ones use the count-scan-emit pipeline
+ *                      (search kernel, then a streaming scan).  Default 2^20.
+ *                      Both paths give identical results.
+ * lj_set_option returns LJ_OK or LJ_E_INVAL (unknown name, bad value);
+ * lj_get_option returns the value, or -1 for an unknown name.
+ */
+int lj_set_option(const char* name, int64_t value);
+int64_t lj_get_option(const char* name);
 
 /* Thread-local message describing the last error of this thread. */
 const char* lj_last_error(void);

@@ -72,8 +72,12 @@ def _load():
 
 
 def _u64(a) -> np.ndarray:
-    a = np.ascontiguousarray(a, dtype=np.uint64)
-    return a
+    a = np.asarray(a)
+    if a.dtype != np.uint64:
+        if a.dtype.kind not in "iu" or (a.size and a.min() < 0):
+            raise TypeError(f"keys must be unsigned 64-bit integers, got {a.dtype}")
+        a = a.astype(np.uint64)
+    return np.ascontiguousarray(a)
 
 
 def _ptr(a: np.ndarray):

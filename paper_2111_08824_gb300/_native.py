@@ -51,6 +51,8 @@ SIGNATURES = {
     "join_count": ([_P, _P, _U64, _P, _P, _P, _P], _I),
     "join_emit": ([_P, _P, _U64, _P, _P, _U64, _P, _P, _P], _I),
     "join_host": ([_P, _P, _U64, _P, _U64, _P, _P], _I),
+    "lj_set_option": ([ctypes.c_char_p, ctypes.c_int64], _I),
+    "lj_get_option": ([ctypes.c_char_p], ctypes.c_int64),
     "lj_last_error": ([], ctypes.c_char_p),
     "lj_version": ([], ctypes.c_char_p),
 }
@@ -192,6 +194,17 @@ def join_host(index: Index, S_host: np.ndarray, pairs_host: np.ndarray, stream=N
     _check(load().join_host(index.handle, _ptr(S_host), S_host.size, _ptr(pairs_host),
                             pairs_host.shape[0], ctypes.byref(total), _stream_ptr(stream)))
     return total.value
+
+
+def lj_set_option(name: str, value: int):
+    _check(load().lj_set_option(name.encode(), int(value)))
+
+
+def lj_get_option(name: str) -> int:
+    v = load().lj_get_option(name.encode())
+    if v == -1:
+        raise LJoinError(-1, lj_last_error())
+    return v
 
 
 def lj_last_error() -> str:

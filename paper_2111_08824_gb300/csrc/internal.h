@@ -48,4 +48,8 @@ int take_device_errors(int device, cudaStream_t s);
 
 int current_device();
 
+// Probe batches of at most this many keys take the single-pass kernel.
+void set_single_pass_max(uint64_t v);
+uint64_t get_single_pass_max();
+
 }  // namespace lj

@@ -6,21 +6,25 @@
 // every match in the range is returned.  Output pairs are written s-major,
 // r-ascending.
 //
-// Kernels
-//   probe_tile_kernel<Model, MODE, K, VEC>
-//     One tile = 256 threads x K rounds x 2 probes (one 16-byte load of two
-//     keys per thread and round).  Each thread keeps its 2K lookups in flight
-//     together (their search loads interleave), then the tile scans its match
-//     counts (warp shuffles + one warp over the per-round warp totals), takes
-//     its global offset with a single-pass decoupled look-back and writes:
-//       MODE kUniqueEmit   (r, j) pairs directly (single-pass join; R unique)
-//       MODE kUniqueCount  counts / offsets, one search per probe (R unique)
-//       MODE kDupCount     counts / offsets from a lower- and an upper-bound
-//                          search (any R)
-//   emit_kernel<Model>
-//     Two-pass emit: recomputes each probe's lower bound, reads its offset,
-//     and lets each warp write the contiguous output range of its 32 probes
-//     with one coalesced 8-byte store per lane and step.
+// Two execution paths, chosen by the size of the probe batch:
+//   single pass (m <= single_pass_max, default 2^20):
+//     probe_single_pass_kernel<Model, MODE, K, VEC>: block tiles of 256
+//     threads x K rounds x 2 probes; lookups, block scan, decoupled look-back
+//     and writes in one launch.
+//   count-scan-emit pipeline (larger batches):
+//     probe_search_kernel: lookups only, one 32-bit word per probe (first
+//       match or "none" for a unique R, the match count otherwise); no scan
+//       and no barrier, so a warp never waits for a slower one.
+//     scan_kernel: streaming scan of those words in uniform tiles (short
+//       look-back waits), output staged in shared memory and written with
+//       coalesced stores (pairs, or offsets / counts).
+//   Measured on the 100M x 400M lognormal workload, the single-pass kernel
+//   spent almost half its time waiting in the look-back for tiles whose
+//   searches were slower; the pipeline's extra 8 bytes per probe of
+//   streaming traffic cost far less.
+//   emit_kernel<Model>: two-pass emit from join_count's offsets; recomputes
+//     each probe's lower bound and lets each warp write the contiguous
+//     output range of its 32 probes with coalesced 8-byte stores.
 #include <algorithm>
 #include <cstring>
 
@@ -53,11 +57,40 @@ struct ProbeParams {
   uint32_t num_tiles;
 };
 
+// Tunables (fixed at compile time; the defaults are the measured best).
+#ifndef LJ_ROUNDS
+#define LJ_ROUNDS 4        // probe rounds per thread (2 probes each)
+#endif
+#ifndef LJ_MINB
+#define LJ_MINB 1          // min resident blocks per SM requested from ptxas
+#endif
+#ifndef LJ_FAN
+#define LJ_FAN 2           // search fan-out: FAN-1 independent pivots per round
+#endif
+#ifndef LJ_SROUNDS
+#define LJ_SROUNDS 1       // search kernel: probe rounds per thread (2 probes each)
+#endif
+#ifndef LJ_SBLOCK
+#define LJ_SBLOCK 128      // search kernel: threads per block
+#endif
+#ifndef LJ_SMINB
+#define LJ_SMINB 1
+#endif
+constexpr int kRounds = LJ_ROUNDS;
+constexpr int kSearchRounds = LJ_SROUNDS;
+constexpr int kSearchBlock = LJ_SBLOCK;
+constexpr uint32_t kNoMatch = 0xFFFFFFFFu;
+enum { kScanPairs = 0, kScanOffsets = 1 };
+// probe batches up to this size take the single-pass kernel (one launch)
+uint64_t g_single_pass_max = 1ull << 20;
+
 // Interleaved bounded searches over NP windows.  For each probe p with
 // window [base, base+len): finds c = the last position whose key is < x
 // (STRICT) or <= x (!STRICT), and returns res = c + 1 (so the lower bound,
 // resp. the upper bound, of x) and cv = R[c] when res > window start.
-template <int NP, bool STRICT>
+// Rounds with FAN > 2 cut the window into FAN parts with FAN-1 independent
+// pivot loads (fewer dependent rounds, more loads); the last rounds halve.
+template <int NP, bool STRICT, int FAN = LJ_FAN>
 __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
                                             const uint64_t (&x)[NP], uint32_t (&base)[NP],
                                             uint32_t (&len)[NP], uint64_t (&cv)[NP]) {
@@ -68,6 +101,43 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
     moved[p] = false;
     start[p] = base[p];
     cv[p] = 0;
+  }
+  if (FAN > 2) {
+    // k-ary rounds while the window has at least 2*FAN keys
+    while (true) {
+      bool any = false;
+      uint64_t v[NP][FAN - 1];
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (len[p] >= 2 * FAN) {
+          any = true;
+          const uint32_t step = len[p] / FAN;
+#pragma unroll
+          for (int t = 1; t < FAN; ++t) v[p][t - 1] = ldg_key(R, base[p] + t * step);
+        }
+      if (!any) break;
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (len[p] >= 2 * FAN) {
+          const uint32_t step = len[p] / FAN;
+          int c = 0;
+          uint64_t last = 0;
+#pragma unroll
+          for (int t = 1; t < FAN; ++t) {
+            const bool go = STRICT ? (v[p][t - 1] < x[p]) : (v[p][t - 1] <= x[p]);
+            if (go) {
+              c = t;
+              last = v[p][t - 1];
+            }
+          }
+          if (c > 0) {
+            cv[p] = last;
+            moved[p] = true;
+          }
+          base[p] += c * step;
+          len[p] = c == FAN - 1 ? len[p] - (FAN - 1) * step : step;
+        }
+    }
   }
   while (true) {
     bool any = false;
@@ -113,26 +183,19 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
   }
 }
 
+// Lookups of 2K probes per thread: round k covers probes
+// j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
+// leaf record -> window, then the interleaved bounded searches.  cnt is the
+// number of matches, r_idx the first matching position (when cnt > 0).
 template <class Model, int MODE, int K, bool VEC>
-__global__ void __launch_bounds__(kBlock) probe_tile_kernel(ProbeParams<Model> P) {
+__device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
+                                              uint32_t stride, uint32_t (&r_idx)[2 * K],
+                                              uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
   constexpr int NP = 2 * K;
-  static_assert(K * kWarps <= 32, "per-round warp totals must fit one warp");
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_wpre[K * kWarps];
-  __shared__ uint64_t s_prefix;
-
-  if (threadIdx.x == 0) s_tile = atomicAdd(P.st.ticket, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t tile_base = (uint64_t)tile * (kBlock * NP);
-
-  // ---- load keys: round k, thread t holds probes 2(k*256+t) + {0, 1}
   uint64_t x[NP];
-  bool valid[NP];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const uint64_t j0 = tile_base + 2ull * (k * kBlock + threadIdx.x);
+    const uint64_t j0 = first + 2ull * stride * k;
     if (VEC && j0 + 1 < P.m) {
       const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(P.S + j0));
       x[2 * k] = v.x;
@@ -146,8 +209,6 @@ __global__ void __launch_bounds__(kBlock) probe_tile_kernel(ProbeParams<Model> P
           valid[2 * k + 1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
     }
   }
-
-  // ---- predict: root -> leaf record -> window
   uint32_t base[NP], len[NP];
   {
     uint32_t leaf[NP];
@@ -165,10 +226,6 @@ __global__ void __launch_bounds__(kBlock) probe_tile_kernel(ProbeParams<Model> P
       len[p] = wh - wl;
     }
   }
-
-  // ---- bounded search
-  uint32_t r_idx[NP];
-  uint32_t cnt[NP];
   if (MODE == kDupCount) {
     uint32_t wh[NP];
 #pragma unroll
@@ -197,8 +254,58 @@ __global__ void __launch_bounds__(kBlock) probe_tile_kernel(ProbeParams<Model> P
       r_idx[p] = base[p] - 1;
     }
   }
+}
 
-  // ---- tile scan: per round a warp scan, then one warp over the K*8 totals
+// Writes of one round: pairs (kUniqueEmit) or counts / offsets.
+template <class Model, int MODE, bool VEC>
+__device__ __forceinline__ void write_round(const ProbeParams<Model>& P, uint64_t j0,
+                                            uint64_t o0, uint32_t c0, uint32_t c1, uint32_t r0,
+                                            uint32_t r1, bool v0, bool v1) {
+  const uint64_t o1 = o0 + c0;
+  if (MODE == kUniqueEmit) {
+    if (c0 && o0 < P.capacity) P.pairs[o0] = lj_pair{r0, (uint32_t)(j0 + P.s_base)};
+    if (c1 && o1 < P.capacity) P.pairs[o1] = lj_pair{r1, (uint32_t)(j0 + 1 + P.s_base)};
+  } else if (VEC && v1) {
+    if (P.offsets) *reinterpret_cast<ulonglong2*>(P.offsets + j0) = make_ulonglong2(o0, o1);
+    if (P.counts) *reinterpret_cast<uint2*>(P.counts + j0) = make_uint2(c0, c1);
+  } else {
+    if (v0) {
+      if (P.offsets) P.offsets[j0] = o0;
+      if (P.counts) P.counts[j0] = c0;
+    }
+    if (v1) {
+      if (P.offsets) P.offsets[j0 + 1] = o1;
+      if (P.counts) P.counts[j0 + 1] = c1;
+    }
+  }
+}
+
+template <class Model, int MODE>
+__device__ __forceinline__ void last_tile_total(const ProbeParams<Model>& P, uint64_t total) {
+  *P.total_ws = total;
+  if (P.total_out) *P.total_out = total;
+  if (P.offsets) P.offsets[P.m] = total;
+  if (MODE == kUniqueEmit && total > P.capacity) atomicOr(P.err, kErrCapacity);
+}
+
+
+// Single-pass kernel (small probe batches): block tiles of 256 threads x K
+// rounds x 2 probes; the block scans its counts, warp 0 takes the tile's
+// offset by look-back, then the block writes pairs or offsets directly.
+template <class Model, int MODE, int K, bool VEC>
+__global__ void __launch_bounds__(kBlock, LJ_MINB) probe_single_pass_kernel(ProbeParams<Model> P) {
+  static_assert(K * kWarps <= 32, "per-round warp totals must fit one warp");
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_wpre[K * kWarps];
+  __shared__ uint64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(P.st.ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t tile_base = (uint64_t)tile * (kBlock * 2 * K);
+  uint32_t r_idx[2 * K], cnt[2 * K];
+  bool valid[2 * K];
+  lookup_probes<Model, MODE, K, VEC>(P, tile_base + 2ull * threadIdx.x, kBlock, r_idx, cnt, valid);
   uint64_t lane_excl[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -216,44 +323,17 @@ __global__ void __launch_bounds__(kBlock) probe_tile_kernel(ProbeParams<Model> P
     const uint64_t pre = lookback_warp(P.st, tile, agg, P.err);
     if (lane == 0) {
       s_prefix = pre;
-      if (tile + 1 == P.num_tiles) {
-        const uint64_t total = pre + agg;
-        *P.total_ws = total;
-        if (P.total_out) *P.total_out = total;
-        if (P.offsets) P.offsets[P.m] = total;
-        if (MODE == kUniqueEmit && total > P.capacity) atomicOr(P.err, kErrCapacity);
-      }
+      if (tile + 1 == P.num_tiles) last_tile_total<Model, MODE>(P, pre + agg);
     }
   }
   __syncthreads();
   const uint64_t tile_prefix = s_prefix;
-
-  // ---- outputs
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint64_t j0 = tile_base + 2ull * (k * kBlock + threadIdx.x);
-    const uint64_t o0 = tile_prefix + s_wpre[k * kWarps + warp] + lane_excl[k];
-    const uint64_t o1 = o0 + cnt[2 * k];
-    if (MODE == kUniqueEmit) {
-      if (cnt[2 * k] && o0 < P.capacity)
-        P.pairs[o0] = lj_pair{r_idx[2 * k], (uint32_t)(j0 + P.s_base)};
-      if (cnt[2 * k + 1] && o1 < P.capacity)
-        P.pairs[o1] = lj_pair{r_idx[2 * k + 1], (uint32_t)(j0 + 1 + P.s_base)};
-    } else {
-      if (VEC && j0 + 1 < P.m) {
-        if (P.offsets) *reinterpret_cast<ulonglong2*>(P.offsets + j0) = make_ulonglong2(o0, o1);
-        if (P.counts) *reinterpret_cast<uint2*>(P.counts + j0) = make_uint2(cnt[2 * k], cnt[2 * k + 1]);
-      } else {
-        if (valid[2 * k]) {
-          if (P.offsets) P.offsets[j0] = o0;
-          if (P.counts) P.counts[j0] = cnt[2 * k];
-        }
-        if (valid[2 * k + 1]) {
-          if (P.offsets) P.offsets[j0 + 1] = o1;
-          if (P.counts) P.counts[j0 + 1] = cnt[2 * k + 1];
-        }
-      }
-    }
+    write_round<Model, MODE, VEC>(P, j0, tile_prefix + s_wpre[k * kWarps + warp] + lane_excl[k],
+                                  cnt[2 * k], cnt[2 * k + 1], r_idx[2 * k], r_idx[2 * k + 1],
+                                  valid[2 * k], valid[2 * k + 1]);
   }
 }
 
@@ -300,20 +380,178 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
   }
 }
 
-constexpr int kRounds = 4;   // probes per thread = 2 * kRounds
-constexpr uint64_t kTileProbes = (uint64_t)kBlock * 2 * kRounds;
+// Search kernel of the count-scan-emit pipeline: every thread looks up 2K
+// probes (j0 = 2*(t + k*T) + {0, 1}, T threads in the grid) and writes one
+// 32-bit word per probe, with no scan and no barrier, so warps never wait
+// for one another:
+//   kUniqueCount  out[j] = first matching position, or kNoMatch
+//   kDupCount     out[j] = number of matches
+template <class Model, int MODE, int K, bool VEC>
+__global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
+    probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t T = gridDim.x * (uint64_t)blockDim.x;
+  uint32_t r_idx[2 * K], cnt[2 * K];
+  bool valid[2 * K];
+  lookup_probes<Model, MODE, K, VEC>(P, 2 * t, (uint32_t)T, r_idx, cnt, valid);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t j0 = 2 * (t + k * T);
+    uint32_t w0, w1;
+    if (MODE == kDupCount) {
+      w0 = cnt[2 * k];
+      w1 = cnt[2 * k + 1];
+    } else {
+      w0 = cnt[2 * k] ? r_idx[2 * k] : kNoMatch;
+      w1 = cnt[2 * k + 1] ? r_idx[2 * k + 1] : kNoMatch;
+    }
+    if (VEC && valid[2 * k + 1]) {
+      *reinterpret_cast<uint2*>(out + j0) = make_uint2(w0, w1);
+    } else {
+      if (valid[2 * k]) out[j0] = w0;
+      if (valid[2 * k + 1]) out[j0 + 1] = w1;
+    }
+  }
+}
+
+// Scan kernel of the pipeline: tiles of 256 threads x 16 words.  Each tile
+// counts its words (kFromMatches: word != kNoMatch; kFromCounts: the word),
+// scans them in the block, takes its offset by decoupled look-back (tiles are
+// uniform, so waits are short), stages its output in shared memory and writes
+// it with coalesced stores:
+//   kScanPairs     (r_idx, s_idx) pairs of the matching probes
+//   kScanOffsets   offsets[j] (u64, exclusive) and optionally counts[j]
+struct ScanParams {
+  const uint32_t* in;
+  uint64_t m;
+  uint32_t s_base;
+  lj_pair* pairs;
+  uint64_t capacity;
+  uint64_t* offsets;
+  uint32_t* counts;       // kScanOffsets from matches: optional 0/1 counts
+  uint64_t* total_ws;
+  uint64_t* total_out;
+  TileState st;
+  uint32_t* err;
+  uint32_t num_tiles;
+};
+
+constexpr int kScanItems = 16;
+constexpr uint64_t kScanTile = (uint64_t)kBlock * kScanItems;
+
+template <int MODE, bool FROM_COUNTS, bool VEC>
+__global__ void __launch_bounds__(kBlock) scan_kernel(ScanParams P) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp[kWarps];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint64_t s_stage[kScanTile];   // 32 KB
+  __shared__ uint64_t s_count;
+  if (threadIdx.x == 0) s_tile = atomicAdd(P.st.ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t tile_base = (uint64_t)tile * kScanTile;
+  const uint64_t base = tile_base + (uint64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  if (VEC && base + kScanItems <= P.m) {
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q) {
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(P.in + base) + q);
+      v[4 * q] = u.x;
+      v[4 * q + 1] = u.y;
+      v[4 * q + 2] = u.z;
+      v[4 * q + 3] = u.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+      v[i] = base + i < P.m ? __ldg(P.in + base + i) : (FROM_COUNTS ? 0u : kNoMatch);
+  }
+  uint64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) sum += FROM_COUNTS ? v[i] : (v[i] != kNoMatch ? 1u : 0u);
+  const uint64_t inc = warp_inclusive_sum(sum, lane);
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t x = lane < kWarps ? s_warp[lane] : 0;
+    const uint64_t xi = warp_inclusive_sum(x, lane);
+    if (lane < kWarps) s_warp[lane] = xi - x;
+    const uint64_t agg = __shfl_sync(0xffffffffu, xi, 31);
+    const uint64_t pre = lookback_warp(P.st, tile, agg, P.err);
+    if (lane == 0) {
+      s_prefix = pre;
+      if (tile + 1 == P.num_tiles) {
+        const uint64_t total = pre + agg;
+        *P.total_ws = total;
+        if (P.total_out) *P.total_out = total;
+        if (P.offsets) P.offsets[P.m] = total;
+        if (MODE == kScanPairs && total > P.capacity) atomicOr(P.err, kErrCapacity);
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t prefix = s_prefix;
+  uint64_t local = s_warp[warp] + inc - sum;   // offset of this thread's first item in the tile
+  if (MODE == kScanPairs) {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+      if (v[i] != kNoMatch) {
+        s_stage[local] = (uint64_t)v[i] | ((uint64_t)(uint32_t)(base + i + P.s_base) << 32);
+        ++local;
+      }
+    if (threadIdx.x == kBlock - 1) s_count = local;   // the tile's number of pairs
+    __syncthreads();
+    const uint64_t cnt = s_count;
+    uint64_t* out = reinterpret_cast<uint64_t*>(P.pairs);
+    for (uint64_t q = threadIdx.x; q < cnt; q += kBlock) {
+      const uint64_t o = prefix + q;
+      if (o < P.capacity) out[o] = s_stage[q];
+    }
+  } else {
+    const uint32_t first = threadIdx.x * kScanItems;
+    if (P.offsets) {
+#pragma unroll
+      for (int i = 0; i < kScanItems; ++i) {
+        s_stage[first + i] = prefix + local;
+        local += FROM_COUNTS ? v[i] : (v[i] != kNoMatch ? 1u : 0u);
+      }
+    }
+    if (!FROM_COUNTS && P.counts && base < P.m) {
+      if (VEC && base + kScanItems <= P.m) {
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q)
+          reinterpret_cast<uint4*>(P.counts + base)[q] =
+              make_uint4(v[4 * q] != kNoMatch, v[4 * q + 1] != kNoMatch, v[4 * q + 2] != kNoMatch,
+                         v[4 * q + 3] != kNoMatch);
+      } else {
+        for (int i = 0; i < kScanItems; ++i)
+          if (base + i < P.m) P.counts[base + i] = v[i] != kNoMatch;
+      }
+    }
+    if (P.offsets) {
+      __syncthreads();
+      const uint64_t len = P.m - tile_base < kScanTile ? P.m - tile_base : kScanTile;
+      for (uint64_t q = threadIdx.x; q < len; q += kBlock) P.offsets[tile_base + q] = s_stage[q];
+    }
+  }
+}
 
 struct Workspace {
   void* mem = nullptr;
   TileState st{};
   uint64_t* total = nullptr;
+  uint32_t* words = nullptr;   // one 32-bit word per probe (search output)
   uint32_t tiles = 0;
 };
 
-int ws_acquire(Workspace& w, uint64_t m, cudaStream_t s) {
-  w.tiles = (uint32_t)std::max<uint64_t>(1, (m + kTileProbes - 1) / kTileProbes);
+// Scratch: header (ticket, total) + tile states for `tiles` tiles + optional
+// per-probe words.  The header and the flags are zeroed on the stream.
+int ws_acquire(Workspace& w, uint32_t tiles, uint64_t words, cudaStream_t s) {
+  w.tiles = std::max<uint32_t>(1, tiles);
   const size_t flags = ((size_t)w.tiles * 4 + 255) / 256 * 256;
-  const size_t bytes = 256 + flags + (size_t)w.tiles * 16;
+  const size_t states = ((size_t)w.tiles * 16 + 255) / 256 * 256;
+  const size_t bytes = 256 + flags + states + words * 4;
   LJ_CUDA(scratch_alloc(&w.mem, bytes, s));
   char* b = (char*)w.mem;
   LJ_CUDA(cudaMemsetAsync(b, 0, 256 + flags, s));
@@ -322,39 +560,49 @@ int ws_acquire(Workspace& w, uint64_t m, cudaStream_t s) {
   w.st.flag = (uint32_t*)(b + 256);
   w.st.agg = (uint64_t*)(b + 256 + flags);
   w.st.incl = w.st.agg + w.tiles;
+  w.words = words ? (uint32_t*)(b + 256 + flags + states) : nullptr;
   return 0;
 }
 
 template <class Model>
-int launch_probe(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
-                 lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
-                 uint64_t* total_dev, uint64_t* total_host, uint32_t s_base, cudaStream_t s) {
-  Workspace w;
-  if (int rc = ws_acquire(w, m, s)) return rc;
-  ProbeParams<Model> P;
+ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
+                               uint32_t s_base) {
+  ProbeParams<Model> P{};
   P.R = idx->R;
   P.leaves = (const typename Model::Leaf*)idx->leaves;
   P.model = model;
   P.S = S;
   P.m = m;
+  P.s_base = s_base;
+  P.err = device_error_word(idx->device);
+  return P;
+}
+
+inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// Single-pass path: one kernel does lookup + scan + write.
+template <class Model>
+int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
+                       lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
+                       uint64_t* total_dev, uint64_t* total_host, uint32_t s_base,
+                       cudaStream_t s) {
+  constexpr uint64_t tile = (uint64_t)kBlock * 2 * kRounds;
+  Workspace w;
+  if (int rc = ws_acquire(w, (uint32_t)((m + tile - 1) / tile), 0, s)) return rc;
+  ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
+  if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   P.pairs = pairs;
   P.capacity = cap;
   P.counts = counts;
   P.offsets = offsets;
   P.total_out = total_dev;
   P.total_ws = w.total;
-  P.s_base = s_base;
   P.st = w.st;
-  P.err = device_error_word(idx->device);
   P.num_tiles = w.tiles;
-  if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
-  const bool vec = (reinterpret_cast<uintptr_t>(S) & 15) == 0 &&
-                   (!offsets || (reinterpret_cast<uintptr_t>(offsets) & 15) == 0) &&
-                   (!counts || (reinterpret_cast<uintptr_t>(counts) & 7) == 0);
-  const dim3 grid(w.tiles), block(kBlock);
-#define LJ_LAUNCH(MODE)                                                            \
-  (vec ? probe_tile_kernel<Model, MODE, kRounds, true><<<grid, block, 0, s>>>(P)  \
-       : probe_tile_kernel<Model, MODE, kRounds, false><<<grid, block, 0, s>>>(P))
+  const bool vec = aligned(S, 16) && (!offsets || aligned(offsets, 16)) && (!counts || aligned(counts, 8));
+#define LJ_LAUNCH(MODE)                                                                     \
+  (vec ? probe_single_pass_kernel<Model, MODE, kRounds, true><<<w.tiles, kBlock, 0, s>>>(P) \
+       : probe_single_pass_kernel<Model, MODE, kRounds, false><<<w.tiles, kBlock, 0, s>>>(P))
   if (mode == kUniqueEmit)
     LJ_LAUNCH(kUniqueEmit);
   else if (mode == kUniqueCount)
@@ -372,22 +620,89 @@ int launch_probe(const lj_index* idx, Model model, int mode, const uint64_t* S, 
   return 0;
 }
 
+// Count-scan-emit path: search kernel -> per-probe words -> scan kernel.
+template <class Model>
+int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
+                    lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
+                    uint64_t* total_dev, uint64_t* total_host, uint32_t s_base, cudaStream_t s) {
+  const bool dup = mode == kDupCount;
+  // duplicates: the search writes counts, into the caller's buffer if given
+  const bool words_in_counts = dup && counts && aligned(counts, 16);
+  Workspace w;
+  if (int rc = ws_acquire(w, (uint32_t)((m + kScanTile - 1) / kScanTile),
+                          words_in_counts ? 0 : ((m + 3) & ~3ull), s))
+    return rc;
+  uint32_t* words = words_in_counts ? counts : w.words;
+  ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
+  if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
+  const bool vec = aligned(S, 16);
+  const uint64_t threads = ((m + 1) / 2 + kSearchRounds - 1) / kSearchRounds;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, (threads + kSearchBlock - 1) / kSearchBlock);
+  if (dup)
+    vec ? probe_search_kernel<Model, kDupCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words)
+        : probe_search_kernel<Model, kDupCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words);
+  else
+    vec ? probe_search_kernel<Model, kUniqueCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words)
+        : probe_search_kernel<Model, kUniqueCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words);
+  LJ_CUDA(cudaGetLastError());
+
+  ScanParams Q{};
+  Q.in = words;
+  Q.m = m;
+  Q.s_base = s_base;
+  Q.pairs = pairs;
+  Q.capacity = cap;
+  Q.offsets = offsets;
+  Q.counts = dup ? nullptr : counts;
+  Q.total_ws = w.total;
+  Q.total_out = total_dev;
+  Q.st = w.st;
+  Q.err = P.err;
+  Q.num_tiles = w.tiles;
+  const bool qvec = aligned(words, 16) && (!Q.counts || aligned(Q.counts, 16));
+  if (mode == kUniqueEmit) {
+    qvec ? scan_kernel<kScanPairs, false, true><<<w.tiles, kBlock, 0, s>>>(Q)
+         : scan_kernel<kScanPairs, false, false><<<w.tiles, kBlock, 0, s>>>(Q);
+  } else {
+    if (dup)
+      qvec ? scan_kernel<kScanOffsets, true, true><<<w.tiles, kBlock, 0, s>>>(Q)
+           : scan_kernel<kScanOffsets, true, false><<<w.tiles, kBlock, 0, s>>>(Q);
+    else
+      qvec ? scan_kernel<kScanOffsets, false, true><<<w.tiles, kBlock, 0, s>>>(Q)
+           : scan_kernel<kScanOffsets, false, false><<<w.tiles, kBlock, 0, s>>>(Q);
+  }
+  LJ_CUDA(cudaGetLastError());
+  if (dup && counts && !words_in_counts)
+    LJ_CUDA(cudaMemcpyAsync(counts, words, m * 4, cudaMemcpyDeviceToDevice, s));
+  if (total_host) LJ_CUDA(cudaMemcpyAsync(total_host, w.total, 8, cudaMemcpyDeviceToHost, s));
+  LJ_CUDA(scratch_free(w.mem, s));
+  if (total_host) {
+    LJ_CUDA(cudaStreamSynchronize(s));
+    if (int rc = take_device_errors(idx->device, s)) return rc;
+  }
+  return 0;
+}
+
+template <class Model>
+int launch_probe(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
+                 lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
+                 uint64_t* total_dev, uint64_t* total_host, uint32_t s_base, cudaStream_t s) {
+  if (m <= g_single_pass_max)
+    return launch_single_pass(idx, model, mode, S, m, pairs, cap, counts, offsets, total_dev,
+                              total_host, s_base, s);
+  return launch_pipeline(idx, model, mode, S, m, pairs, cap, counts, offsets, total_dev,
+                         total_host, s_base, s);
+}
+
 template <class Model>
 int launch_emit(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
                 const uint64_t* offsets, lj_pair* pairs, uint64_t cap, uint32_t s_base,
                 cudaStream_t s) {
-  ProbeParams<Model> P{};
-  P.R = idx->R;
-  P.leaves = (const typename Model::Leaf*)idx->leaves;
-  P.model = model;
-  P.S = S;
-  P.m = m;
+  ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
+  if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   P.pairs = pairs;
   P.capacity = cap;
   P.offsets = const_cast<uint64_t*>(offsets);
-  P.s_base = s_base;
-  P.err = device_error_word(idx->device);
-  if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   const uint64_t blocks = (m + kBlock - 1) / kBlock;
   emit_kernel<Model><<<(unsigned)blocks, kBlock, 0, s>>>(P);
   LJ_CUDA(cudaGetLastError());
@@ -413,7 +728,7 @@ int check_common(const lj_index* idx, const uint64_t* S, uint64_t m, const char*
 
 }  // namespace
 
-// Shared with the chunked host join (same translation unit family).
+// Shared with the chunked host join.
 int probe_count_impl(const lj_index* idx, const uint64_t* S, uint64_t m, uint32_t* counts,
                      uint64_t* offsets, uint64_t* total_dev, uint64_t* total_host,
                      cudaStream_t s) {
@@ -447,6 +762,9 @@ int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const ui
   }
   return 0;
 }
+
+void set_single_pass_max(uint64_t v) { g_single_pass_max = v; }
+uint64_t get_single_pass_max() { return g_single_pass_max; }
 
 }  // namespace lj
 
@@ -493,4 +811,22 @@ extern "C" int join_emit(const lj_index* idx, const uint64_t* S_dev, uint64_t m,
     return fail(LJ_E_CAPACITY, "join_emit: %llu pairs do not fit the capacity of %llu",
                 (unsigned long long)*written_host, (unsigned long long)capacity);
   return LJ_OK;
+}
+
+extern "C" int lj_set_option(const char* name, int64_t value) {
+  using namespace lj;
+  if (!name) return fail(LJ_E_INVAL, "lj_set_option: name is NULL");
+  if (!strcmp(name, "single_pass_max")) {
+    if (value < 0) return fail(LJ_E_INVAL, "single_pass_max must be >= 0");
+    set_single_pass_max((uint64_t)value);
+    return LJ_OK;
+  }
+  return fail(LJ_E_INVAL, "lj_set_option: unknown option '%s'", name);
+}
+
+extern "C" int64_t lj_get_option(const char* name) {
+  using namespace lj;
+  if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
+  fail(LJ_E_INVAL, "lj_get_option: unknown option '%s'", name ? name : "(null)");
+  return -1;
 }

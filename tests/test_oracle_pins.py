@@ -277,6 +277,7 @@ def test_rmi_lookup_equals_sort_merge(fp64):
     S = np.concatenate([rng.choice(R, 3000),
                         rng.integers(0, int(R[-1]) * 2, 3000, dtype=np.uint64),
                         np.array([0, 1, int(R[0]) - 1, int(R[-1]) + 1, 2**64 - 1], np.uint64)])
+    assert S.dtype == np.uint64
     lo, hi, _ = oracle.join_ranges(R, S)
     for L in (1, 100, 4096):
         m = oracle.rmi_fit(R, L, fp64=fp64)

@@ -22,13 +22,24 @@ pytestmark = pytest.mark.gpu
 TOP = np.uint64(2**64 - 1)
 
 
+@pytest.fixture(params=["single_pass", "pipeline"], autouse=True)
+def probe_path(request):
+    """Run every test on both execution paths of the probe."""
+    import paper_2111_08824_gb300 as lj
+    old = lj.lj_get_option("single_pass_max")
+    lj.lj_set_option("single_pass_max", 1 << 40 if request.param == "single_pass" else 0)
+    yield request.param
+    lj.lj_set_option("single_pass_max", old)
+
+
 def _lj():
     import paper_2111_08824_gb300 as lj
     return lj
 
 
 def dev(a: np.ndarray):
-    a = np.ascontiguousarray(a, dtype=np.uint64)
+    assert a.dtype == np.uint64, a.dtype
+    a = np.ascontiguousarray(a)
     return torch.from_numpy(a.view(np.int64)).cuda()
 
 
@@ -99,8 +110,8 @@ def _relation(kind, rng, n):
         c = rng.integers(0, 2**62, 16, dtype=np.uint64)
         return np.unique(c[rng.integers(0, 16, n)] + rng.integers(0, 5000, n).astype(np.uint64))
     if kind == "extremes":
-        return np.unique(np.concatenate([rng.integers(0, 2**64 - 1, n, dtype=np.uint64,
-                                                      endpoint=True), [0, TOP]]).astype(np.uint64))
+        keys = rng.integers(0, 2**64 - 1, n, dtype=np.uint64, endpoint=True)
+        return np.unique(np.concatenate([keys, np.array([0, TOP], np.uint64)]))
     raise ValueError(kind)
 
 
@@ -159,9 +170,11 @@ def test_join_unique_parity(kind, path, prec):
 def test_join_duplicates_parity(prec):
     rng = np.random.default_rng(21)
     R = np.sort(np.concatenate([rng.integers(0, 5000, 40000, dtype=np.uint64),
-                                np.full(300, 777, np.uint64), [0, 0, TOP, TOP]]).astype(np.uint64))
+                                np.full(300, 777, np.uint64),
+                                np.array([0, 0, TOP, TOP], np.uint64)]))
     S = np.concatenate([R[rng.integers(0, R.size, 6000)],
-                        rng.integers(0, 6000, 4000, dtype=np.uint64), [TOP, 0, 777]])
+                        rng.integers(0, 6000, 4000, dtype=np.uint64),
+                        np.array([TOP, 0, 777], np.uint64)])
     for L in (1, 64, 5000, 100000):
         check_against_oracle(R, S, L, prec, "two_pass")
 
