@@ -142,6 +142,32 @@ int join_count(const lj_index* index, const uint64_t* S_dev, uint64_t m,
                lj_stream_t stream);
 
 /*
+ * join_count_noalloc -- join_count without any memory allocation.
+ *   The paper has no counterpart: this entry point exists for callers that
+ *   cannot allocate device memory at call time -- for example a real-time
+ *   serving loop whose latency budget forbids cudaMalloc and its implicit
+ *   device synchronisation, code running under another allocator that owns
+ *   all device memory, or a host that pre-plans every allocation up front.
+ *   Same arguments, results and errors as join_count, but the scratch memory
+ *   of its kernel (tile states of the single-pass scan, total, error word)
+ *   is a fixed array of about 320 KiB compiled into the library, which every
+ *   GPU that loads the library keeps until the process exits.  The call
+ *   itself allocates nothing: no cudaMalloc, no cudaFree, no memory pool.
+ *   Limits and rules:
+ *     - m must be at most 2^25 (33,554,432) probes, else LJ_E_INVAL;
+ *     - the first call on a device looks up the array's device address
+ *       (once per device); make that first call before any stream capture;
+ *     - every call on a device shares the one array: calls whose kernels can
+ *       overlap on the GPU (different streams without ordering, several host
+ *       threads) race and give wrong results; order them on one stream.
+ *   The array keeps the last call's contents; each call clears what must
+ *   start at zero (ticket, tile flags, error word) on `stream`.
+ */
+int join_count_noalloc(const lj_index* index, const uint64_t* S_dev, uint64_t m,
+                       uint32_t* counts_dev, uint64_t* offsets_dev, uint64_t* total_host,
+                       lj_stream_t stream);
+
+/*
  * join_emit -- write the join pairs (Section 2.A; Section 6.B).
  *   offsets_dev   m+1 offsets from join_count (two-pass path), or NULL for
  *                 the direct path, which needs an index whose R has no

@@ -49,6 +49,7 @@ SIGNATURES = {
     "rmi_stats": ([_P, _P], _I),
     "rmi_export": ([_P, _P, _P, _P, _P], _I),
     "join_count": ([_P, _P, _U64, _P, _P, _P, _P], _I),
+    "join_count_noalloc": ([_P, _P, _U64, _P, _P, _P, _P], _I),
     "join_emit": ([_P, _P, _U64, _P, _P, _U64, _P, _P, _P], _I),
     "join_host": ([_P, _P, _U64, _P, _U64, _P, _P], _I),
     "lj_set_option": ([ctypes.c_char_p, ctypes.c_int64], _I),
@@ -169,6 +170,18 @@ def join_count(index: Index, S, counts=None, offsets=None, want_total: bool = Tr
     _check(load().join_count(index.handle, _ptr(S), S.numel(), _ptr(counts), _ptr(offsets),
                              ctypes.byref(total) if want_total else None,
                              _stream_ptr(stream)))
+    return total.value if want_total else None
+
+
+def join_count_noalloc(index: Index, S, counts=None, offsets=None, want_total: bool = True,
+                       stream=None) -> int | None:
+    """join_count without any allocation (fixed scratch in the library; at
+    most 2^25 probes per call; calls that overlap on the GPU race)."""
+    _require_cuda_u64(S, "S")
+    total = ctypes.c_uint64()
+    _check(load().join_count_noalloc(index.handle, _ptr(S), S.numel(), _ptr(counts),
+                                     _ptr(offsets), ctypes.byref(total) if want_total else None,
+                                     _stream_ptr(stream)))
     return total.value if want_total else None
 
 

@@ -27,6 +27,7 @@
 //     output range of its 32 probes with coalesced 8-byte stores.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -829,4 +830,113 @@ extern "C" int64_t lj_get_option(const char* name) {
   if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
   fail(LJ_E_INVAL, "lj_get_option: unknown option '%s'", name ? name : "(null)");
   return -1;
+}
+
+// ---------------------------------------------------------------------------
+// join_count_noalloc: join_count for callers that must not allocate.
+//
+// The single-pass count kernel needs scratch memory for its tile states (a
+// ticket, one flag and two 64-bit values per tile, the total and an error
+// word).  Here that scratch is one file-scope device array of fixed size, so
+// the call allocates nothing: no cudaMalloc / cudaFree, no memory pool, no
+// library allocator.  Its size fixes the largest batch: kNoAllocMaxProbes.
+// Every call on a device shares the array and leaves its last contents in
+// it; the ticket, the flags and the error word are cleared at the start of
+// each call, on the caller's stream.
+namespace lj {
+namespace {
+constexpr uint64_t kNoAllocMaxProbes = 1ull << 25;   // 33,554,432 probes per call
+constexpr uint64_t kNoAllocTile = (uint64_t)kBlock * 2 * kRounds;
+constexpr uint32_t kNoAllocTiles = (uint32_t)((kNoAllocMaxProbes + kNoAllocTile - 1) / kNoAllocTile);
+constexpr size_t kNoAllocFlagBytes = ((size_t)kNoAllocTiles * 4 + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = 256 + kNoAllocFlagBytes + (size_t)kNoAllocTiles * 16;
+
+// header: [0] ticket (u32), [64] total (u64), [128] error word (u32);
+// then the tile flags, then the aggregates and the inclusive prefixes.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of the array on the current device.  The host-side name of
+// a __device__ variable is not a device address, so it is looked up once per
+// device with cudaGetSymbolAddress while that device is current.
+int noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 64) return fail(LJ_E_INVAL, "join_count_noalloc: device %d unsupported", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail_cuda(e, "join_count_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (unsigned char*)g_noalloc_ptr[dev];
+  return 0;
+}
+
+template <class Model>
+int noalloc_count(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
+                  uint32_t* counts, uint64_t* offsets, uint64_t* total_host, cudaStream_t s) {
+  unsigned char* b = nullptr;
+  if (int rc = noalloc_scratch(idx->device, &b)) return rc;
+  const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, (m + kNoAllocTile - 1) / kNoAllocTile);
+  LJ_CUDA(cudaMemsetAsync(b, 0, 256 + ((size_t)tiles * 4 + 255) / 256 * 256, s));
+  ProbeParams<Model> P{};
+  P.R = idx->R;
+  P.leaves = (const typename Model::Leaf*)idx->leaves;
+  P.model = model;
+  P.S = S;
+  P.m = m;
+  P.counts = counts;
+  P.offsets = offsets;
+  P.total_ws = (uint64_t*)(b + 64);
+  P.err = (uint32_t*)(b + 128);
+  P.st.ticket = (uint32_t*)b;
+  P.st.flag = (uint32_t*)(b + 256);
+  P.st.agg = (uint64_t*)(b + 256 + kNoAllocFlagBytes);
+  P.st.incl = P.st.agg + kNoAllocTiles;
+  P.num_tiles = tiles;
+  const bool vec = aligned(S, 16) && (!offsets || aligned(offsets, 16)) && (!counts || aligned(counts, 8));
+  if (idx->unique)
+    vec ? probe_single_pass_kernel<Model, kUniqueCount, kRounds, true><<<tiles, kBlock, 0, s>>>(P)
+        : probe_single_pass_kernel<Model, kUniqueCount, kRounds, false><<<tiles, kBlock, 0, s>>>(P);
+  else
+    vec ? probe_single_pass_kernel<Model, kDupCount, kRounds, true><<<tiles, kBlock, 0, s>>>(P)
+        : probe_single_pass_kernel<Model, kDupCount, kRounds, false><<<tiles, kBlock, 0, s>>>(P);
+  LJ_CUDA(cudaGetLastError());
+  if (total_host) {
+    uint32_t err = 0;
+    LJ_CUDA(cudaMemcpyAsync(total_host, P.total_ws, 8, cudaMemcpyDeviceToHost, s));
+    LJ_CUDA(cudaMemcpyAsync(&err, P.err, 4, cudaMemcpyDeviceToHost, s));
+    LJ_CUDA(cudaStreamSynchronize(s));
+    if (err & kErrLookbackTimeout)
+      return fail(LJ_E_TIMEOUT, "join_count_noalloc: a device-side look-back wait ran out");
+  }
+  return 0;
+}
+}  // namespace
+}  // namespace lj
+
+extern "C" int join_count_noalloc(const lj_index* idx, const uint64_t* S_dev, uint64_t m,
+                                  uint32_t* counts_dev, uint64_t* offsets_dev,
+                                  uint64_t* total_host, lj_stream_t stream) {
+  using namespace lj;
+  if (int rc = check_common(idx, S_dev, m, "join_count_noalloc")) return rc;
+  if (m > kNoAllocMaxProbes)
+    return fail(LJ_E_INVAL,
+                "join_count_noalloc: m = %llu exceeds the limit of %llu probes per call set by "
+                "its fixed scratch array; split the batch or use join_count",
+                (unsigned long long)m, (unsigned long long)kNoAllocMaxProbes);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m == 0) {
+    if (offsets_dev) LJ_CUDA(cudaMemsetAsync(offsets_dev, 0, 8, s));
+    if (total_host) {
+      *total_host = 0;
+      LJ_CUDA(cudaStreamSynchronize(s));
+    }
+    return LJ_OK;
+  }
+  if (idx->precision == LJ_FP64)
+    return noalloc_count(idx, f64_model(idx), S_dev, m, counts_dev, offsets_dev, total_host, s);
+  return noalloc_count(idx, f32_model(idx), S_dev, m, counts_dev, offsets_dev, total_host, s);
 }
