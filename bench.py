@@ -163,6 +163,25 @@ def _config(args, wl):
                 wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
 
 
+def _ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2111_08824_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    if d.get("csrc_sha256") != h.hexdigest():
+        return None
+    return d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch")
+
+
 def cpu_baseline(wl, sample: int) -> dict:
     import oracle
     oracle.build()
@@ -245,22 +264,21 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    lj.lj_profile_report()                       # drop earlier records
+    lj.lj_set_option("profile", 1)               # per-kernel events on the launch stream
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for i in range(args.steps):
-        ev[i][0].record(stream)
+    for _ in range(args.steps):
         step()
-        ev[i][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
+    lj.lj_set_option("profile", 0)
+    kernels = lj.lj_profile_report()
     if dist:
         dist.barrier()
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    per_launch = [a.elapsed_time(b) for a, b in ev]
     if dist:
         t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -268,7 +286,8 @@ def main():
     ms_per_step = elapsed_ms / args.steps
     value = world * m / (ms_per_step / 1e3)
 
-    # ---- end to end through the C ABI with host buffers (pinned)
+    # ---- end to end through the C ABI with host buffers (pinned): S is read
+    # in place by the GPU, pairs are copied out while the next chunk is probed
     S_host = torch.from_numpy(wl.S.view(np.int64)).pin_memory()
     P_host = torch.empty((max(total, 1), 2), dtype=torch.int32).pin_memory()
     S_np = S_host.numpy().view(np.uint64)
@@ -283,11 +302,19 @@ def main():
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         assert got == total
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (algorithmic bytes per launch)
     peak, peak_kind = _peaks()
-    alg_bytes = 8 * m + 8 * n + 8 * total + 32 * L
-    launch_ms = statistics.mean(per_launch) / launches_per_step if unique else statistics.mean(per_launch)
-    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    alg = {
+        "probe_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,   # S, R once, leaves, 4-B result
+        "scan_kernel": 4 * m + (8 * total if unique else 8 * (m + 1)),
+        "probe_single_pass_kernel": 8 * m + 8 * n + 32 * L + 8 * total,
+        "emit_kernel": 8 * m + 8 * n + 32 * L + 8 * (m + 1) + 8 * total,
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    dom_ms = kernels[dom]["total_ms"] / kernels[dom]["launches"]
+    achieved = alg[dom] / (dom_ms / 1e3) / 1e9
+    pass_bytes = 8 * m + 8 * n + 8 * total + 32 * L
+    traffic = _ncu_traffic(dom)
     line = {
         "metric": "probe_keys_per_s", "value": value, "unit": "keys/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -299,14 +326,18 @@ def main():
         "build_ms": st["build_ms"], "mean_window": st["mean_window"],
         "max_window": st["max_window"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_kind": peak_kind,
-                     "kernel": "probe_tile_kernel" if unique else "probe_tile_kernel+emit_kernel",
-                     "alg_bytes_per_launch": alg_bytes},
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind + " copy bandwidth (hbm_gbs)",
+                     "kernel": dom, "alg_bytes_per_launch": alg[dom],
+                     "launch_ms": dom_ms},
+        "roofline_pass": {"alg_bytes": pass_bytes, "achieved": pass_bytes / (ms_per_step / 1e3) / 1e9,
+                          "frac": pass_bytes / (ms_per_step / 1e3) / 1e9 / peak},
+        "kernels": kernels,
         "e2e": None if e2e_s is None else {
             "value": world * m / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": 8 * m,
-            "d2h_bytes_per_step": 8 * total},
-        "gpu_launches": launches_per_step * args.steps,
+            "d2h_bytes_per_step": 8 * total,
+            "note": "S pinned on the host and read in place over NVLink-C2C; pairs copied out"},
+        "gpu_launches": sum(k["launches"] for k in kernels.values()),
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

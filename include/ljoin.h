@@ -207,11 +207,24 @@ int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
  *                      launch); larger ones use the count-scan-emit pipeline
  *                      (search kernel, then a streaming scan).  Default 2^20.
  *                      Both paths give identical results.
+ *   "profile"          1: record CUDA events around every kernel the library
+ *                      launches (on the launch's stream); lj_profile_report
+ *                      returns the per-kernel totals.  0 (default): off.
  * lj_set_option returns LJ_OK or LJ_E_INVAL (unknown name, bad value);
  * lj_get_option returns the value, or -1 for an unknown name.
  */
 int lj_set_option(const char* name, int64_t value);
 int64_t lj_get_option(const char* name);
+
+/*
+ * lj_profile_report -- per-kernel timings recorded since the last report
+ * (with the "profile" option on), as JSON
+ *   {"<kernel>": {"launches": N, "total_ms": T, "min_ms": a, "max_ms": b}, ...}
+ * written NUL-terminated into buf (len bytes).  Waits for the recorded events;
+ * clears the records.  Returns the string length, or LJ_E_INVAL if buf is too
+ * small (the records are then lost), LJ_E_CUDA if an event failed.
+ */
+int lj_profile_report(char* buf, size_t len);
 
 /* Thread-local message describing the last error of this thread. */
 const char* lj_last_error(void);

@@ -10,11 +10,13 @@ use; there is no CPU fallback.
 """
 from ._native import (LJ_FP32, LJ_FP64, Index, LJoinError, join_count, join_count_noalloc,
                       join_emit, join_host,
-                      library_path, lj_get_option, lj_last_error, lj_set_option,
+                      library_path, lj_get_option, lj_last_error, lj_profile_report,
+                      lj_set_option,
                       lj_version, load, rmi_build, rmi_export,
                       rmi_free, rmi_stats)
 
 __all__ = ["LJ_FP32", "LJ_FP64", "Index", "LJoinError", "join_count", "join_count_noalloc",
            "join_emit", "join_host",
-           "library_path", "lj_get_option", "lj_last_error", "lj_set_option", "lj_version", "load", "rmi_build", "rmi_export",
+           "library_path", "lj_get_option", "lj_last_error", "lj_profile_report",
+           "lj_set_option", "lj_version", "load", "rmi_build", "rmi_export",
            "rmi_free", "rmi_stats"]

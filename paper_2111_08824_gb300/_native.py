@@ -54,6 +54,7 @@ SIGNATURES = {
     "join_host": ([_P, _P, _U64, _P, _U64, _P, _P], _I),
     "lj_set_option": ([ctypes.c_char_p, ctypes.c_int64], _I),
     "lj_get_option": ([ctypes.c_char_p], ctypes.c_int64),
+    "lj_profile_report": ([ctypes.c_char_p, ctypes.c_size_t], _I),
     "lj_last_error": ([], ctypes.c_char_p),
     "lj_version": ([], ctypes.c_char_p),
 }
@@ -218,6 +219,16 @@ def lj_get_option(name: str) -> int:
     if v == -1:
         raise LJoinError(-1, lj_last_error())
     return v
+
+
+def lj_profile_report() -> dict:
+    """Per-kernel timings recorded with the "profile" option on (and clear them)."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    n = load().lj_profile_report(buf, len(buf))
+    if n < 0:
+        raise LJoinError(n, lj_last_error())
+    return json.loads(buf.value.decode())
 
 
 def lj_last_error() -> str:

@@ -1,7 +1,10 @@
 // Error reporting, scratch memory, and the host-only index entry points.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "device_common.cuh"
@@ -94,9 +97,107 @@ int take_device_errors(int dev, cudaStream_t s) {
   return 0;
 }
 
+namespace {
+std::atomic<bool> g_profile{false};
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof;
+}  // namespace
+
+void set_profiling(bool on) { g_profile.store(on); }
+bool profiling() { return g_profile.load(std::memory_order_relaxed); }
+
+KernelTimer::KernelTimer(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  if (!profiling()) return;
+  if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
+    if (a_) cudaEventDestroy(a_);
+    a_ = b_ = nullptr;
+    return;
+  }
+  cudaEventRecord(a_, s_);
+}
+
+KernelTimer::~KernelTimer() {
+  if (!a_) return;
+  cudaEventRecord(b_, s_);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back({name_, a_, b_});
+}
+
 }  // namespace lj
 
 extern "C" {
+
+int lj_set_option(const char* name, int64_t value) {
+  using namespace lj;
+  if (!name) return fail(LJ_E_INVAL, "lj_set_option: name is NULL");
+  if (!strcmp(name, "single_pass_max")) {
+    if (value < 0) return fail(LJ_E_INVAL, "single_pass_max must be >= 0");
+    set_single_pass_max((uint64_t)value);
+    return LJ_OK;
+  }
+  if (!strcmp(name, "profile")) {
+    set_profiling(value != 0);
+    return LJ_OK;
+  }
+  return fail(LJ_E_INVAL, "lj_set_option: unknown option '%s'", name);
+}
+
+int64_t lj_get_option(const char* name) {
+  using namespace lj;
+  if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
+  if (name && !strcmp(name, "profile")) return profiling() ? 1 : 0;
+  fail(LJ_E_INVAL, "lj_get_option: unknown option '%s'", name ? name : "(null)");
+  return -1;
+}
+
+int lj_profile_report(char* buf, size_t len) {
+  using namespace lj;
+  std::vector<ProfRec> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    recs.swap(g_prof);
+  }
+  struct Agg {
+    uint64_t n = 0;
+    double total = 0, mn = 1e300, mx = 0;
+  };
+  std::map<std::string, Agg> agg;
+  int rc = 0;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      Agg& a = agg[r.name];
+      a.n++;
+      a.total += ms;
+      a.mn = ms < a.mn ? ms : a.mn;
+      a.mx = ms > a.mx ? ms : a.mx;
+    } else {
+      rc = LJ_E_CUDA;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : agg) {
+    char tmp[256];
+    snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %llu, \"total_ms\": %.6f, \"min_ms\": %.6f, \"max_ms\": %.6f}",
+             first ? "" : ", ", kv.first.c_str(), (unsigned long long)kv.second.n, kv.second.total,
+             kv.second.mn, kv.second.mx);
+    out += tmp;
+    first = false;
+  }
+  out += "}";
+  if (rc) return fail(rc, "lj_profile_report: an event could not be read");
+  if (!buf || len <= out.size()) return fail(LJ_E_INVAL, "lj_profile_report: buffer of %zu bytes too small (%zu needed)", len, out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return (int)out.size();
+}
+
 
 const char* lj_last_error(void) { return lj::g_err; }
 

@@ -1,10 +1,13 @@
 // join_host: the whole join from host buffers, pipelined in chunks.
 //
-// Unique R (single-pass path): two device buffers for S chunks and two for
-// pair chunks.  While chunk c is probed on the caller's stream, chunk c+1 is
-// copied in on a copy stream and chunk c-1's pairs are copied out on another,
-// so host<->device transfers overlap the lookups.  The host waits only for
-// each chunk's pair count (8 bytes) before issuing its copy-out.
+// Unique R: two device buffers for pair chunks (and, unless S can be read in
+// place, two for S chunks).  While chunk c is probed on the caller's stream,
+// chunk c+1 is copied in on a copy stream and chunk c-1's pairs are copied
+// out on another, so host<->device transfers overlap the lookups.  The host
+// waits only for each chunk's pair count (8 bytes) before its copy-out.
+// When S is page-locked host memory the GPU reads it in place (over
+// NVLink-C2C on Grace-Blackwell, at a cost the latency-bound lookups hide) and
+// no copy-in is issued.
 // R with duplicates: per chunk, count (offsets) -> emit -> copy out.
 #include <algorithm>
 #include <vector>
@@ -61,6 +64,15 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
   const uint64_t chunk = std::min<uint64_t>(m, kHostChunk);
   const uint64_t nchunks = (m + chunk - 1) / chunk;
   uint64_t written = 0;
+  // page-locked (or registered) S can be read by the kernels in place
+  const uint64_t* S_mapped = nullptr;
+  {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, S_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer)
+      S_mapped = (const uint64_t*)at.devicePointer;
+    cudaGetLastError();   // clear a possible "not a CUDA pointer" error
+  }
 
   if (idx->unique) {
     char* ws = nullptr;
@@ -69,19 +81,25 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
     uint64_t* Sd[2] = {(uint64_t*)ws, (uint64_t*)(ws + chunk * 8)};
     lj_pair* Pd[2] = {(lj_pair*)(ws + 2 * chunk * 8), (lj_pair*)(ws + 3 * chunk * 8)};
     uint64_t* tot_d = (uint64_t*)(ws + 4 * chunk * 8);
-    uint64_t* tot_h = nullptr;
-    LJ_CUDA(cudaMallocHost(&tot_h, 2 * sizeof(uint64_t)));
+    // two page-locked counters per host thread, allocated on first use
+    static thread_local uint64_t* tot_h = nullptr;
+    if (!tot_h) LJ_CUDA(cudaMallocHost(&tot_h, 2 * sizeof(uint64_t)));
     int rc = 0;
     auto issue = [&](uint64_t c) -> int {
       const int b = (int)(c & 1);
       const uint64_t off = c * chunk, len = std::min(chunk, m - off);
-      // S buffer b was last read by compute(c-2)
-      LJ_CUDA(cudaStreamWaitEvent(st.in, comp_done[b], 0));
-      LJ_CUDA(cudaMemcpyAsync(Sd[b], S_host + off, len * 8, cudaMemcpyHostToDevice, st.in));
-      LJ_CUDA(cudaEventRecord(in_done[b], st.in));
-      LJ_CUDA(cudaStreamWaitEvent(s, in_done[b], 0));
+      const uint64_t* Sc = Sd[b];
+      if (S_mapped) {
+        Sc = S_mapped + off;
+      } else {
+        // S buffer b was last read by compute(c-2)
+        LJ_CUDA(cudaStreamWaitEvent(st.in, comp_done[b], 0));
+        LJ_CUDA(cudaMemcpyAsync(Sd[b], S_host + off, len * 8, cudaMemcpyHostToDevice, st.in));
+        LJ_CUDA(cudaEventRecord(in_done[b], st.in));
+        LJ_CUDA(cudaStreamWaitEvent(s, in_done[b], 0));
+      }
       LJ_CUDA(cudaStreamWaitEvent(s, out_done[b], 0));   // pair buffer b drained
-      if (int r = probe_emit_impl(idx, Sd[b], len, nullptr, Pd[b], len, tot_d + b, nullptr,
+      if (int r = probe_emit_impl(idx, Sc, len, nullptr, Pd[b], len, tot_d + b, nullptr,
                                   (uint32_t)off, s))
         return r;
       LJ_CUDA(cudaMemcpyAsync(tot_h + b, tot_d + b, 8, cudaMemcpyDeviceToHost, s));
@@ -107,7 +125,6 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
     }
     cudaStreamSynchronize(st.out);
     cudaStreamSynchronize(s);
-    cudaFreeHost(tot_h);
     scratch_free(ws, s);
     cudaStreamSynchronize(s);
     if (rc) return rc;
@@ -119,12 +136,16 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
     int rc = 0;
     for (uint64_t c = 0; c < nchunks && !rc; ++c) {
       const uint64_t off = c * chunk, len = std::min(chunk, m - off);
-      if (cudaMemcpyAsync(Sd, S_host + off, len * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      const uint64_t* Sc = Sd;
+      if (S_mapped) {
+        Sc = S_mapped + off;
+      } else if (cudaMemcpyAsync(Sd, S_host + off, len * 8, cudaMemcpyHostToDevice, s) !=
+                 cudaSuccess) {
         rc = fail(LJ_E_CUDA, "join_host: copy-in failed");
         break;
       }
       uint64_t cnt = 0;
-      if ((rc = probe_count_impl(idx, Sd, len, nullptr, off_d, nullptr, &cnt, s))) break;
+      if ((rc = probe_count_impl(idx, Sc, len, nullptr, off_d, nullptr, &cnt, s))) break;
       const uint64_t room = capacity > written ? capacity - written : 0;
       const uint64_t take = std::min(cnt, room);
       if (take) {
@@ -133,7 +154,7 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
           rc = fail(LJ_E_NOMEM, "join_host: no room for %llu pairs", (unsigned long long)take);
           break;
         }
-        if ((rc = probe_emit_impl(idx, Sd, len, off_d, Pd, take, nullptr, nullptr, (uint32_t)off,
+        if ((rc = probe_emit_impl(idx, Sc, len, off_d, Pd, take, nullptr, nullptr, (uint32_t)off,
                                   s)))
           break;
         cudaMemcpyAsync(pairs_host + written, Pd, take * 8, cudaMemcpyDeviceToHost, s);

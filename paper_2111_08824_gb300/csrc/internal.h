@@ -48,6 +48,24 @@ int take_device_errors(int device, cudaStream_t s);
 
 int current_device();
 
+// Opt-in per-kernel timing (lj_set_option("profile", 1)): CUDA events are
+// recorded around each launch on its own stream; lj_profile_report
+// aggregates them.  Costs nothing when profiling is off.
+class KernelTimer {
+ public:
+  KernelTimer(const char* name, cudaStream_t s);
+  ~KernelTimer();
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+void set_profiling(bool on);
+bool profiling();
+
 // Probe batches of at most this many keys take the single-pass kernel.
 void set_single_pass_max(uint64_t v);
 uint64_t get_single_pass_max();

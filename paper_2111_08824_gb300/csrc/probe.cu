@@ -15,9 +15,11 @@
 //     probe_search_kernel: lookups only, one 32-bit word per probe (first
 //       match or "none" for a unique R, the match count otherwise); no scan
 //       and no barrier, so a warp never waits for a slower one.
-//     scan_kernel: streaming scan of those words in uniform tiles (short
-//       look-back waits), output staged in shared memory and written with
-//       coalesced stores (pairs, or offsets / counts).
+//       Each warp also adds its probes' match count to its tile's count.
+//     tile_scan_kernel: exclusive scan of the per-tile counts.
+//     compact_kernel: every tile scans its words, stages its output in shared
+//       memory and writes it with coalesced stores (pairs, or offsets and
+//       counts); tiles know their offsets up front, so none waits.
 //   Measured on the 100M x 400M lognormal workload, the single-pass kernel
 //   spent almost half its time waiting in the look-back for tiles whose
 //   searches were slower; the pipeline's extra 8 bytes per probe of
@@ -82,6 +84,8 @@ constexpr int kSearchRounds = LJ_SROUNDS;
 constexpr int kSearchBlock = LJ_SBLOCK;
 constexpr uint32_t kNoMatch = 0xFFFFFFFFu;
 enum { kScanPairs = 0, kScanOffsets = 1 };
+constexpr int kScanItems = 16;
+constexpr uint64_t kCompactTile = 256ull * kScanItems;   // probes per compaction tile
 // probe batches up to this size take the single-pass kernel (one launch)
 uint64_t g_single_pass_max = 1ull << 20;
 
@@ -387,9 +391,14 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
 // for one another:
 //   kUniqueCount  out[j] = first matching position, or kNoMatch
 //   kDupCount     out[j] = number of matches
+// Each block also adds its probes' match count to the count of their
+// compaction tile (kCompactTile probes; a block's probes never straddle two).
 template <class Model, int MODE, int K, bool VEC>
 __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
-    probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out) {
+    probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
+                        unsigned long long* __restrict__ tile_counts) {
+  static_assert(kCompactTile % (2 * kSearchBlock) == 0, "a block's probes must share a tile");
+  __shared__ unsigned long long s_count[kSearchBlock / 32];
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t T = gridDim.x * (uint64_t)blockDim.x;
   uint32_t r_idx[2 * K], cnt[2 * K];
@@ -412,16 +421,89 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
       if (valid[2 * k]) out[j0] = w0;
       if (valid[2 * k + 1]) out[j0 + 1] = w1;
     }
+    // the block's 2*blockDim probes of this round lie in one compaction tile:
+    // one atomic per block and round (per-warp atomics contended badly)
+    unsigned long long c = (unsigned long long)cnt[2 * k] + cnt[2 * k + 1];
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    if ((threadIdx.x & 31) == 0) s_count[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tot = 0;
+#pragma unroll
+      for (int w = 0; w < kSearchBlock / 32; ++w) tot += s_count[w];
+      if (tot) atomicAdd(tile_counts + j0 / kCompactTile, tot);
+    }
+    __syncthreads();
   }
 }
 
-// Scan kernel of the pipeline: tiles of 256 threads x 16 words.  Each tile
-// counts its words (kFromMatches: word != kNoMatch; kFromCounts: the word),
-// scans them in the block, takes its offset by decoupled look-back (tiles are
-// uniform, so waits are short), stages its output in shared memory and writes
-// it with coalesced stores:
+// Exclusive scan of the per-tile counts: blocks of 256 threads x 16 counts
+// with a decoupled look-back between blocks (a few hundred at most).
+// prefix[t] = first output position of tile t, prefix[tiles] = |J|; the last
+// block also publishes the total.
+constexpr int kTileScanItems = 16;
+constexpr uint32_t kTileScanSpan = kBlock * kTileScanItems;
+
+__global__ void __launch_bounds__(kBlock) tile_scan_kernel(const unsigned long long* counts,
+                                                           uint32_t tiles, uint64_t* prefix,
+                                                           TileState st, uint32_t blocks,
+                                                           uint64_t* total_ws, uint64_t* total_out,
+                                                           uint64_t* offsets_end, uint64_t capacity,
+                                                           uint32_t* err) {
+  __shared__ uint32_t s_blk;
+  __shared__ uint64_t s_warp[kWarps];
+  __shared__ uint64_t s_prefix;
+  if (threadIdx.x == 0) s_blk = atomicAdd(st.ticket, 1u);
+  __syncthreads();
+  const uint32_t blk = s_blk;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t base = (uint64_t)blk * kTileScanSpan + (uint64_t)threadIdx.x * kTileScanItems;
+  uint64_t v[kTileScanItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kTileScanItems; ++i) {
+    v[i] = base + i < tiles ? counts[base + i] : 0;
+    sum += v[i];
+  }
+  const uint64_t inc = warp_inclusive_sum(sum, lane);
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint64_t x = lane < kWarps ? s_warp[lane] : 0;
+    const uint64_t xi = warp_inclusive_sum(x, lane);
+    if (lane < kWarps) s_warp[lane] = xi - x;
+    const uint64_t agg = __shfl_sync(0xffffffffu, xi, 31);
+    const uint64_t pre = lookback_warp(st, blk, agg, err);
+    if (lane == 0) {
+      s_prefix = pre;
+      if (blk + 1 == blocks) {
+        const uint64_t total = pre + agg;
+        prefix[tiles] = total;
+        *total_ws = total;
+        if (total_out) *total_out = total;
+        if (offsets_end) *offsets_end = total;
+        if (total > capacity) atomicOr(err, kErrCapacity);
+      }
+    }
+  }
+  __syncthreads();
+  uint64_t run = s_prefix + s_warp[w] + inc - sum;
+#pragma unroll
+  for (int i = 0; i < kTileScanItems; ++i) {
+    if (base + i < tiles) prefix[base + i] = run;
+    run += v[i];
+  }
+}
+
+// Compaction kernel of the pipeline: tiles of 256 threads x 16 words
+// (kCompactTile probes).  Each tile already knows its first output position
+// (tile_scan_kernel), so tiles never wait for one another: load the words,
+// scan them in the block, stage the output in shared memory and write it
+// with coalesced stores:
 //   kScanPairs     (r_idx, s_idx) pairs of the matching probes
 //   kScanOffsets   offsets[j] (u64, exclusive) and optionally counts[j]
+// (FROM_COUNTS: the word is a match count; else a position or kNoMatch).
 struct ScanParams {
   const uint32_t* in;
   uint64_t m;
@@ -430,29 +512,19 @@ struct ScanParams {
   uint64_t capacity;
   uint64_t* offsets;
   uint32_t* counts;       // kScanOffsets from matches: optional 0/1 counts
-  uint64_t* total_ws;
-  uint64_t* total_out;
-  TileState st;
-  uint32_t* err;
-  uint32_t num_tiles;
+  const uint64_t* tile_prefix;
 };
 
-constexpr int kScanItems = 16;
-constexpr uint64_t kScanTile = (uint64_t)kBlock * kScanItems;
-
 template <int MODE, bool FROM_COUNTS, bool VEC>
-__global__ void __launch_bounds__(kBlock) scan_kernel(ScanParams P) {
-  __shared__ uint32_t s_tile;
+__global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
   __shared__ uint64_t s_warp[kWarps];
-  __shared__ uint64_t s_prefix;
-  __shared__ uint64_t s_stage[kScanTile];   // 32 KB
+  __shared__ uint64_t s_stage[kCompactTile];   // 32 KB
   __shared__ uint64_t s_count;
-  if (threadIdx.x == 0) s_tile = atomicAdd(P.st.ticket, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
+  const uint32_t tile = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t tile_base = (uint64_t)tile * kScanTile;
+  const uint64_t tile_base = (uint64_t)tile * kCompactTile;
   const uint64_t base = tile_base + (uint64_t)threadIdx.x * kScanItems;
+  const uint64_t prefix = P.tile_prefix[tile];
   uint32_t v[kScanItems];
   if (VEC && base + kScanItems <= P.m) {
 #pragma unroll
@@ -478,22 +550,9 @@ __global__ void __launch_bounds__(kBlock) scan_kernel(ScanParams P) {
     const uint64_t x = lane < kWarps ? s_warp[lane] : 0;
     const uint64_t xi = warp_inclusive_sum(x, lane);
     if (lane < kWarps) s_warp[lane] = xi - x;
-    const uint64_t agg = __shfl_sync(0xffffffffu, xi, 31);
-    const uint64_t pre = lookback_warp(P.st, tile, agg, P.err);
-    if (lane == 0) {
-      s_prefix = pre;
-      if (tile + 1 == P.num_tiles) {
-        const uint64_t total = pre + agg;
-        *P.total_ws = total;
-        if (P.total_out) *P.total_out = total;
-        if (P.offsets) P.offsets[P.m] = total;
-        if (MODE == kScanPairs && total > P.capacity) atomicOr(P.err, kErrCapacity);
-      }
-    }
   }
   __syncthreads();
-  const uint64_t prefix = s_prefix;
-  uint64_t local = s_warp[warp] + inc - sum;   // offset of this thread's first item in the tile
+  uint64_t local = s_warp[warp] + inc - sum;   // tile offset of this thread's first item
   if (MODE == kScanPairs) {
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i)
@@ -532,7 +591,7 @@ __global__ void __launch_bounds__(kBlock) scan_kernel(ScanParams P) {
     }
     if (P.offsets) {
       __syncthreads();
-      const uint64_t len = P.m - tile_base < kScanTile ? P.m - tile_base : kScanTile;
+      const uint64_t len = P.m - tile_base < kCompactTile ? P.m - tile_base : kCompactTile;
       for (uint64_t q = threadIdx.x; q < len; q += kBlock) P.offsets[tile_base + q] = s_stage[q];
     }
   }
@@ -601,6 +660,7 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
   P.st = w.st;
   P.num_tiles = w.tiles;
   const bool vec = aligned(S, 16) && (!offsets || aligned(offsets, 16)) && (!counts || aligned(counts, 8));
+  KernelTimer kt("probe_single_pass_kernel", s);
 #define LJ_LAUNCH(MODE)                                                                     \
   (vec ? probe_single_pass_kernel<Model, MODE, kRounds, true><<<w.tiles, kBlock, 0, s>>>(P) \
        : probe_single_pass_kernel<Model, MODE, kRounds, false><<<w.tiles, kBlock, 0, s>>>(P))
@@ -621,7 +681,8 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
   return 0;
 }
 
-// Count-scan-emit path: search kernel -> per-probe words -> scan kernel.
+// Count-scan-emit path: search kernel (per-probe words + per-tile counts)
+// -> tile_scan_kernel (tile prefixes, total) -> compact_kernel.
 template <class Model>
 int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
                     lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
@@ -629,22 +690,50 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   const bool dup = mode == kDupCount;
   // duplicates: the search writes counts, into the caller's buffer if given
   const bool words_in_counts = dup && counts && aligned(counts, 16);
-  Workspace w;
-  if (int rc = ws_acquire(w, (uint32_t)((m + kScanTile - 1) / kScanTile),
-                          words_in_counts ? 0 : ((m + 3) & ~3ull), s))
-    return rc;
-  uint32_t* words = words_in_counts ? counts : w.words;
+  const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, (m + kCompactTile - 1) / kCompactTile);
+  const size_t b_cnt = ((size_t)tiles * 8 + 255) / 256 * 256;
+  const size_t b_pre = ((size_t)(tiles + 1) * 8 + 255) / 256 * 256;
+  const size_t b_words = words_in_counts ? 0 : ((m + 3) & ~3ull) * 4;
+  const uint32_t scan_blocks = (tiles + kTileScanSpan - 1) / kTileScanSpan;
+  const size_t b_flags = ((size_t)scan_blocks * 4 + 255) / 256 * 256;
+  const size_t b_states = ((size_t)scan_blocks * 16 + 255) / 256 * 256;
+  // layout: header | tile counts | scan flags | (zeroed so far) scan states |
+  //         tile prefixes | words
+  char* ws = nullptr;
+  LJ_CUDA(scratch_alloc((void**)&ws, 256 + b_cnt + b_flags + b_states + b_pre + b_words, s));
+  LJ_CUDA(cudaMemsetAsync(ws, 0, 256 + b_cnt + b_flags, s));
+  uint64_t* total_ws = (uint64_t*)(ws + 64);
+  unsigned long long* tile_counts = (unsigned long long*)(ws + 256);
+  TileState st;
+  st.ticket = (uint32_t*)(ws + 128);
+  st.flag = (uint32_t*)(ws + 256 + b_cnt);
+  st.agg = (uint64_t*)(ws + 256 + b_cnt + b_flags);
+  st.incl = st.agg + scan_blocks;
+  uint64_t* tile_prefix = (uint64_t*)(ws + 256 + b_cnt + b_flags + b_states);
+  uint32_t* words = words_in_counts ? counts : (uint32_t*)(ws + 256 + b_cnt + b_flags + b_states + b_pre);
+
   ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
   if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   const bool vec = aligned(S, 16);
   const uint64_t threads = ((m + 1) / 2 + kSearchRounds - 1) / kSearchRounds;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (threads + kSearchBlock - 1) / kSearchBlock);
-  if (dup)
-    vec ? probe_search_kernel<Model, kDupCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words)
-        : probe_search_kernel<Model, kDupCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words);
-  else
-    vec ? probe_search_kernel<Model, kUniqueCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words)
-        : probe_search_kernel<Model, kUniqueCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words);
+  {
+    KernelTimer kt("probe_search_kernel", s);
+    if (dup)
+      vec ? probe_search_kernel<Model, kDupCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
+          : probe_search_kernel<Model, kDupCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
+    else
+      vec ? probe_search_kernel<Model, kUniqueCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
+          : probe_search_kernel<Model, kUniqueCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
+  }
+  LJ_CUDA(cudaGetLastError());
+  {
+    KernelTimer kt("tile_scan_kernel", s);
+    tile_scan_kernel<<<scan_blocks, kBlock, 0, s>>>(tile_counts, tiles, tile_prefix, st,
+                                                   scan_blocks, total_ws, total_dev,
+                                                   offsets ? offsets + m : nullptr,
+                                                   mode == kUniqueEmit ? cap : ~0ull, P.err);
+  }
   LJ_CUDA(cudaGetLastError());
 
   ScanParams Q{};
@@ -655,28 +744,26 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   Q.capacity = cap;
   Q.offsets = offsets;
   Q.counts = dup ? nullptr : counts;
-  Q.total_ws = w.total;
-  Q.total_out = total_dev;
-  Q.st = w.st;
-  Q.err = P.err;
-  Q.num_tiles = w.tiles;
+  Q.tile_prefix = tile_prefix;
   const bool qvec = aligned(words, 16) && (!Q.counts || aligned(Q.counts, 16));
-  if (mode == kUniqueEmit) {
-    qvec ? scan_kernel<kScanPairs, false, true><<<w.tiles, kBlock, 0, s>>>(Q)
-         : scan_kernel<kScanPairs, false, false><<<w.tiles, kBlock, 0, s>>>(Q);
-  } else {
-    if (dup)
-      qvec ? scan_kernel<kScanOffsets, true, true><<<w.tiles, kBlock, 0, s>>>(Q)
-           : scan_kernel<kScanOffsets, true, false><<<w.tiles, kBlock, 0, s>>>(Q);
+  const bool need_compact = mode == kUniqueEmit || offsets || Q.counts;
+  if (need_compact) {
+    KernelTimer kt("compact_kernel", s);
+    if (mode == kUniqueEmit)
+      qvec ? compact_kernel<kScanPairs, false, true><<<tiles, kBlock, 0, s>>>(Q)
+           : compact_kernel<kScanPairs, false, false><<<tiles, kBlock, 0, s>>>(Q);
+    else if (dup)
+      qvec ? compact_kernel<kScanOffsets, true, true><<<tiles, kBlock, 0, s>>>(Q)
+           : compact_kernel<kScanOffsets, true, false><<<tiles, kBlock, 0, s>>>(Q);
     else
-      qvec ? scan_kernel<kScanOffsets, false, true><<<w.tiles, kBlock, 0, s>>>(Q)
-           : scan_kernel<kScanOffsets, false, false><<<w.tiles, kBlock, 0, s>>>(Q);
+      qvec ? compact_kernel<kScanOffsets, false, true><<<tiles, kBlock, 0, s>>>(Q)
+           : compact_kernel<kScanOffsets, false, false><<<tiles, kBlock, 0, s>>>(Q);
   }
   LJ_CUDA(cudaGetLastError());
   if (dup && counts && !words_in_counts)
     LJ_CUDA(cudaMemcpyAsync(counts, words, m * 4, cudaMemcpyDeviceToDevice, s));
-  if (total_host) LJ_CUDA(cudaMemcpyAsync(total_host, w.total, 8, cudaMemcpyDeviceToHost, s));
-  LJ_CUDA(scratch_free(w.mem, s));
+  if (total_host) LJ_CUDA(cudaMemcpyAsync(total_host, total_ws, 8, cudaMemcpyDeviceToHost, s));
+  LJ_CUDA(scratch_free(ws, s));
   if (total_host) {
     LJ_CUDA(cudaStreamSynchronize(s));
     if (int rc = take_device_errors(idx->device, s)) return rc;
@@ -705,7 +792,10 @@ int launch_emit(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
   P.capacity = cap;
   P.offsets = const_cast<uint64_t*>(offsets);
   const uint64_t blocks = (m + kBlock - 1) / kBlock;
-  emit_kernel<Model><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+  {
+    KernelTimer kt("emit_kernel", s);
+    emit_kernel<Model><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+  }
   LJ_CUDA(cudaGetLastError());
   return 0;
 }
@@ -812,24 +902,6 @@ extern "C" int join_emit(const lj_index* idx, const uint64_t* S_dev, uint64_t m,
     return fail(LJ_E_CAPACITY, "join_emit: %llu pairs do not fit the capacity of %llu",
                 (unsigned long long)*written_host, (unsigned long long)capacity);
   return LJ_OK;
-}
-
-extern "C" int lj_set_option(const char* name, int64_t value) {
-  using namespace lj;
-  if (!name) return fail(LJ_E_INVAL, "lj_set_option: name is NULL");
-  if (!strcmp(name, "single_pass_max")) {
-    if (value < 0) return fail(LJ_E_INVAL, "single_pass_max must be >= 0");
-    set_single_pass_max((uint64_t)value);
-    return LJ_OK;
-  }
-  return fail(LJ_E_INVAL, "lj_set_option: unknown option '%s'", name);
-}
-
-extern "C" int64_t lj_get_option(const char* name) {
-  using namespace lj;
-  if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
-  fail(LJ_E_INVAL, "lj_get_option: unknown option '%s'", name ? name : "(null)");
-  return -1;
 }
 
 // ---------------------------------------------------------------------------
