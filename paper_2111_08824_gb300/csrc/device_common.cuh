@@ -62,17 +62,20 @@ struct ModelF32 {
     v = fminf(fmaxf(v, -kPredClampF), kPredClampF);
     return (int64_t)v;
   }
+  // one 32-byte load (the record is one aligned sector)
   __device__ __forceinline__ static Leaf load_leaf(const Leaf* leaves, uint32_t l) {
-    const uint4* p = reinterpret_cast<const uint4*>(leaves + l);
-    uint4 u0 = __ldg(p), u1 = __ldg(p + 1);
+    unsigned long long w0, w1, w2, w3;
+    asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+        : "l"(leaves + l));
     Leaf r;
-    r.base_key = (uint64_t)u0.x | ((uint64_t)u0.y << 32);
-    r.lo = u0.z;
-    r.hi = u0.w;
-    r.a = __uint_as_float(u1.x);
-    r.b = __uint_as_float(u1.y);
-    r.e_lo = (int32_t)u1.z;
-    r.e_hi = (int32_t)u1.w;
+    r.base_key = w0;
+    r.lo = (uint32_t)w1;
+    r.hi = (uint32_t)(w1 >> 32);
+    r.a = __uint_as_float((uint32_t)w2);
+    r.b = __uint_as_float((uint32_t)(w2 >> 32));
+    r.e_lo = (int32_t)(uint32_t)w3;
+    r.e_hi = (int32_t)(uint32_t)(w3 >> 32);
     return r;
   }
   __device__ __forceinline__ static int64_t pred(const Leaf& lf, uint64_t x) {
@@ -133,6 +136,18 @@ __device__ __forceinline__ void window(const typename Model::Leaf& lf, uint64_t 
 
 __device__ __forceinline__ uint64_t ldg_key(const uint64_t* R, uint32_t i) {
   return __ldg(reinterpret_cast<const unsigned long long*>(R) + i);
+}
+
+// Four consecutive keys R[g .. g+3] with one 32-byte load (R + g 32-byte aligned).
+__device__ __forceinline__ void ldg_key4(const uint64_t* R, uint32_t g, uint64_t (&k)[4]) {
+  unsigned long long a, b, c, d;
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+      : "l"(R + g));
+  k[0] = a;
+  k[1] = b;
+  k[2] = c;
+  k[3] = d;
 }
 
 // ------------------------------------------------------------ warp / block --

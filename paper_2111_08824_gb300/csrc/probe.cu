@@ -44,6 +44,8 @@ enum { kUniqueEmit = 0, kUniqueCount = 1, kDupCount = 2 };
 template <class Model>
 struct ProbeParams {
   const uint64_t* R;
+  uint32_t n;            // |R|
+  bool r32;              // R is 32-byte aligned (4-key sector loads allowed)
   const typename Model::Leaf* leaves;
   Model model;
   const uint64_t* S;
@@ -79,6 +81,9 @@ struct ProbeParams {
 #ifndef LJ_SMINB
 #define LJ_SMINB 1
 #endif
+#ifndef LJ_ENDGAME
+#define LJ_ENDGAME false   // search kernel: resolve the last <= 4 keys in one round (measured slower)
+#endif
 constexpr int kRounds = LJ_ROUNDS;
 constexpr int kSearchRounds = LJ_SROUNDS;
 constexpr int kSearchBlock = LJ_SBLOCK;
@@ -94,9 +99,11 @@ uint64_t g_single_pass_max = 1ull << 20;
 // (STRICT) or <= x (!STRICT), and returns res = c + 1 (so the lower bound,
 // resp. the upper bound, of x) and cv = R[c] when res > window start.
 // Rounds with FAN > 2 cut the window into FAN parts with FAN-1 independent
-// pivot loads (fewer dependent rounds, more loads); the last rounds halve.
-template <int NP, bool STRICT, int FAN = LJ_FAN>
-__device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
+// pivot loads (fewer dependent rounds, more loads); the later rounds halve.
+// ENDGAME: halving stops at 4 keys; the last <= 4 keys are then read in one
+// round (a single 32-byte load when they share an aligned sector of R).
+template <int NP, bool STRICT, bool ENDGAME = false, int FAN = LJ_FAN>
+__device__ __forceinline__ void search_last(const uint64_t* __restrict__ R, uint32_t n, bool r32,
                                             const uint64_t (&x)[NP], uint32_t (&base)[NP],
                                             uint32_t (&len)[NP], uint64_t (&cv)[NP]) {
   bool moved[NP];
@@ -144,19 +151,20 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
         }
     }
   }
+  constexpr uint32_t kStop = ENDGAME ? 4u : 1u;
   while (true) {
     bool any = false;
     uint64_t v[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p)
-      if (len[p] > 1) {
+      if (len[p] > kStop) {
         any = true;
         v[p] = ldg_key(R, base[p] + (len[p] >> 1));
       }
     if (!any) break;
 #pragma unroll
     for (int p = 0; p < NP; ++p)
-      if (len[p] > 1) {
+      if (len[p] > kStop) {
         const uint32_t half = len[p] >> 1;
         const bool go = STRICT ? (v[p] < x[p]) : (v[p] <= x[p]);
         if (go) {
@@ -167,6 +175,43 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
         len[p] -= half;
       }
   }
+  if constexpr (ENDGAME) {
+    // len <= 4: read the remaining keys in one round and count how many of
+    // them pass the test (a prefix, as R is sorted)
+    uint64_t k[NP][4];
+    uint32_t shift[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      shift[p] = 0;
+      if (len[p] > 0) {
+        const uint32_t g = base[p] & ~3u;
+        if (r32 && base[p] + len[p] - 1 <= g + 3 && g + 3 < n) {
+          ldg_key4(R, g, k[p]);
+          shift[p] = base[p] - g;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) k[p][i] = i < (int)len[p] ? ldg_key(R, base[p] + i) : 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t q = shift[p] + i;   // only the window's keys count
+        const uint64_t kv = q == 0 ? k[p][0] : q == 1 ? k[p][1] : q == 2 ? k[p][2] : k[p][3];
+        const bool in = i < (int)len[p] && q < 4;
+        const bool go = STRICT ? (kv < x[p]) : (kv <= x[p]);
+        if (in && go) {
+          c = i + 1;
+          cv[p] = kv;
+        }
+      }
+      base[p] += c;   // c == 0 with a non-empty window only when nothing moved
+      len[p] = start[p];
+    }
+  } else {
   uint64_t w[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p)
@@ -186,13 +231,14 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
     }
     len[p] = start[p];   // keep the window start for the caller
   }
+  }
 }
 
 // Lookups of 2K probes per thread: round k covers probes
 // j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
 // leaf record -> window, then the interleaved bounded searches.  cnt is the
 // number of matches, r_idx the first matching position (when cnt > 0).
-template <class Model, int MODE, int K, bool VEC>
+template <class Model, int MODE, int K, bool VEC, bool ENDGAME = false>
 __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
                                               uint32_t stride, uint32_t (&r_idx)[2 * K],
                                               uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
@@ -236,14 +282,14 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
 #pragma unroll
     for (int p = 0; p < NP; ++p) wh[p] = base[p] + len[p];
     uint64_t cv[NP];
-    search_last<NP, true>(P.R, x, base, len, cv);   // base = lower bound
+    search_last<NP, true, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);   // base = lower bound
     uint32_t lb[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       lb[p] = base[p];
       len[p] = wh[p] - base[p];
     }
-    search_last<NP, false>(P.R, x, base, len, cv);  // base = upper bound
+    search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       cnt[p] = valid[p] ? base[p] - lb[p] : 0;
@@ -251,7 +297,7 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
     }
   } else {
     uint64_t cv[NP];
-    search_last<NP, false>(P.R, x, base, len, cv);  // base = upper bound, len = start
+    search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound, len = start
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
@@ -360,7 +406,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
     uint64_t xk[1] = {key};
     uint32_t b[1] = {wl}, l[1] = {wh - wl};
     uint64_t cv[1];
-    search_last<1, true>(P.R, xk, b, l, cv);
+    search_last<1, true>(P.R, P.n, P.r32, xk, b, l, cv);
     lb = b[0];
     off = P.offsets[j];
     end = P.offsets[j + 1];
@@ -403,7 +449,7 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
   const uint64_t T = gridDim.x * (uint64_t)blockDim.x;
   uint32_t r_idx[2 * K], cnt[2 * K];
   bool valid[2 * K];
-  lookup_probes<Model, MODE, K, VEC>(P, 2 * t, (uint32_t)T, r_idx, cnt, valid);
+  lookup_probes<Model, MODE, K, VEC, LJ_ENDGAME>(P, 2 * t, (uint32_t)T, r_idx, cnt, valid);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint64_t j0 = 2 * (t + k * T);
@@ -629,6 +675,8 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
                                uint32_t s_base) {
   ProbeParams<Model> P{};
   P.R = idx->R;
+  P.n = (uint32_t)idx->n;
+  P.r32 = (reinterpret_cast<uintptr_t>(idx->R) & 31) == 0;
   P.leaves = (const typename Model::Leaf*)idx->leaves;
   P.model = model;
   P.S = S;
