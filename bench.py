@@ -194,13 +194,92 @@ def cpu_baseline(wl, sample: int) -> dict:
             "sample": f"first {m_s} probes of S against the full R ({dt:.1f} s, single thread)"}
 
 
+def run_batched(args, rank, world, dist):
+    """4096 uneven joins: per-join launches of the plain probe vs one batched
+    plan run vs the same run replayed from a CUDA graph (same GPU, same data)."""
+    import torch
+
+    import paper_2111_08824_gb300 as lj
+    from datagen import device as dg
+    t0 = time.perf_counter()
+    joins = dg.batched_workload(k=args.joins, seed=args.seed + 1000 * rank, device="cuda",
+                                scale=args.scale)
+    gen_s = time.perf_counter() - t0
+    lj.rmi_autotune_clear()
+    t0 = time.perf_counter()
+    idx, leaves = [], []
+    for j in joins:
+        L, _ = lj.rmi_autotune(j["R"], j["S"][: 1 << 16])
+        leaves.append(L)
+        idx.append(lj.rmi_build(j["R"], L, "fp32"))
+    tune_build_s = time.perf_counter() - t0
+    S_list = [j["S"] for j in joins]
+    pairs = [torch.empty((max(j["m"], 1), 2), dtype=torch.int32, device="cuda") for j in joins]
+    m_total = sum(j["m"] for j in joins)
+    n_total = sum(j["n"] for j in joins)
+    stream = torch.cuda.Stream()
+    plan = lj.join_batch_plan(idx, S_list, pairs)
+    with torch.cuda.stream(stream):
+        shape = plan.autotune(stream=stream)
+    totals = plan.run()
+    pairs_total = sum(totals)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def per_join():
+        for ix, S, p in zip(idx, S_list, pairs):
+            lj.join_emit(ix, S, p, want_total=False, stream=stream)
+
+    ms_per_join = timed(per_join, max(1, args.steps // 4))
+    ms_batch = timed(lambda: plan.run(want_totals=False, stream=stream), args.steps)
+    plan.capture(stream)
+    lj.lj_profile_report()
+    ms_graph = timed(lambda: plan.run(want_totals=False, stream=stream), args.steps)
+    assert plan.run(stream=stream) == totals
+    line = {
+        "metric": "probe_keys_per_s", "value": world * m_total / (ms_graph / 1e3), "unit": "keys/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 keys, f32 model", "data": "synthetic (generated on the device)",
+        "config": {"workload": "batched_4096", "joins": len(joins), "sum_n": n_total,
+                   "sum_m": m_total, "scale": args.scale, "seed": args.seed,
+                   "leaves": "autotuned per R", "l2": "inputs larger than L2"},
+        "pairs": pairs_total,
+        "per_join_launches": {"ms_per_step": ms_per_join, "keys_per_s": m_total / (ms_per_join / 1e3)},
+        "batched_run": {"ms_per_step": ms_batch, "keys_per_s": m_total / (ms_batch / 1e3)},
+        "graph_replay": {"ms_per_step": ms_graph, "keys_per_s": m_total / (ms_graph / 1e3)},
+        "speedup_vs_per_join": ms_per_join / ms_graph,
+        "gen_s": gen_s, "tune_and_build_s": tune_build_s,
+        "leaves_chosen": sorted(set(leaves)),
+        "tile_shape_chosen": {"block": shape[0], "tiles_per_item": shape[1]},
+        "gpu_launches": 3 * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lognormal_100m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="lognormal_100m",
+                    choices=sorted(WORKLOADS) + ["batched_4096"])
+    ap.add_argument("--joins", type=int, default=4096, help="batched workload: number of joins")
+    ap.add_argument("--scale", type=float, default=1.0, help="batched workload: size scale")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1 << 25)
@@ -223,6 +302,11 @@ def main():
 
     import paper_2111_08824_gb300 as lj
     torch.cuda.set_device(local)
+    if args.workload == "batched_4096":
+        run_batched(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     w = WORKLOADS[args.workload]
     # weak scaling: every rank probes its own S (seeded by rank) against the
     # replicated R; no collective on the data path.

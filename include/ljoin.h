@@ -198,6 +198,87 @@ int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
               lj_pair* pairs_host, uint64_t capacity, uint64_t* written_host,
               lj_stream_t stream);
 
+/* ----------------------------------------------------------- batches ---- */
+
+typedef struct lj_batch lj_batch;      /* opaque batch plan, owned by the library */
+
+/*
+ * join_batch_plan -- prepare k independent joins (Section 2.A / 2.D probe of
+ * S_j against index_j, each into its own pairs buffer) to run together.
+ *   indexes[k]   built indexes; R must be unique in each (else
+ *                LJ_E_NOTUNIQUE) and all must share one precision
+ *   S_dev[k], m[k]                 probe keys of each join (device)
+ *   pairs_dev[k], capacity[k]      output of each join (device); pairs beyond
+ *                                  a join's capacity are not written
+ * The plan copies the descriptors to the device and allocates all scratch
+ * (4 bytes per probe of the batch plus small tables) up front; it borrows
+ * every pointer, which must stay valid while the plan is used.  Synchronises.
+ * Errors: LJ_E_INVAL, LJ_E_NOTUNIQUE, LJ_E_NOMEM, LJ_E_CUDA.
+ */
+int join_batch_plan(const lj_index* const* indexes, const uint64_t* const* S_dev,
+                    const uint64_t* m, uint32_t k, lj_pair* const* pairs_dev,
+                    const uint64_t* capacity, lj_stream_t stream, lj_batch** out);
+
+/*
+ * join_batch_run -- run every join of a plan: one persistent search launch
+ * that balances all joins' tiles over the GPU, one scan, one compaction;
+ * asynchronous, allocation-free.  Outputs:
+ *   written_dev   optional device array of k uint64: each join's |J|
+ *   written_host  optional host array of k uint64; if given the call
+ *                 synchronises and reports LJ_E_CAPACITY if a join overflowed.
+ * A plan's runs must not overlap on the GPU (they share the plan's scratch).
+ */
+int join_batch_run(lj_batch* plan, uint64_t* written_dev, uint64_t* written_host,
+                   lj_stream_t stream);
+
+/*
+ * join_batch_capture -- record one run of the plan as a CUDA graph on
+ * `stream` (a non-default stream); later join_batch_run calls launch the
+ * graph instead of the individual operations.  Errors: LJ_E_INVAL, LJ_E_CUDA.
+ */
+int join_batch_capture(lj_batch* plan, lj_stream_t stream);
+
+/*
+ * join_batch_set_shape -- work-item shape of the batched search: `block`
+ * threads per block (128 or 256, two probes per thread and tile) and
+ * `tiles_per_item` consecutive tiles of one join per work item (1, 4 or 8).
+ * Default 128 x 4 (1024 probes per item).  Drops a captured graph.
+ * Synchronises.  Errors: LJ_E_INVAL, LJ_E_CUDA.
+ */
+int join_batch_set_shape(lj_batch* plan, int block, int tiles_per_item);
+
+/*
+ * join_batch_autotune -- time one run of the plan for each work-item shape
+ * (128 or 256 threads x 1, 4 or 8 tiles) and keep the fastest; the chosen
+ * shape is returned in best_block / best_tiles (nullable).  The runs write
+ * the joins' outputs.  Synchronises.  Errors: as join_batch_run.
+ */
+int join_batch_autotune(lj_batch* plan, lj_stream_t stream, int* best_block, int* best_tiles);
+
+/* Release a plan (its scratch and graph).  NULL is ok. */
+void join_batch_free(lj_batch* plan);
+
+/* join_batch -- plan + run + free in one call (the one-shot form).  written_host
+ * (k uint64, nullable) receives each join's |J|.  Synchronises. */
+int join_batch(const lj_index* const* indexes, const uint64_t* const* S_dev, const uint64_t* m,
+               uint32_t k, lj_pair* const* pairs_dev, const uint64_t* capacity,
+               uint64_t* written_host, lj_stream_t stream);
+
+/*
+ * rmi_autotune -- choose the leaf count L for an index over R (the paper tunes
+ * its RMIs with an optimiser, Section 6.A; this is the library's own tuner):
+ * builds the index for L = 2^8, 2^10, ... up to min(2^22, n/2), times the probe
+ * path on the sample S_sample_dev (m_sample keys, device) and returns the L
+ * with the least time per key (best_ns_per_key: that time, or -1 when the
+ * answer came from the cache).  Answers are cached per (floor(log2 n), skew
+ * bucket of R, precision); rmi_autotune_clear empties the cache.
+ * Synchronises.  Errors: those of rmi_build / join_emit.
+ */
+int rmi_autotune(const uint64_t* R_dev, uint64_t n, const uint64_t* S_sample_dev,
+                 uint64_t m_sample, int precision, lj_stream_t stream, uint32_t* best_leaves,
+                 double* best_ns_per_key);
+void rmi_autotune_clear(void);
+
 /* ------------------------------------------------------ diagnostics ----- */
 
 /*

@@ -52,6 +52,15 @@ SIGNATURES = {
     "join_count_noalloc": ([_P, _P, _U64, _P, _P, _P, _P], _I),
     "join_emit": ([_P, _P, _U64, _P, _P, _U64, _P, _P, _P], _I),
     "join_host": ([_P, _P, _U64, _P, _U64, _P, _P], _I),
+    "join_batch_plan": ([_P, _P, _P, _U32, _P, _P, _P, _P], _I),
+    "join_batch_run": ([_P, _P, _P, _P], _I),
+    "join_batch_capture": ([_P, _P], _I),
+    "join_batch_set_shape": ([_P, _I, _I], _I),
+    "join_batch_autotune": ([_P, _P, _P, _P], _I),
+    "join_batch_free": ([_P], None),
+    "join_batch": ([_P, _P, _P, _U32, _P, _P, _P, _P], _I),
+    "rmi_autotune": ([_P, _U64, _P, _U64, _I, _P, _P, _P], _I),
+    "rmi_autotune_clear": ([], None),
     "lj_set_option": ([ctypes.c_char_p, ctypes.c_int64], _I),
     "lj_get_option": ([ctypes.c_char_p], ctypes.c_int64),
     "lj_profile_report": ([ctypes.c_char_p, ctypes.c_size_t], _I),
@@ -208,6 +217,94 @@ def join_host(index: Index, S_host: np.ndarray, pairs_host: np.ndarray, stream=N
     _check(load().join_host(index.handle, _ptr(S_host), S_host.size, _ptr(pairs_host),
                             pairs_host.shape[0], ctypes.byref(total), _stream_ptr(stream)))
     return total.value
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = _ptr(t)
+    return arr
+
+
+class BatchPlan:
+    """A plan of k joins (unique-R indexes of one precision) that run together:
+    one persistent search launch, one scan, one compaction per run."""
+
+    def __init__(self, indexes, S_list, pairs_list, stream=None):
+        k = len(indexes)
+        assert k == len(S_list) == len(pairs_list) and k > 0
+        for S in S_list:
+            _require_cuda_u64(S, "S")
+        self._keep = (list(indexes), list(S_list), list(pairs_list))
+        m = (ctypes.c_uint64 * k)(*[S.numel() for S in S_list])
+        cap = (ctypes.c_uint64 * k)(*[p.shape[0] for p in pairs_list])
+        out = ctypes.c_void_p()
+        _check(load().join_batch_plan((ctypes.c_void_p * k)(*[ix.handle for ix in indexes]),
+                                      _ptr_array(S_list), m, k, _ptr_array(pairs_list), cap,
+                                      _stream_ptr(stream), ctypes.byref(out)))
+        self.handle = out.value
+        self.k = k
+
+    def run(self, want_totals: bool = True, written=None, stream=None):
+        tot = (ctypes.c_uint64 * self.k)()
+        _check(load().join_batch_run(self.handle, _ptr(written),
+                                     tot if want_totals else None, _stream_ptr(stream)))
+        return list(tot) if want_totals else None
+
+    def capture(self, stream):
+        _check(load().join_batch_capture(self.handle, _stream_ptr(stream)))
+
+    def set_shape(self, block: int, tiles_per_item: int):
+        _check(load().join_batch_set_shape(self.handle, int(block), int(tiles_per_item)))
+
+    def autotune(self, stream=None) -> tuple[int, int]:
+        """Pick the fastest work-item shape by timing one run of each."""
+        bb, bt = ctypes.c_int(), ctypes.c_int()
+        _check(load().join_batch_autotune(self.handle, _stream_ptr(stream), ctypes.byref(bb),
+                                          ctypes.byref(bt)))
+        return bb.value, bt.value
+
+    def free(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.join_batch_free(h)
+
+    def __del__(self):
+        self.free()
+
+
+def join_batch_plan(indexes, S_list, pairs_list, stream=None) -> BatchPlan:
+    return BatchPlan(indexes, S_list, pairs_list, stream)
+
+
+def join_batch(indexes, S_list, pairs_list, stream=None) -> list:
+    """Plan + run + free: each join's |J| (pairs written into pairs_list[j])."""
+    k = len(indexes)
+    for S in S_list:
+        _require_cuda_u64(S, "S")
+    m = (ctypes.c_uint64 * k)(*[S.numel() for S in S_list])
+    cap = (ctypes.c_uint64 * k)(*[p.shape[0] for p in pairs_list])
+    tot = (ctypes.c_uint64 * k)()
+    _check(load().join_batch((ctypes.c_void_p * k)(*[ix.handle for ix in indexes]),
+                             _ptr_array(S_list), m, k, _ptr_array(pairs_list), cap, tot,
+                             _stream_ptr(stream)))
+    return list(tot)
+
+
+def rmi_autotune(R, S_sample, precision: str | int = "fp32", stream=None) -> tuple[int, float]:
+    """Leaf count with the least probe time per key on S_sample (cached)."""
+    _require_cuda_u64(R, "R")
+    _require_cuda_u64(S_sample, "S_sample")
+    prec = {"fp32": LJ_FP32, "fp64": LJ_FP64}.get(precision, precision)
+    L = ctypes.c_uint32()
+    ns = ctypes.c_double()
+    _check(load().rmi_autotune(_ptr(R), R.numel(), _ptr(S_sample), S_sample.numel(), prec,
+                               _stream_ptr(stream), ctypes.byref(L), ctypes.byref(ns)))
+    return L.value, ns.value
+
+
+def rmi_autotune_clear():
+    load().rmi_autotune_clear()
 
 
 def lj_set_option(name: str, value: int):

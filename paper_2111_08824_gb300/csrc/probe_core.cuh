@@ -1,0 +1,343 @@
+// Device code shared by the probe paths (single join, batched joins):
+// tunables, probe parameters, the interleaved bounded search of the learned
+// lookup (Section 2.D of Sabek and Kraska, "The Case for Learned In-Memory
+// Joins": root -> leaf -> predicted position -> binary search between the
+// leaf's error bounds) and the scan of per-tile match counts.
+#pragma once
+
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace lj {
+namespace {   // internal linkage: each translation unit keeps its own copy
+
+constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+enum { kUniqueEmit = 0, kUniqueCount = 1, kDupCount = 2 };
+
+template <class Model>
+struct ProbeParams {
+  const uint64_t* R;
+  uint32_t n;            // |R|
+  bool r32;              // R is 32-byte aligned (4-key sector loads allowed)
+  const typename Model::Leaf* leaves;
+  Model model;
+  const uint64_t* S;
+  uint64_t m;
+  lj_pair* pairs;
+  uint64_t capacity;
+  uint32_t* counts;      // optional
+  uint64_t* offsets;     // optional, m + 1
+  uint64_t* total_out;   // optional, device
+  uint64_t* total_ws;    // workspace copy of the total
+  uint32_t s_base;       // added to s_idx (chunked host joins)
+  TileState st;
+  uint32_t* err;
+  uint32_t num_tiles;
+};
+
+// Tunables (fixed at compile time; the defaults are the measured best).
+#ifndef LJ_ROUNDS
+#define LJ_ROUNDS 4        // probe rounds per thread (2 probes each)
+#endif
+#ifndef LJ_MINB
+#define LJ_MINB 1          // min resident blocks per SM requested from ptxas
+#endif
+#ifndef LJ_FAN
+#define LJ_FAN 2           // search fan-out: FAN-1 independent pivots per round
+#endif
+#ifndef LJ_SROUNDS
+#define LJ_SROUNDS 1       // search kernel: probe rounds per thread (2 probes each)
+#endif
+#ifndef LJ_SBLOCK
+#define LJ_SBLOCK 128      // search kernel: threads per block
+#endif
+#ifndef LJ_SMINB
+#define LJ_SMINB 1
+#endif
+#ifndef LJ_ENDGAME
+#define LJ_ENDGAME false   // search kernel: resolve the last <= 4 keys in one round (measured slower)
+#endif
+constexpr int kRounds = LJ_ROUNDS;
+constexpr int kSearchRounds = LJ_SROUNDS;
+constexpr int kSearchBlock = LJ_SBLOCK;
+constexpr uint32_t kNoMatch = 0xFFFFFFFFu;
+enum { kScanPairs = 0, kScanOffsets = 1 };
+constexpr int kScanItems = 16;
+constexpr uint64_t kCompactTile = 256ull * kScanItems;   // probes per compaction tile
+
+// Interleaved bounded searches over NP windows.  For each probe p with
+// window [base, base+len): finds c = the last position whose key is < x
+// (STRICT) or <= x (!STRICT), and returns res = c + 1 (so the lower bound,
+// resp. the upper bound, of x) and cv = R[c] when res > window start.
+// Rounds with FAN > 2 cut the window into FAN parts with FAN-1 independent
+// pivot loads (fewer dependent rounds, more loads); the later rounds halve.
+// ENDGAME: halving stops at 4 keys; the last <= 4 keys are then read in one
+// round (a single 32-byte load when they share an aligned sector of R).
+template <int NP, bool STRICT, bool ENDGAME = false, int FAN = LJ_FAN>
+__device__ __forceinline__ void search_last(const uint64_t* __restrict__ R, uint32_t n, bool r32,
+                                            const uint64_t (&x)[NP], uint32_t (&base)[NP],
+                                            uint32_t (&len)[NP], uint64_t (&cv)[NP]) {
+  bool moved[NP];
+  uint32_t start[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    moved[p] = false;
+    start[p] = base[p];
+    cv[p] = 0;
+  }
+  if (FAN > 2) {
+    // k-ary rounds while the window has at least 2*FAN keys
+    while (true) {
+      bool any = false;
+      uint64_t v[NP][FAN - 1];
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (len[p] >= 2 * FAN) {
+          any = true;
+          const uint32_t step = len[p] / FAN;
+#pragma unroll
+          for (int t = 1; t < FAN; ++t) v[p][t - 1] = ldg_key(R, base[p] + t * step);
+        }
+      if (!any) break;
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        if (len[p] >= 2 * FAN) {
+          const uint32_t step = len[p] / FAN;
+          int c = 0;
+          uint64_t last = 0;
+#pragma unroll
+          for (int t = 1; t < FAN; ++t) {
+            const bool go = STRICT ? (v[p][t - 1] < x[p]) : (v[p][t - 1] <= x[p]);
+            if (go) {
+              c = t;
+              last = v[p][t - 1];
+            }
+          }
+          if (c > 0) {
+            cv[p] = last;
+            moved[p] = true;
+          }
+          base[p] += c * step;
+          len[p] = c == FAN - 1 ? len[p] - (FAN - 1) * step : step;
+        }
+    }
+  }
+  constexpr uint32_t kStop = ENDGAME ? 4u : 1u;
+  while (true) {
+    bool any = false;
+    uint64_t v[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (len[p] > kStop) {
+        any = true;
+        v[p] = ldg_key(R, base[p] + (len[p] >> 1));
+      }
+    if (!any) break;
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (len[p] > kStop) {
+        const uint32_t half = len[p] >> 1;
+        const bool go = STRICT ? (v[p] < x[p]) : (v[p] <= x[p]);
+        if (go) {
+          base[p] += half;
+          cv[p] = v[p];
+          moved[p] = true;
+        }
+        len[p] -= half;
+      }
+  }
+  if constexpr (ENDGAME) {
+    // len <= 4: read the remaining keys in one round and count how many of
+    // them pass the test (a prefix, as R is sorted)
+    uint64_t k[NP][4];
+    uint32_t shift[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      shift[p] = 0;
+      if (len[p] > 0) {
+        const uint32_t g = base[p] & ~3u;
+        if (r32 && base[p] + len[p] - 1 <= g + 3 && g + 3 < n) {
+          ldg_key4(R, g, k[p]);
+          shift[p] = base[p] - g;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) k[p][i] = i < (int)len[p] ? ldg_key(R, base[p] + i) : 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t q = shift[p] + i;   // only the window's keys count
+        const uint64_t kv = q == 0 ? k[p][0] : q == 1 ? k[p][1] : q == 2 ? k[p][2] : k[p][3];
+        const bool in = i < (int)len[p] && q < 4;
+        const bool go = STRICT ? (kv < x[p]) : (kv <= x[p]);
+        if (in && go) {
+          c = i + 1;
+          cv[p] = kv;
+        }
+      }
+      base[p] += c;   // c == 0 with a non-empty window only when nothing moved
+      len[p] = start[p];
+    }
+  } else {
+  uint64_t w[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p)
+    if (len[p] == 1 && !moved[p]) w[p] = ldg_key(R, base[p]);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    if (len[p] == 0) {          // empty window
+      base[p] = start[p];
+    } else if (moved[p]) {
+      base[p] += 1;
+    } else {
+      const bool go = STRICT ? (w[p] < x[p]) : (w[p] <= x[p]);
+      if (go) {
+        cv[p] = w[p];
+        base[p] += 1;
+      }
+    }
+    len[p] = start[p];   // keep the window start for the caller
+  }
+  }
+}
+
+// Lookups of 2K probes per thread: round k covers probes
+// j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
+// leaf record -> window, then the interleaved bounded searches.  cnt is the
+// number of matches, r_idx the first matching position (when cnt > 0).
+template <class Model, int MODE, int K, bool VEC, bool ENDGAME = false>
+__device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
+                                              uint32_t stride, uint32_t (&r_idx)[2 * K],
+                                              uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
+  constexpr int NP = 2 * K;
+  uint64_t x[NP];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t j0 = first + 2ull * stride * k;
+    if (VEC && j0 + 1 < P.m) {
+      const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(P.S + j0));
+      x[2 * k] = v.x;
+      x[2 * k + 1] = v.y;
+      valid[2 * k] = valid[2 * k + 1] = true;
+    } else {
+      valid[2 * k] = j0 < P.m;
+      valid[2 * k + 1] = j0 + 1 < P.m;
+      x[2 * k] = valid[2 * k] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0) : 0;
+      x[2 * k + 1] =
+          valid[2 * k + 1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
+    }
+  }
+  uint32_t base[NP], len[NP];
+  {
+    uint32_t leaf[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) leaf[p] = P.model.leaf(x[p]);
+    typename Model::Leaf lf[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (valid[p]) lf[p] = Model::load_leaf(P.leaves, leaf[p]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      uint32_t wl = 0, wh = 0;
+      if (valid[p]) window<Model>(lf[p], x[p], wl, wh);
+      base[p] = wl;
+      len[p] = wh - wl;
+    }
+  }
+  if (MODE == kDupCount) {
+    uint32_t wh[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) wh[p] = base[p] + len[p];
+    uint64_t cv[NP];
+    search_last<NP, true, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);   // base = lower bound
+    uint32_t lb[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      lb[p] = base[p];
+      len[p] = wh[p] - base[p];
+    }
+    search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      cnt[p] = valid[p] ? base[p] - lb[p] : 0;
+      r_idx[p] = lb[p];
+    }
+  } else {
+    uint64_t cv[NP];
+    search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound, len = start
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
+      cnt[p] = match ? 1u : 0u;
+      r_idx[p] = base[p] - 1;
+    }
+  }
+}
+
+// Exclusive scan of the per-tile counts: blocks of 256 threads x 16 counts
+// with a decoupled look-back between blocks (a few hundred at most).
+// prefix[t] = first output position of tile t, prefix[tiles] = |J|; the last
+// block also publishes the total.
+constexpr int kTileScanItems = 16;
+constexpr uint32_t kTileScanSpan = kBlock * kTileScanItems;
+
+__global__ void __launch_bounds__(kBlock) tile_scan_kernel(const unsigned long long* counts,
+                                                           uint32_t tiles, uint64_t* prefix,
+                                                           TileState st, uint32_t blocks,
+                                                           uint64_t* total_ws, uint64_t* total_out,
+                                                           uint64_t* offsets_end, uint64_t capacity,
+                                                           uint32_t* err) {
+  __shared__ uint32_t s_blk;
+  __shared__ uint64_t s_warp[kWarps];
+  __shared__ uint64_t s_prefix;
+  if (threadIdx.x == 0) s_blk = atomicAdd(st.ticket, 1u);
+  __syncthreads();
+  const uint32_t blk = s_blk;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t base = (uint64_t)blk * kTileScanSpan + (uint64_t)threadIdx.x * kTileScanItems;
+  uint64_t v[kTileScanItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kTileScanItems; ++i) {
+    v[i] = base + i < tiles ? counts[base + i] : 0;
+    sum += v[i];
+  }
+  const uint64_t inc = warp_inclusive_sum(sum, lane);
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint64_t x = lane < kWarps ? s_warp[lane] : 0;
+    const uint64_t xi = warp_inclusive_sum(x, lane);
+    if (lane < kWarps) s_warp[lane] = xi - x;
+    const uint64_t agg = __shfl_sync(0xffffffffu, xi, 31);
+    const uint64_t pre = lookback_warp(st, blk, agg, err);
+    if (lane == 0) {
+      s_prefix = pre;
+      if (blk + 1 == blocks) {
+        const uint64_t total = pre + agg;
+        prefix[tiles] = total;
+        *total_ws = total;
+        if (total_out) *total_out = total;
+        if (offsets_end) *offsets_end = total;
+        if (total > capacity) atomicOr(err, kErrCapacity);
+      }
+    }
+  }
+  __syncthreads();
+  uint64_t run = s_prefix + s_warp[w] + inc - sum;
+#pragma unroll
+  for (int i = 0; i < kTileScanItems; ++i) {
+    if (base + i < tiles) prefix[base + i] = run;
+    run += v[i];
+  }
+}
+
+}  // namespace
+}  // namespace lj
