@@ -270,6 +270,144 @@ def run_batched(args, rank, world, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_served(args, rank, world, dist):
+    """64 resident relations, Poisson arrivals; continuous-batching server vs
+    a plain per-request probe fed by the same arrival times."""
+    import queue
+    import threading
+
+    import torch
+
+    import paper_2111_08824_gb300 as lj
+    from datagen import device as dg
+    t0 = time.perf_counter()
+    rels = dg.batched_workload(k=64, seed=args.seed + 77, device="cuda",
+                               n_range=(1 << 20, 1 << 26), m_range=(2, 4), scale=args.scale)
+    lj.rmi_autotune_clear()
+    idx = []
+    for j in rels:
+        R = j["R"]
+        L, _ = lj.rmi_autotune(R, R[torch.randint(0, R.numel(), (1 << 16,), device="cuda")])
+        idx.append(lj.rmi_build(R, L, "fp32"))
+    # a pool of requests, replayed in order: relation uniform, m log-uniform
+    # in [2^10, 2^23], 70% keys drawn from the relation, 30% fresh 62-bit keys
+    rng = np.random.default_rng(args.seed + 5)
+    pool = []
+    for q in range(args.joins if args.joins != 4096 else 1024):
+        r = int(rng.integers(0, len(rels)))
+        m = int(np.exp(rng.uniform(np.log(1 << 10), np.log(1 << 23))) * args.scale) or 1
+        R = rels[r]["R"]
+        g = torch.Generator(device="cuda").manual_seed(args.seed * 1000 + q)
+        hits = R[torch.randint(0, R.numel(), (m,), device="cuda", generator=g)]
+        miss = torch.randint(0, 2**62, (m,), device="cuda", generator=g)
+        coin = torch.rand(m, device="cuda", generator=g) < 0.7
+        pool.append((r, torch.where(coin, hits, miss).contiguous()))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    n_req = int(args.rate * args.duration)
+    gaps = rng.exponential(1.0 / args.rate, n_req)
+
+    def serve(rate_gaps):
+        srv = lj.Server(hbm_budget_bytes=150 << 30, streams=4, max_batch=256)
+        rids = [srv.add_relation(ix) for ix in idx]
+        tickets = queue.Queue()
+        done_keys = [0]
+
+        def waiter():
+            while True:
+                t = tickets.get()
+                if t is None:
+                    return
+                res = srv.wait(t)
+                done_keys[0] += res["pairs"]
+                srv.release(t)
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        start = time.perf_counter()
+        nxt = start
+        for q, gap in enumerate(rate_gaps):
+            nxt += gap
+            dt = nxt - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)          # releases the GIL for the other thread
+            r, S = pool[q % len(pool)]
+            tickets.put(srv.submit(rids[r], S))
+        tickets.put(None)
+        th.join()
+        st = srv.stats()
+        srv.close()
+        return st
+
+    def plain(rate_gaps):
+        """Each request alone with join_emit on one stream, in arrival order."""
+        work = queue.Queue()
+        lat = []
+        keys = [0]
+        bufs = {}
+
+        def worker():
+            while True:
+                item = work.get()
+                if item is None:
+                    return
+                t_arr, q = item
+                r, S = pool[q % len(pool)]
+                p = bufs.get(q % len(pool))
+                if p is None:
+                    p = bufs[q % len(pool)] = torch.empty((max(S.numel(), 1), 2),
+                                                          dtype=torch.int32, device="cuda")
+                lj.join_emit(idx[r], S, p)
+                keys[0] += S.numel()
+                lat.append((time.perf_counter() - t_arr) * 1e6)
+
+        th = threading.Thread(target=worker)
+        th.start()
+        start = time.perf_counter()
+        nxt = start
+        for q, gap in enumerate(rate_gaps):
+            nxt += gap
+            dt = nxt - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)          # releases the GIL for the other thread
+            work.put((time.perf_counter(), q))
+        work.put(None)
+        th.join()
+        span = time.perf_counter() - start
+        lat.sort()
+        return {"p50_us": lat[len(lat) // 2], "p99_us": lat[int(0.99 * (len(lat) - 1))],
+                "keys_per_s": keys[0] / span, "completed": len(lat)}
+
+    # warm-up both paths on a few requests
+    serve(gaps[:64])
+    plain(gaps[:64])
+    s_srv = serve(gaps)
+    s_plain = plain(gaps)
+    # saturation: all requests at once (closed batch), both paths
+    burst = np.zeros(min(n_req, 4 * len(pool)))
+    sat_srv = serve(burst)
+    sat_plain = plain(burst)
+    line = {
+        "metric": "served_p99_latency_us", "value": s_srv["p99_us"], "unit": "us",
+        "n_gpus": world, "steps": n_req, "warmup": 64, "ms_per_step": s_srv["mean_us"] / 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 keys, f32 model", "data": "synthetic (generated on the device)",
+        "config": {"workload": "served_64", "relations": len(rels),
+                   "sum_n": int(sum(j["n"] for j in rels)), "rate_per_s": args.rate,
+                   "duration_s": args.duration, "requests": n_req, "pool": len(pool),
+                   "hbm_budget_gb": 150, "streams": 4, "scale": args.scale},
+        "server": {k: s_srv[k] for k in ("p50_us", "p99_us", "mean_us", "keys_per_s",
+                                          "completed", "batches", "mean_batch", "mem_peak")},
+        "plain_per_request": s_plain,
+        "saturation": {"server": {k: sat_srv[k] for k in ("p50_us", "p99_us", "keys_per_s",
+                                                           "mean_batch")},
+                       "plain_per_request": sat_plain},
+        "setup_s": setup_s,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,7 +415,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lognormal_100m",
-                    choices=sorted(WORKLOADS) + ["batched_4096"])
+                    choices=sorted(WORKLOADS) + ["batched_4096", "served_64"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="served workload: requests/s")
+    ap.add_argument("--duration", type=float, default=5.0, help="served workload: seconds")
     ap.add_argument("--joins", type=int, default=4096, help="batched workload: number of joins")
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: size scale")
     ap.add_argument("--seed", type=int, default=0)
@@ -302,6 +442,11 @@ def main():
 
     import paper_2111_08824_gb300 as lj
     torch.cuda.set_device(local)
+    if args.workload == "served_64":
+        run_served(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.workload == "batched_4096":
         run_batched(args, rank, world, dist)
         if dist:

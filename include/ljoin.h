@@ -279,6 +279,70 @@ int rmi_autotune(const uint64_t* R_dev, uint64_t n, const uint64_t* S_sample_dev
                  double* best_ns_per_key);
 void rmi_autotune_clear(void);
 
+/* ----------------------------------------------------------- serving ---- */
+
+typedef struct lj_server lj_server;    /* opaque request server */
+typedef uint64_t lj_ticket;            /* one submitted request */
+
+typedef struct {
+  uint64_t hbm_budget_bytes;   /* device memory requests may hold at once */
+  uint32_t streams;            /* in-flight batches (slots), 1..16 */
+  uint32_t max_batch;          /* requests per batch, 1..65536 */
+} lj_server_cfg;
+
+typedef struct {
+  int32_t status;              /* 0, or the request's LJ_E_* error */
+  uint64_t pairs;              /* |J| of the request */
+  const lj_pair* pairs_dev;    /* server-owned result until join_release */
+  double latency_us;           /* submit -> completion seen by the server */
+  double queue_us;             /* submit -> launch */
+} lj_result;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, keys, batches;
+  double mean_batch;           /* requests per launched batch */
+  uint64_t mem_in_use, mem_peak;
+  double p50_us, p99_us, mean_us, max_us;
+  double span_s;               /* first submit -> last completion */
+  double keys_per_s;           /* probe keys completed / span */
+} lj_server_stats;
+
+/*
+ * Serving: resident learned indexes answer probe requests with continuous
+ * batching.  Each request is one join (Section 2.A probe of its keys against
+ * a resident relation's index, Section 2.D), answered exactly as join_emit
+ * would answer it alone.  A scheduler thread admits pending requests first
+ * come, first served, when an in-flight slot is free and the memory they need
+ * (12 bytes per probe: 8 for pairs, 4 for search words) fits the budget;
+ * every admitted group runs as one batched launch on its slot's stream, so
+ * batches admitted while others run overlap on the device.
+ *
+ * join_server_create   start a server on the current device.
+ * join_server_add_relation  register a built index (unique R, one precision
+ *                      for all relations; borrowed); returns its id.
+ * join_submit          queue a request: m probe keys at S (device or
+ *                      page-locked host memory, valid until the request
+ *                      completes).  Returns at once.  LJ_E_BUDGET if the
+ *                      request alone exceeds the budget.
+ * join_wait            wait (timeout_us < 0: forever) for a request;
+ *                      LJ_E_TIMEOUT if it is not done in time.
+ * join_fetch           copy a completed request's pairs to dst_dev
+ *                      (stream-ordered on `stream`).
+ * join_release         drop a completed request and free its pairs.
+ * join_server_stats    counters and latency percentiles (reset: clear them).
+ * join_server_destroy  finish queued work, stop the scheduler, free all.
+ */
+int join_server_create(const lj_server_cfg* cfg, lj_server** out);
+int join_server_add_relation(lj_server* server, const lj_index* index, uint32_t* rel_id);
+int join_submit(lj_server* server, uint32_t rel_id, const uint64_t* S, uint64_t m,
+                lj_ticket* ticket);
+int join_wait(lj_server* server, lj_ticket ticket, int64_t timeout_us, lj_result* result);
+int join_fetch(lj_server* server, lj_ticket ticket, lj_pair* dst_dev, uint64_t capacity,
+               lj_stream_t stream);
+int join_release(lj_server* server, lj_ticket ticket);
+int join_server_stats(lj_server* server, lj_server_stats* out, int reset);
+void join_server_destroy(lj_server* server);
+
 /* ------------------------------------------------------ diagnostics ----- */
 
 /*

@@ -38,6 +38,27 @@ class lj_index_stats(ctypes.Structure):
                 ("build_ms", ctypes.c_double)]
 
 
+class lj_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("streams", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32)]
+
+
+class lj_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("pairs", ctypes.c_uint64),
+                ("pairs_dev", ctypes.c_void_p), ("latency_us", ctypes.c_double),
+                ("queue_us", ctypes.c_double)]
+
+
+class lj_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("keys", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double),
+                ("mem_in_use", ctypes.c_uint64), ("mem_peak", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("span_s", ctypes.c_double), ("keys_per_s", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -60,6 +81,14 @@ SIGNATURES = {
     "join_batch_free": ([_P], None),
     "join_batch": ([_P, _P, _P, _U32, _P, _P, _P, _P], _I),
     "rmi_autotune": ([_P, _U64, _P, _U64, _I, _P, _P, _P], _I),
+    "join_server_create": ([_P, _P], _I),
+    "join_server_add_relation": ([_P, _P, _P], _I),
+    "join_submit": ([_P, _U32, _P, _U64, _P], _I),
+    "join_wait": ([_P, _U64, ctypes.c_int64, _P], _I),
+    "join_fetch": ([_P, _U64, _P, _U64, _P], _I),
+    "join_release": ([_P, _U64], _I),
+    "join_server_stats": ([_P, _P, _I], _I),
+    "join_server_destroy": ([_P], None),
     "rmi_autotune_clear": ([], None),
     "lj_set_option": ([ctypes.c_char_p, ctypes.c_int64], _I),
     "lj_get_option": ([ctypes.c_char_p], ctypes.c_int64),
@@ -305,6 +334,60 @@ def rmi_autotune(R, S_sample, precision: str | int = "fp32", stream=None) -> tup
 
 def rmi_autotune_clear():
     load().rmi_autotune_clear()
+
+
+class Server:
+    """Continuous-batching join server over resident learned indexes."""
+
+    def __init__(self, hbm_budget_bytes: int = 150 << 30, streams: int = 4,
+                 max_batch: int = 1024):
+        cfg = lj_server_cfg(hbm_budget_bytes, streams, max_batch)
+        out = ctypes.c_void_p()
+        _check(load().join_server_create(ctypes.byref(cfg), ctypes.byref(out)))
+        self.handle = out.value
+        self._keep = {}          # ticket -> S (must stay alive until the request is done)
+        self._rels = []
+
+    def add_relation(self, index: Index) -> int:
+        rid = ctypes.c_uint32()
+        _check(load().join_server_add_relation(self.handle, index.handle, ctypes.byref(rid)))
+        self._rels.append(index)
+        return rid.value
+
+    def submit(self, rel: int, S) -> int:
+        t = ctypes.c_uint64()
+        _check(load().join_submit(self.handle, rel, _ptr(S), S.numel() if hasattr(S, "numel")
+                                  else S.size, ctypes.byref(t)))
+        self._keep[t.value] = S
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        r = lj_result()
+        _check(load().join_wait(self.handle, ticket, timeout_us, ctypes.byref(r)))
+        return {"status": r.status, "pairs": r.pairs, "latency_us": r.latency_us,
+                "queue_us": r.queue_us}
+
+    def fetch(self, ticket: int, out, stream=None):
+        _check(load().join_fetch(self.handle, ticket, _ptr(out), out.shape[0],
+                                 _stream_ptr(stream)))
+
+    def release(self, ticket: int):
+        _check(load().join_release(self.handle, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = lj_server_stats()
+        _check(load().join_server_stats(self.handle, ctypes.byref(st), int(reset)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.join_server_destroy(h)
+        self._keep = {}
+
+    def __del__(self):
+        self.close()
 
 
 def lj_set_option(name: str, value: int):

@@ -323,6 +323,158 @@ int skew_bucket(const uint64_t* R, uint64_t n, cudaStream_t s, int* out) {
 }
 
 }  // namespace
+
+// ------------------------------------------------ dynamic batches (serving) --
+
+namespace {
+constexpr int kDynBlock = 128, kDynChunk = 8;
+constexpr uint64_t kDynItem = 2ull * kDynBlock * kDynChunk;
+
+struct DynLayout {
+  uint64_t tiles = 0, items = 0;
+  uint32_t scan_blocks = 0;
+  size_t b_cnt = 0, b_flags = 0, b_states = 0, b_pre = 0, b_words = 0;
+  size_t total() const { return 256 + b_cnt + b_flags + b_states + b_pre + b_words; }
+};
+
+DynLayout dyn_layout(const BatchJob* jobs, uint32_t k) {
+  DynLayout L;
+  uint64_t words = 0;
+  for (uint32_t j = 0; j < k; ++j) {
+    L.tiles += (jobs[j].m + kCompactTile - 1) / kCompactTile;
+    L.items += (jobs[j].m + kDynItem - 1) / kDynItem;
+    words += (jobs[j].m + 3) & ~3ull;
+  }
+  const uint64_t Tc = std::max<uint64_t>(1, L.tiles);
+  L.scan_blocks = (uint32_t)((Tc + kTileScanSpan - 1) / kTileScanSpan);
+  L.b_cnt = (Tc * 8 + 255) / 256 * 256;
+  L.b_flags = ((size_t)L.scan_blocks * 4 + 255) / 256 * 256;
+  L.b_states = ((size_t)L.scan_blocks * 16 + 255) / 256 * 256;
+  L.b_pre = ((Tc + 1) * 8 + 255) / 256 * 256;
+  L.b_words = std::max<uint64_t>(words, 4) * 4;
+  return L;
+}
+
+unsigned dyn_grid(int dev, int precision) {
+  static unsigned grid[2][64] = {};
+  const int p = precision == LJ_FP64 ? 1 : 0;
+  if (dev >= 0 && dev < 64 && grid[p][dev]) return grid[p][dev];
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (p)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, batch_search_kernel<ModelF64, kDynBlock, kDynChunk>, kDynBlock, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, batch_search_kernel<ModelF32, kDynBlock, kDynChunk>, kDynBlock, 0);
+  const unsigned g = (unsigned)std::max(1, sms * std::max(1, per_sm));
+  if (dev >= 0 && dev < 64) grid[p][dev] = g;
+  return g;
+}
+}  // namespace
+
+int dyn_batch_alloc(DynBatchBuffers& b, uint32_t max_jobs) {
+  b.max_jobs = max_jobs;
+  LJ_CUDA(cudaMalloc(&b.desc_dev, (size_t)max_jobs * sizeof(JoinDesc)));
+  LJ_CUDA(cudaMalloc(&b.item0_dev, (size_t)(max_jobs + 1) * 8));
+  LJ_CUDA(cudaMalloc(&b.comp0_dev, (size_t)(max_jobs + 1) * 8));
+  LJ_CUDA(cudaMallocHost(&b.desc_host, (size_t)max_jobs * sizeof(JoinDesc)));
+  LJ_CUDA(cudaMallocHost(&b.item0_host, (size_t)(max_jobs + 1) * 8));
+  LJ_CUDA(cudaMallocHost(&b.comp0_host, (size_t)(max_jobs + 1) * 8));
+  return 0;
+}
+
+void dyn_batch_release(DynBatchBuffers& b) {
+  if (b.desc_dev) cudaFree(b.desc_dev);
+  if (b.item0_dev) cudaFree(b.item0_dev);
+  if (b.comp0_dev) cudaFree(b.comp0_dev);
+  if (b.desc_host) cudaFreeHost(b.desc_host);
+  if (b.item0_host) cudaFreeHost(b.item0_host);
+  if (b.comp0_host) cudaFreeHost(b.comp0_host);
+  b = DynBatchBuffers{};
+}
+
+size_t dyn_batch_scratch_bytes(const BatchJob* jobs, uint32_t k) { return dyn_layout(jobs, k).total(); }
+
+int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, char* scratch,
+                      uint64_t* written, cudaStream_t s) {
+  if (k == 0) return 0;
+  if (k > buf.max_jobs) return fail(LJ_E_INVAL, "dynamic batch of %u jobs > %u", k, buf.max_jobs);
+  const int prec = jobs[0].idx->precision;
+  const int dev = jobs[0].idx->device;
+  JoinDesc* hd = (JoinDesc*)buf.desc_host;
+  const DynLayout L = dyn_layout(jobs, k);
+  uint64_t words = 0;
+  buf.item0_host[0] = buf.comp0_host[0] = 0;
+  for (uint32_t j = 0; j < k; ++j) {
+    const lj_index* x = jobs[j].idx;
+    if (!x->unique || x->precision != prec)
+      return fail(LJ_E_INVAL, "dynamic batch: job %u needs a unique R of the batch's precision", j);
+    JoinDesc& d = hd[j];
+    d.R = x->R;
+    d.leaves = x->leaves;
+    d.S = jobs[j].S;
+    d.out = jobs[j].out;
+    d.m = jobs[j].m;
+    d.cap = jobs[j].cap;
+    d.words_off = words;
+    d.a0 = prec == LJ_FP64 ? x->root_f64[0] : (double)x->root_f32[0];
+    d.b0 = prec == LJ_FP64 ? x->root_f64[1] : (double)x->root_f32[1];
+    d.L = x->L;
+    d.n = (uint32_t)x->n;
+    d.r32 = (reinterpret_cast<uintptr_t>(x->R) & 31) == 0;
+    d.pad = 0;
+    words += (jobs[j].m + 3) & ~3ull;
+    buf.item0_host[j + 1] = buf.item0_host[j] + (jobs[j].m + kDynItem - 1) / kDynItem;
+    buf.comp0_host[j + 1] = buf.comp0_host[j] + (jobs[j].m + kCompactTile - 1) / kCompactTile;
+  }
+  LJ_CUDA(cudaMemcpyAsync(buf.desc_dev, hd, (size_t)k * sizeof(JoinDesc), cudaMemcpyHostToDevice, s));
+  LJ_CUDA(cudaMemcpyAsync(buf.item0_dev, buf.item0_host, (size_t)(k + 1) * 8, cudaMemcpyHostToDevice, s));
+  LJ_CUDA(cudaMemcpyAsync(buf.comp0_dev, buf.comp0_host, (size_t)(k + 1) * 8, cudaMemcpyHostToDevice, s));
+  char* p = scratch + 256;
+  unsigned long long* counts = (unsigned long long*)p;
+  p += L.b_cnt;
+  TileState st;
+  st.ticket = (uint32_t*)(scratch + 192);
+  st.flag = (uint32_t*)p;
+  p += L.b_flags;
+  const size_t zero = p - scratch;
+  st.agg = (uint64_t*)p;
+  st.incl = st.agg + L.scan_blocks;
+  p += L.b_states;
+  uint64_t* prefix = (uint64_t*)p;
+  p += L.b_pre;
+  uint32_t* wds = (uint32_t*)p;
+  uint32_t* err = device_error_word(dev);
+  if (!err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
+  LJ_CUDA(cudaMemsetAsync(scratch, 0, zero, s));
+  LJ_CUDA(cudaMemsetAsync(written, 0, (size_t)k * 8, s));
+  if (L.tiles == 0) return 0;
+  const JoinDesc* desc = (const JoinDesc*)buf.desc_dev;
+  uint32_t* ticket = (uint32_t*)(scratch + 64);
+  {
+    KernelTimer kt("batch_search_kernel", s);
+    if (prec == LJ_FP64)
+      batch_search_kernel<ModelF64, kDynBlock, kDynChunk><<<dyn_grid(dev, prec), kDynBlock, 0, s>>>(
+          desc, buf.item0_dev, k, L.items, buf.comp0_dev, counts, wds, ticket);
+    else
+      batch_search_kernel<ModelF32, kDynBlock, kDynChunk><<<dyn_grid(dev, prec), kDynBlock, 0, s>>>(
+          desc, buf.item0_dev, k, L.items, buf.comp0_dev, counts, wds, ticket);
+  }
+  LJ_CUDA(cudaGetLastError());
+  tile_scan_kernel<<<L.scan_blocks, kBlock, 0, s>>>(counts, (uint32_t)L.tiles, prefix, st,
+                                                    L.scan_blocks, (uint64_t*)(scratch + 128),
+                                                    nullptr, nullptr, ~0ull, err);
+  LJ_CUDA(cudaGetLastError());
+  {
+    KernelTimer kt("batch_compact_kernel", s);
+    batch_compact_kernel<true><<<(unsigned)L.tiles, kBlock, 0, s>>>(desc, buf.comp0_dev, k, prefix,
+                                                                    wds, written, err);
+  }
+  LJ_CUDA(cudaGetLastError());
+  return 0;
+}
+
 }  // namespace lj
 
 extern "C" {

@@ -66,6 +66,36 @@ class KernelTimer {
 void set_profiling(bool on);
 bool profiling();
 
+// One join of a dynamically formed batch (serving): index (unique R), probe
+// keys (device or page-locked host memory), output pairs and their room.
+struct BatchJob {
+  const lj_index* idx;
+  const uint64_t* S;
+  uint64_t m;
+  lj_pair* out;
+  uint64_t cap;
+};
+
+// Per-slot buffers of dynamic batches: descriptor tables on the device and
+// their page-locked host staging (reused only after the slot's batch ends).
+struct DynBatchBuffers {
+  uint32_t max_jobs = 0;
+  void* desc_dev = nullptr;
+  uint64_t* item0_dev = nullptr;
+  uint64_t* comp0_dev = nullptr;
+  void* desc_host = nullptr;
+  uint64_t* item0_host = nullptr;
+  uint64_t* comp0_host = nullptr;
+};
+int dyn_batch_alloc(DynBatchBuffers& b, uint32_t max_jobs);
+void dyn_batch_release(DynBatchBuffers& b);
+// Scratch bytes a dynamic batch of these jobs needs (4 bytes per probe + tables).
+size_t dyn_batch_scratch_bytes(const BatchJob* jobs, uint32_t k);
+// Enqueue the batched search, scan and compaction of k jobs on s; writes each
+// job's |J| to written_dev[k].  No allocation, no synchronisation.
+int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, char* scratch,
+                      uint64_t* written_dev, cudaStream_t s);
+
 // Probe batches of at most this many keys take the single-pass kernel.
 void set_single_pass_max(uint64_t v);
 uint64_t get_single_pass_max();

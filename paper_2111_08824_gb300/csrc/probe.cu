@@ -165,56 +165,57 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
   }
 }
 
-// Search kernel of the count-scan-emit pipeline: every thread looks up 2K
-// probes (j0 = 2*(t + k*T) + {0, 1}, T threads in the grid) and writes one
-// 32-bit word per probe, with no scan and no barrier, so warps never wait
-// for one another:
+// Search kernel of the count-scan-emit pipeline: block b looks up the CHUNK
+// consecutive tiles of 2*kSearchBlock probes starting at probe
+// b * CHUNK * 2 * kSearchBlock, two probes per thread and tile, and writes one
+// 32-bit word per probe, with no scan, so a warp never waits for a slower one
+// until the end of its block's chunk:
 //   kUniqueCount  out[j] = first matching position, or kNoMatch
 //   kDupCount     out[j] = number of matches
-// Each block also adds its probes' match count to the count of their
-// compaction tile (kCompactTile probes; a block's probes never straddle two).
-template <class Model, int MODE, int K, bool VEC>
+// At the end of the chunk the block adds its probes' match count to the
+// count of their compaction tile (a chunk never straddles two): one barrier
+// and one atomic per chunk (per-warp atomics contended badly).
+template <class Model, int MODE, int CHUNK, bool VEC>
 __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
                         unsigned long long* __restrict__ tile_counts) {
-  static_assert(kCompactTile % (2 * kSearchBlock) == 0, "a block's probes must share a tile");
+  constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * CHUNK;
+  static_assert(kCompactTile % kChunkProbes == 0, "a chunk must lie in one compaction tile");
   __shared__ unsigned long long s_count[kSearchBlock / 32];
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t T = gridDim.x * (uint64_t)blockDim.x;
-  uint32_t r_idx[2 * K], cnt[2 * K];
-  bool valid[2 * K];
-  lookup_probes<Model, MODE, K, VEC, LJ_ENDGAME>(P, 2 * t, (uint32_t)T, r_idx, cnt, valid);
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const uint64_t j0 = 2 * (t + k * T);
+  const uint64_t first = blockIdx.x * kChunkProbes;
+  unsigned long long c = 0;
+#pragma unroll 1
+  for (int t = 0; t < CHUNK; ++t) {
+    const uint64_t j0 = first + (uint64_t)t * 2 * kSearchBlock + 2 * threadIdx.x;
+    if (j0 >= P.m) break;
+    uint32_t r_idx[2], cnt[2];
+    bool valid[2];
+    lookup_probes<Model, MODE, 1, VEC, LJ_ENDGAME>(P, j0, 0, r_idx, cnt, valid);
     uint32_t w0, w1;
     if (MODE == kDupCount) {
-      w0 = cnt[2 * k];
-      w1 = cnt[2 * k + 1];
+      w0 = cnt[0];
+      w1 = cnt[1];
     } else {
-      w0 = cnt[2 * k] ? r_idx[2 * k] : kNoMatch;
-      w1 = cnt[2 * k + 1] ? r_idx[2 * k + 1] : kNoMatch;
+      w0 = cnt[0] ? r_idx[0] : kNoMatch;
+      w1 = cnt[1] ? r_idx[1] : kNoMatch;
     }
-    if (VEC && valid[2 * k + 1]) {
+    if (VEC && valid[1]) {
       *reinterpret_cast<uint2*>(out + j0) = make_uint2(w0, w1);
     } else {
-      if (valid[2 * k]) out[j0] = w0;
-      if (valid[2 * k + 1]) out[j0 + 1] = w1;
+      if (valid[0]) out[j0] = w0;
+      if (valid[1]) out[j0 + 1] = w1;
     }
-    // the block's 2*blockDim probes of this round lie in one compaction tile:
-    // one atomic per block and round (per-warp atomics contended badly)
-    unsigned long long c = (unsigned long long)cnt[2 * k] + cnt[2 * k + 1];
+    c += (unsigned long long)cnt[0] + cnt[1];
+  }
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
-    if ((threadIdx.x & 31) == 0) s_count[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long tot = 0;
+  for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if ((threadIdx.x & 31) == 0) s_count[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
 #pragma unroll
-      for (int w = 0; w < kSearchBlock / 32; ++w) tot += s_count[w];
-      if (tot) atomicAdd(tile_counts + j0 / kCompactTile, tot);
-    }
-    __syncthreads();
+    for (int w = 0; w < kSearchBlock / 32; ++w) tot += s_count[w];
+    if (tot) atomicAdd(tile_counts + first / kCompactTile, tot);
   }
 }
 
@@ -439,16 +440,16 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
   if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   const bool vec = aligned(S, 16);
-  const uint64_t threads = ((m + 1) / 2 + kSearchRounds - 1) / kSearchRounds;
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, (threads + kSearchBlock - 1) / kSearchBlock);
+  constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
   {
     KernelTimer kt("probe_search_kernel", s);
     if (dup)
-      vec ? probe_search_kernel<Model, kDupCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
-          : probe_search_kernel<Model, kDupCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
+      vec ? probe_search_kernel<Model, kDupCount, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
+          : probe_search_kernel<Model, kDupCount, kSearchChunk, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
     else
-      vec ? probe_search_kernel<Model, kUniqueCount, kSearchRounds, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
-          : probe_search_kernel<Model, kUniqueCount, kSearchRounds, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
+      vec ? probe_search_kernel<Model, kUniqueCount, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
+          : probe_search_kernel<Model, kUniqueCount, kSearchChunk, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
   }
   LJ_CUDA(cudaGetLastError());
   {

@@ -48,8 +48,8 @@ struct ProbeParams {
 #ifndef LJ_FAN
 #define LJ_FAN 2           // search fan-out: FAN-1 independent pivots per round
 #endif
-#ifndef LJ_SROUNDS
-#define LJ_SROUNDS 1       // search kernel: probe rounds per thread (2 probes each)
+#ifndef LJ_SCHUNK
+#define LJ_SCHUNK 1        // search kernel: tiles of 2*LJ_SBLOCK probes per block (1 measured best)
 #endif
 #ifndef LJ_SBLOCK
 #define LJ_SBLOCK 128      // search kernel: threads per block
@@ -61,7 +61,7 @@ struct ProbeParams {
 #define LJ_ENDGAME false   // search kernel: resolve the last <= 4 keys in one round (measured slower)
 #endif
 constexpr int kRounds = LJ_ROUNDS;
-constexpr int kSearchRounds = LJ_SROUNDS;
+constexpr int kSearchChunk = LJ_SCHUNK;
 constexpr int kSearchBlock = LJ_SBLOCK;
 constexpr uint32_t kNoMatch = 0xFFFFFFFFu;
 enum { kScanPairs = 0, kScanOffsets = 1 };
