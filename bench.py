@@ -111,6 +111,21 @@ def dist_setup(n_gpus: int):
     return rank, world, local, pg
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Max of a per-rank value over all ranks (the slowest rank's time)."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world: int, units_per_rank: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in the step."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
 def run_reference(args, rank, world):
     """CPU oracle (sort-merge) on bounded samples of the same workload."""
     import oracle
@@ -463,6 +478,12 @@ def main():
     idx = lj.rmi_build(Rd, L, wl.precision)
     st = idx.stats()
     unique = bool(st["unique"])
+    # precision variants: windows re-measured under each model precision
+    windows = {}
+    for prec in ("fp32", "fp64"):
+        s2 = st if prec == wl.precision else lj.rmi_build(Rd, L, prec).stats()
+        windows[prec] = {"mean_window": s2["mean_window"], "max_window": s2["max_window"],
+                         "build_ms": s2["build_ms"]}
     stream = torch.cuda.current_stream()
 
     if unique:
@@ -507,13 +528,9 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = reduce_max(t_start.elapsed_time(t_end), dist, "cuda")
     ms_per_step = elapsed_ms / args.steps
-    value = world * m / (ms_per_step / 1e3)
+    value = weak_value(world, m, ms_per_step)
 
     # ---- end to end through the C ABI with host buffers (pinned): S is read
     # in place by the GPU, pairs are copied out while the next chunk is probed
@@ -553,7 +570,7 @@ def main():
         "pairs": int(total), "pairs_per_s": world * total / (ms_per_step / 1e3),
         "paper_metric_tuples_per_s": world * (n + m) / (ms_per_step / 1e3),
         "build_ms": st["build_ms"], "mean_window": st["mean_window"],
-        "max_window": st["max_window"],
+        "max_window": st["max_window"], "windows_by_precision": windows,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " copy bandwidth (hbm_gbs)",

@@ -373,24 +373,18 @@ unsigned dyn_grid(int dev, int precision) {
 }
 }  // namespace
 
+static size_t dyn_table_bytes(uint32_t k) { return (size_t)k * sizeof(JoinDesc) + 2 * (size_t)(k + 1) * 8; }
+
 int dyn_batch_alloc(DynBatchBuffers& b, uint32_t max_jobs) {
   b.max_jobs = max_jobs;
-  LJ_CUDA(cudaMalloc(&b.desc_dev, (size_t)max_jobs * sizeof(JoinDesc)));
-  LJ_CUDA(cudaMalloc(&b.item0_dev, (size_t)(max_jobs + 1) * 8));
-  LJ_CUDA(cudaMalloc(&b.comp0_dev, (size_t)(max_jobs + 1) * 8));
-  LJ_CUDA(cudaMallocHost(&b.desc_host, (size_t)max_jobs * sizeof(JoinDesc)));
-  LJ_CUDA(cudaMallocHost(&b.item0_host, (size_t)(max_jobs + 1) * 8));
-  LJ_CUDA(cudaMallocHost(&b.comp0_host, (size_t)(max_jobs + 1) * 8));
+  LJ_CUDA(cudaMalloc(&b.dev, dyn_table_bytes(max_jobs)));
+  LJ_CUDA(cudaMallocHost(&b.host, dyn_table_bytes(max_jobs)));
   return 0;
 }
 
 void dyn_batch_release(DynBatchBuffers& b) {
-  if (b.desc_dev) cudaFree(b.desc_dev);
-  if (b.item0_dev) cudaFree(b.item0_dev);
-  if (b.comp0_dev) cudaFree(b.comp0_dev);
-  if (b.desc_host) cudaFreeHost(b.desc_host);
-  if (b.item0_host) cudaFreeHost(b.item0_host);
-  if (b.comp0_host) cudaFreeHost(b.comp0_host);
+  if (b.dev) cudaFree(b.dev);
+  if (b.host) cudaFreeHost(b.host);
   b = DynBatchBuffers{};
 }
 
@@ -402,10 +396,16 @@ int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, ch
   if (k > buf.max_jobs) return fail(LJ_E_INVAL, "dynamic batch of %u jobs > %u", k, buf.max_jobs);
   const int prec = jobs[0].idx->precision;
   const int dev = jobs[0].idx->device;
-  JoinDesc* hd = (JoinDesc*)buf.desc_host;
+  // tables for k jobs, packed: descriptors | item0[k+1] | comp0[k+1]
+  JoinDesc* hd = (JoinDesc*)buf.host;
+  uint64_t* item0_host = (uint64_t*)(buf.host + (size_t)k * sizeof(JoinDesc));
+  uint64_t* comp0_host = item0_host + (k + 1);
+  const JoinDesc* desc = (const JoinDesc*)buf.dev;
+  const uint64_t* item0_dev = (const uint64_t*)(buf.dev + (size_t)k * sizeof(JoinDesc));
+  const uint64_t* comp0_dev = item0_dev + (k + 1);
   const DynLayout L = dyn_layout(jobs, k);
   uint64_t words = 0;
-  buf.item0_host[0] = buf.comp0_host[0] = 0;
+  item0_host[0] = comp0_host[0] = 0;
   for (uint32_t j = 0; j < k; ++j) {
     const lj_index* x = jobs[j].idx;
     if (!x->unique || x->precision != prec)
@@ -425,12 +425,10 @@ int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, ch
     d.r32 = (reinterpret_cast<uintptr_t>(x->R) & 31) == 0;
     d.pad = 0;
     words += (jobs[j].m + 3) & ~3ull;
-    buf.item0_host[j + 1] = buf.item0_host[j] + (jobs[j].m + kDynItem - 1) / kDynItem;
-    buf.comp0_host[j + 1] = buf.comp0_host[j] + (jobs[j].m + kCompactTile - 1) / kCompactTile;
+    item0_host[j + 1] = item0_host[j] + (jobs[j].m + kDynItem - 1) / kDynItem;
+    comp0_host[j + 1] = comp0_host[j] + (jobs[j].m + kCompactTile - 1) / kCompactTile;
   }
-  LJ_CUDA(cudaMemcpyAsync(buf.desc_dev, hd, (size_t)k * sizeof(JoinDesc), cudaMemcpyHostToDevice, s));
-  LJ_CUDA(cudaMemcpyAsync(buf.item0_dev, buf.item0_host, (size_t)(k + 1) * 8, cudaMemcpyHostToDevice, s));
-  LJ_CUDA(cudaMemcpyAsync(buf.comp0_dev, buf.comp0_host, (size_t)(k + 1) * 8, cudaMemcpyHostToDevice, s));
+  LJ_CUDA(cudaMemcpyAsync(buf.dev, buf.host, dyn_table_bytes(k), cudaMemcpyHostToDevice, s));
   char* p = scratch + 256;
   unsigned long long* counts = (unsigned long long*)p;
   p += L.b_cnt;
@@ -450,16 +448,15 @@ int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, ch
   LJ_CUDA(cudaMemsetAsync(scratch, 0, zero, s));
   LJ_CUDA(cudaMemsetAsync(written, 0, (size_t)k * 8, s));
   if (L.tiles == 0) return 0;
-  const JoinDesc* desc = (const JoinDesc*)buf.desc_dev;
   uint32_t* ticket = (uint32_t*)(scratch + 64);
   {
     KernelTimer kt("batch_search_kernel", s);
     if (prec == LJ_FP64)
       batch_search_kernel<ModelF64, kDynBlock, kDynChunk><<<dyn_grid(dev, prec), kDynBlock, 0, s>>>(
-          desc, buf.item0_dev, k, L.items, buf.comp0_dev, counts, wds, ticket);
+          desc, item0_dev, k, L.items, comp0_dev, counts, wds, ticket);
     else
       batch_search_kernel<ModelF32, kDynBlock, kDynChunk><<<dyn_grid(dev, prec), kDynBlock, 0, s>>>(
-          desc, buf.item0_dev, k, L.items, buf.comp0_dev, counts, wds, ticket);
+          desc, item0_dev, k, L.items, comp0_dev, counts, wds, ticket);
   }
   LJ_CUDA(cudaGetLastError());
   tile_scan_kernel<<<L.scan_blocks, kBlock, 0, s>>>(counts, (uint32_t)L.tiles, prefix, st,
@@ -468,7 +465,7 @@ int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, ch
   LJ_CUDA(cudaGetLastError());
   {
     KernelTimer kt("batch_compact_kernel", s);
-    batch_compact_kernel<true><<<(unsigned)L.tiles, kBlock, 0, s>>>(desc, buf.comp0_dev, k, prefix,
+    batch_compact_kernel<true><<<(unsigned)L.tiles, kBlock, 0, s>>>(desc, comp0_dev, k, prefix,
                                                                     wds, written, err);
   }
   LJ_CUDA(cudaGetLastError());

@@ -80,12 +80,8 @@ struct BatchJob {
 // their page-locked host staging (reused only after the slot's batch ends).
 struct DynBatchBuffers {
   uint32_t max_jobs = 0;
-  void* desc_dev = nullptr;
-  uint64_t* item0_dev = nullptr;
-  uint64_t* comp0_dev = nullptr;
-  void* desc_host = nullptr;
-  uint64_t* item0_host = nullptr;
-  uint64_t* comp0_host = nullptr;
+  char* dev = nullptr;    // descriptors, then the two tile tables (one upload)
+  char* host = nullptr;   // page-locked staging with the same layout
 };
 int dyn_batch_alloc(DynBatchBuffers& b, uint32_t max_jobs);
 void dyn_batch_release(DynBatchBuffers& b);

@@ -14,10 +14,12 @@
 //               admitted into the next free slot, so batches overlap on the
 //               device (continuous batching, not a queue in front of a
 //               single worker).
-//   completion  the scheduler polls each slot's event; a finished batch
+//   completion  a host callback enqueued behind each batch wakes the
+//               scheduler, which checks the slot's event; a finished batch
 //               releases its scratch and wakes the waiting clients.
 // Latency of a request = submit to completion detected (host clock).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -70,6 +72,7 @@ struct lj_server {
   uint64_t next_id = 1;
   uint64_t mem_in_use = 0, mem_peak = 0;
   bool stop = false;
+  std::atomic<bool> wake{false};   // set by the completion callbacks
   std::thread sched;
   // statistics
   std::vector<double> lat_us;
@@ -99,6 +102,13 @@ void complete_slot(lj_server* sv, Slot& sl) {
   sl.busy = false;
 }
 
+// Host callback enqueued after each batch: wakes the scheduler (no CUDA calls).
+void CUDART_CB on_batch_done(void* p) {
+  lj_server* sv = static_cast<lj_server*>(p);
+  sv->wake.store(true);
+  sv->cv_sched.notify_one();
+}
+
 // Launch the admitted requests `batch` on slot `sl` (called with sv->mu held).
 int launch_slot(lj_server* sv, Slot& sl, std::vector<Request*>& batch) {
   std::vector<lj::BatchJob> jobs(batch.size());
@@ -119,7 +129,8 @@ int launch_slot(lj_server* sv, Slot& sl, std::vector<Request*>& batch) {
     return rc;
   if (cudaMemcpyAsync(sl.written_host, sl.written_dev, jobs.size() * 8, cudaMemcpyDeviceToHost,
                       sl.stream) != cudaSuccess ||
-      cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
+      cudaEventRecord(sl.done, sl.stream) != cudaSuccess ||
+      cudaLaunchHostFunc(sl.stream, on_batch_done, sv) != cudaSuccess)
     return lj::fail(LJ_E_CUDA, "server: cannot enqueue the completion of a batch");
   sl.reqs = batch;
   sl.busy = true;
@@ -172,7 +183,11 @@ void scheduler(lj_server* sv) {
       for (Slot& sl : sv->slots) idle = idle && !sl.busy;
       if (idle) break;
     }
-    if (!progressed) sv->cv_sched.wait_for(lk, std::chrono::microseconds(20));
+    // sleep until a submission or a batch completion (callback) wakes us;
+    // the timeout only guards against a wake-up lost between check and wait
+    if (!progressed)
+      sv->cv_sched.wait_for(lk, std::chrono::microseconds(200),
+                            [&] { return sv->wake.exchange(false) || sv->stop; });
   }
 }
 
@@ -259,6 +274,7 @@ int join_submit(lj_server* sv, uint32_t rel_id, const uint64_t* S, uint64_t m, l
     sv->pending.push_back(r);
     *out = r->id;
   }
+  sv->wake.store(true);
   sv->cv_sched.notify_one();
   return LJ_OK;
 }
@@ -312,6 +328,7 @@ int join_release(lj_server* sv, lj_ticket t) {
   if (r->status == 0) sv->mem_in_use -= r->need - r->m * 4;
   sv->reqs.erase(it);
   delete r;
+  sv->wake.store(true);
   sv->cv_sched.notify_one();
   return LJ_OK;
 }
