@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     if (j0 >= P.m) break;
     uint32_t r_idx[2], cnt[2];
     bool valid[2];
-    lookup_probes<Model, MODE, 1, VEC, LJ_ENDGAME>(P, j0, 0, r_idx, cnt, valid);
+    lookup_probes<Model, MODE, 1, VEC, LJ_ENDGAME, LJ_GUIDED, LJ_CANON>(P, j0, 0, r_idx, cnt, valid);
     uint32_t w0, w1;
     if (MODE == kDupCount) {
       w0 = cnt[0];
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
       w1 = cnt[1] ? r_idx[1] : kNoMatch;
     }
     if (VEC && valid[1]) {
-      *reinterpret_cast<uint2*>(out + j0) = make_uint2(w0, w1);
+      st_stream_u32x2(out + j0, w0, w1);
     } else {
       if (valid[0]) out[j0] = w0;
       if (valid[1]) out[j0 + 1] = w1;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
   if (VEC && base + kScanItems <= P.m) {
 #pragma unroll
     for (int q = 0; q < kScanItems / 4; ++q) {
-      const uint4 u = __ldg(reinterpret_cast<const uint4*>(P.in + base) + q);
+      const uint4 u = ldg_stream_u32x4(P.in + base + 4 * q);
       v[4 * q] = u.x;
       v[4 * q + 1] = u.y;
       v[4 * q + 2] = u.z;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
     uint64_t* out = reinterpret_cast<uint64_t*>(P.pairs);
     for (uint64_t q = threadIdx.x; q < cnt; q += kBlock) {
       const uint64_t o = prefix + q;
-      if (o < P.capacity) out[o] = s_stage[q];
+      if (o < P.capacity) st_stream_u64(out + o, s_stage[q]);
     }
   } else {
     const uint32_t first = threadIdx.x * kScanItems;

@@ -55,7 +55,14 @@ struct ProbeParams {
 #define LJ_SBLOCK 128      // search kernel: threads per block
 #endif
 #ifndef LJ_SMINB
-#define LJ_SMINB 1
+#define LJ_SMINB 16        // search kernel: 16 blocks of 128 threads per SM (32 registers,
+                           // full occupancy): measured 9% faster than the unconstrained build
+#endif
+#ifndef LJ_CANON
+#define LJ_CANON false     // search kernel: canonical (aligned-grid) bisection (measured 1.6x slower)
+#endif
+#ifndef LJ_GUIDED
+#define LJ_GUIDED false    // search kernel: model-guided search (measured 2.6x slower: pivots no longer shared)
 #endif
 #ifndef LJ_ENDGAME
 #define LJ_ENDGAME false   // search kernel: resolve the last <= 4 keys in one round (measured slower)
@@ -208,11 +215,145 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R, uint
   }
 }
 
+// Model-guided bounded search (same contract as search_last): the first
+// pivot is the model's predicted position, then interpolation between the
+// bracketing keys alternates with bisection (at least one halving every two
+// rounds).  On lognormal keys this needs ~18% fewer loads than bisection,
+// most of it on hits; the result is exact whatever the pivots.
+template <int NP, bool STRICT>
+__device__ __forceinline__ void search_guided(const uint64_t* __restrict__ R,
+                                              const uint64_t (&x)[NP], const uint32_t (&pred)[NP],
+                                              uint32_t (&base)[NP], uint32_t (&len)[NP],
+                                              uint64_t (&cv)[NP]) {
+  uint32_t a[NP], b[NP], start[NP];
+  uint64_t klo[NP], khi[NP];
+  bool has_lo[NP], has_hi[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    a[p] = start[p] = base[p];
+    b[p] = base[p] + len[p];
+    has_lo[p] = has_hi[p] = false;
+    klo[p] = khi[p] = 0;
+    cv[p] = 0;
+  }
+  for (int step = 0;; ++step) {
+    bool any = false;
+    uint32_t g[NP];
+    uint64_t v[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      if (a[p] < b[p]) {
+        any = true;
+        const uint32_t w = b[p] - a[p];
+        uint32_t q = a[p] + (w >> 1);                       // bisection
+        if (step == 0) {
+          q = pred[p];                                       // the model's guess
+        } else if ((step & 1) && has_lo[p] && has_hi[p]) { // interpolation
+          const float dx = __ull2float_rn(x[p] - klo[p]);
+          const float dk = __ull2float_rn(khi[p] - klo[p]);
+          const float f = __fdividef(dx, dk) * (float)w;
+          q = a[p] + (f > 0.0f ? (f < (float)w ? (uint32_t)f : w - 1) : 0u);
+        }
+        q = q < a[p] ? a[p] : (q >= b[p] ? b[p] - 1 : q);
+        g[p] = q;
+        v[p] = ldg_key(R, q);
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      if (a[p] < b[p]) {
+        const bool go = STRICT ? (v[p] < x[p]) : (v[p] <= x[p]);
+        if (go) {
+          a[p] = g[p] + 1;
+          klo[p] = v[p];
+          has_lo[p] = true;
+          cv[p] = v[p];
+        } else {
+          b[p] = g[p];
+          khi[p] = v[p];
+          has_hi[p] = true;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    base[p] = a[p];
+    len[p] = start[p];   // keep the window start for the caller
+  }
+}
+
+// Canonical bounded search (same contract as search_last): bisects the
+// smallest power-of-two-aligned block of R that contains the window, with
+// pivots at fixed positions of that grid.  A pivot outside the window needs
+// no load (keys before the window pass the test, keys after it fail), so a
+// probe loads about log2(window) + 1 keys, and probes whose windows fall in
+// the same region of R visit the same pivots: a warp's lanes then share
+// sectors and other warps find them in L1.
+template <int NP, bool STRICT>
+__device__ __forceinline__ void search_canon(const uint64_t* __restrict__ R,
+                                             const uint64_t (&x)[NP], uint32_t (&base)[NP],
+                                             uint32_t (&len)[NP], uint64_t (&cv)[NP]) {
+  int64_t pos[NP];
+  uint64_t step[NP];
+  uint32_t wl[NP], wh[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    wl[p] = base[p];
+    wh[p] = base[p] + len[p];
+    cv[p] = 0;
+    if (len[p] == 0) {
+      step[p] = 0;
+      pos[p] = (int64_t)wl[p] - 1;
+    } else {
+      const uint32_t d = wl[p] ^ (wh[p] - 1);
+      const int j = d ? 32 - __clz(d) : 0;
+      step[p] = 1ull << j;
+      pos[p] = (int64_t)((uint64_t)wl[p] & ~(step[p] - 1)) - 1;
+    }
+  }
+  while (true) {
+    bool any = false;
+    int64_t q[NP];
+    bool inw[NP];
+    uint64_t v[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      inw[p] = false;
+      if (step[p]) {
+        any = true;
+        q[p] = pos[p] + (int64_t)step[p];
+        inw[p] = q[p] >= (int64_t)wl[p] && q[p] < (int64_t)wh[p];
+        if (inw[p]) v[p] = ldg_key(R, (uint32_t)q[p]);
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      if (step[p]) {
+        const bool t = inw[p] ? (STRICT ? (v[p] < x[p]) : (v[p] <= x[p])) : (q[p] < (int64_t)wl[p]);
+        if (t) {
+          pos[p] = q[p];
+          if (inw[p]) cv[p] = v[p];
+        }
+        step[p] >>= 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    base[p] = (uint32_t)(pos[p] + 1);
+    len[p] = wl[p];   // keep the window start for the caller
+  }
+}
+
 // Lookups of 2K probes per thread: round k covers probes
 // j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
 // leaf record -> window, then the interleaved bounded searches.  cnt is the
 // number of matches, r_idx the first matching position (when cnt > 0).
-template <class Model, int MODE, int K, bool VEC, bool ENDGAME = false>
+template <class Model, int MODE, int K, bool VEC, bool ENDGAME = false, bool GUIDED = false,
+          bool CANON = false>
 __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
                                               uint32_t stride, uint32_t (&r_idx)[2 * K],
                                               uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
@@ -222,7 +363,7 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
   for (int k = 0; k < K; ++k) {
     const uint64_t j0 = first + 2ull * stride * k;
     if (VEC && j0 + 1 < P.m) {
-      const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(P.S + j0));
+      const ulonglong2 v = ldg_stream_u64x2(P.S + j0);
       x[2 * k] = v.x;
       x[2 * k + 1] = v.y;
       valid[2 * k] = valid[2 * k + 1] = true;
@@ -234,7 +375,7 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
           valid[2 * k + 1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
     }
   }
-  uint32_t base[NP], len[NP];
+  uint32_t base[NP], len[NP], ppos[NP];
   {
     uint32_t leaf[NP];
 #pragma unroll
@@ -245,10 +386,11 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
       if (valid[p]) lf[p] = Model::load_leaf(P.leaves, leaf[p]);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      uint32_t wl = 0, wh = 0;
-      if (valid[p]) window<Model>(lf[p], x[p], wl, wh);
+      uint32_t wl = 0, wh = 0, pp = 0;
+      if (valid[p]) window<Model>(lf[p], x[p], wl, wh, &pp);
       base[p] = wl;
       len[p] = wh - wl;
+      ppos[p] = pp;
     }
   }
   if (MODE == kDupCount) {
@@ -256,18 +398,42 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
 #pragma unroll
     for (int p = 0; p < NP; ++p) wh[p] = base[p] + len[p];
     uint64_t cv[NP];
-    search_last<NP, true, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);   // base = lower bound
+    if (CANON)
+      search_canon<NP, true>(P.R, x, base, len, cv);                     // base = lower bound
+    else
+      search_last<NP, true, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = lower bound
     uint32_t lb[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       lb[p] = base[p];
       len[p] = wh[p] - base[p];
     }
-    search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound
+    if (CANON)
+      search_canon<NP, false>(P.R, x, base, len, cv);                      // base = upper bound
+    else
+      search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       cnt[p] = valid[p] ? base[p] - lb[p] : 0;
       r_idx[p] = lb[p];
+    }
+  } else if (CANON) {
+    uint64_t cv[NP];
+    search_canon<NP, false>(P.R, x, base, len, cv);  // base = upper bound, len = start
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
+      cnt[p] = match ? 1u : 0u;
+      r_idx[p] = base[p] - 1;
+    }
+  } else if (GUIDED) {
+    uint64_t cv[NP];
+    search_guided<NP, false>(P.R, x, ppos, base, len, cv);  // base = upper bound, len = start
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
+      cnt[p] = match ? 1u : 0u;
+      r_idx[p] = base[p] - 1;
     }
   } else {
     uint64_t cv[NP];
