@@ -352,6 +352,8 @@ void join_server_destroy(lj_server* server);
  *                      launch); larger ones use the count-scan-emit pipeline
  *                      (search kernel, then a streaming scan).  Default 2^20.
  *                      Both paths give identical results.
+ *   "host_chunk"       probe keys per chunk of join_host (2^16 .. 2^32-1;
+ *                      default 2^25).
  *   "profile"          1: record CUDA events around every kernel the library
  *                      launches (on the launch's stream); lj_profile_report
  *                      returns the per-kernel totals.  0 (default): off.

@@ -143,6 +143,12 @@ int lj_set_option(const char* name, int64_t value) {
     set_profiling(value != 0);
     return LJ_OK;
   }
+  if (!strcmp(name, "host_chunk")) {
+    if (value < (1 << 16) || value >= (1ll << 32))
+      return fail(LJ_E_INVAL, "host_chunk must be in [2^16, 2^32)");
+    set_host_chunk((uint64_t)value);
+    return LJ_OK;
+  }
   return fail(LJ_E_INVAL, "lj_set_option: unknown option '%s'", name);
 }
 
@@ -150,6 +156,7 @@ int64_t lj_get_option(const char* name) {
   using namespace lj;
   if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
   if (name && !strcmp(name, "profile")) return profiling() ? 1 : 0;
+  if (name && !strcmp(name, "host_chunk")) return (int64_t)get_host_chunk();
   fail(LJ_E_INVAL, "lj_get_option: unknown option '%s'", name ? name : "(null)");
   return -1;
 }

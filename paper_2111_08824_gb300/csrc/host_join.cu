@@ -27,17 +27,27 @@ int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const ui
 namespace {
 
 struct Streams {
-  cudaStream_t in = nullptr, out = nullptr;
+  cudaStream_t in = nullptr, out[2] = {nullptr, nullptr};
   cudaEvent_t ev[8] = {};
   ~Streams() {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
     if (in) cudaStreamDestroy(in);
-    if (out) cudaStreamDestroy(out);
+    for (auto& o : out)
+      if (o) cudaStreamDestroy(o);
   }
 };
 
-constexpr uint64_t kHostChunk = 1ull << 25;   // 32M keys = 256 MB per chunk
+}  // namespace
+
+namespace lj {
+// probe keys per chunk of a host join (option "host_chunk")
+uint64_t g_host_chunk = 1ull << 25;
+void set_host_chunk(uint64_t v) { g_host_chunk = v; }
+uint64_t get_host_chunk() { return g_host_chunk; }
+}  // namespace lj
+
+namespace {
 
 }  // namespace
 
@@ -56,12 +66,13 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
   }
   Streams st;
   LJ_CUDA(cudaStreamCreateWithFlags(&st.in, cudaStreamNonBlocking));
-  LJ_CUDA(cudaStreamCreateWithFlags(&st.out, cudaStreamNonBlocking));
+  LJ_CUDA(cudaStreamCreateWithFlags(&st.out[0], cudaStreamNonBlocking));
+  LJ_CUDA(cudaStreamCreateWithFlags(&st.out[1], cudaStreamNonBlocking));
   for (auto& e : st.ev) LJ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   cudaEvent_t* in_done = st.ev;        // [2]
   cudaEvent_t* comp_done = st.ev + 2;  // [2]
   cudaEvent_t* out_done = st.ev + 4;   // [2]
-  const uint64_t chunk = std::min<uint64_t>(m, kHostChunk);
+  const uint64_t chunk = std::min<uint64_t>(m, std::max<uint64_t>(g_host_chunk, 1u << 16));
   const uint64_t nchunks = (m + chunk - 1) / chunk;
   uint64_t written = 0;
   // page-locked (or registered) S can be read by the kernels in place
@@ -117,13 +128,15 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
       const uint64_t cnt = tot_h[b];
       const uint64_t room = capacity > written ? capacity - written : 0;
       const uint64_t take = std::min(cnt, room);
-      cudaStreamWaitEvent(st.out, comp_done[b], 0);
+      // copy-outs alternate between two streams so consecutive ones overlap
+      cudaStreamWaitEvent(st.out[b], comp_done[b], 0);
       if (take)
-        cudaMemcpyAsync(pairs_host + written, Pd[b], take * 8, cudaMemcpyDeviceToHost, st.out);
-      cudaEventRecord(out_done[b], st.out);
+        cudaMemcpyAsync(pairs_host + written, Pd[b], take * 8, cudaMemcpyDeviceToHost, st.out[b]);
+      cudaEventRecord(out_done[b], st.out[b]);
       written += cnt;
     }
-    cudaStreamSynchronize(st.out);
+    cudaStreamSynchronize(st.out[0]);
+    cudaStreamSynchronize(st.out[1]);
     cudaStreamSynchronize(s);
     scratch_free(ws, s);
     cudaStreamSynchronize(s);

@@ -92,6 +92,10 @@ size_t dyn_batch_scratch_bytes(const BatchJob* jobs, uint32_t k);
 int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, char* scratch,
                       uint64_t* written_dev, cudaStream_t s);
 
+// Probe keys per chunk of join_host.
+void set_host_chunk(uint64_t v);
+uint64_t get_host_chunk();
+
 // Probe batches of at most this many keys take the single-pass kernel.
 void set_single_pass_max(uint64_t v);
 uint64_t get_single_pass_max();
