@@ -178,6 +178,9 @@ def _config(args, wl):
                 wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
 
 
+KERNEL_SOURCES = ("device_common.cuh", "probe_core.cuh", "probe.cu")
+
+
 def _ncu_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel sources (else None)."""
@@ -189,7 +192,7 @@ def _ncu_traffic(kernel: str):
         d = json.load(f)
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2111_08824_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES:           # the files the probe kernels are built from
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     if d.get("csrc_sha256") != h.hexdigest():
