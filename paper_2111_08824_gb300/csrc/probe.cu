@@ -443,6 +443,16 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
   {
+    if (LJ_CARVEOUT >= 0) {
+      static bool once = [] {
+        cudaFuncSetAttribute(probe_search_kernel<Model, kDupCount, kSearchChunk, true>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
+        cudaFuncSetAttribute(probe_search_kernel<Model, kDupCount, kSearchChunk, false>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
+        cudaFuncSetAttribute(probe_search_kernel<Model, kUniqueCount, kSearchChunk, true>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
+        cudaFuncSetAttribute(probe_search_kernel<Model, kUniqueCount, kSearchChunk, false>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
+        return true;
+      }();
+      (void)once;
+    }
     KernelTimer kt("probe_search_kernel", s);
     if (dup)
       vec ? probe_search_kernel<Model, kDupCount, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)

@@ -64,6 +64,9 @@ struct ProbeParams {
 #ifndef LJ_GUIDED
 #define LJ_GUIDED false    // search kernel: model-guided search (measured 2.6x slower: pivots no longer shared)
 #endif
+#ifndef LJ_CARVEOUT
+#define LJ_CARVEOUT -1     // search kernel: preferred shared-memory carveout in percent (-1: driver default)
+#endif
 #ifndef LJ_ENDGAME
 #define LJ_ENDGAME false   // search kernel: resolve the last <= 4 keys in one round (measured slower)
 #endif
