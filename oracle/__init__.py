@@ -15,6 +15,9 @@ Learned In-Memory Joins"):
                              Section 6.B (duplicates return all matches)
   rmi_fit / rmi_lookup       Section 2.D (two-level RMI with per-leaf
                              min/max error bounds and a bounded search)
+  grmi_build / grmi_join     Section 3.A (gapped RMI: model-based insertion
+                             into gapped key and payload arrays, lookup by
+                             exponential search from the predicted slot)
 """
 from __future__ import annotations
 
@@ -67,6 +70,16 @@ def _load():
             lib.lj_oracle_rmi_lookup.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int,
                                                  P, P, P, P, U64, P, P, P, P]
             lib.lj_oracle_rmi_lookup.restype = ctypes.c_uint32
+            lib.lj_oracle_grmi_pslot.argtypes = [P, ctypes.c_uint32, ctypes.c_int, P, P, P,
+                                                 ctypes.c_uint32, U64]
+            lib.lj_oracle_grmi_pslot.restype = U64
+            lib.lj_oracle_grmi_build.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int, P, P, P,
+                                                 ctypes.c_uint32, P, P, U64, P]
+            lib.lj_oracle_grmi_build.restype = ctypes.c_int64
+            lib.lj_oracle_grmi_join_ranges.argtypes = [P, ctypes.c_uint32, ctypes.c_int, P, P,
+                                                       P, ctypes.c_uint32, P, P, U64, P, U64,
+                                                       P, P, P]
+            lib.lj_oracle_grmi_join_ranges.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -169,3 +182,55 @@ def rmi_lookup(R, rmi: RMI, x: int) -> dict:
         _ptr(rmi.leaf_dep), _ptr(rmi.err), int(x), *[ctypes.byref(o) for o in out])
     lb, ub, wl, wh = (o.value for o in out)
     return {"leaf": int(leaf), "lb": lb, "ub": ub, "w_lo": wl, "w_hi": wh}
+
+
+@dataclass
+class GRMI:
+    """Gapped arrays of a GRMI (oracle side): C slots of keys, C+1 payloads
+    (positions in R; pos[C] = n), and the slot every key of R took."""
+    rmi: RMI
+    gaps: int
+    keys: np.ndarray       # (C,) uint64
+    pos: np.ndarray        # (C+1,) uint32
+    slot_of_key: np.ndarray  # (n,) uint64
+
+
+def grmi_pslot(R, rmi: RMI, gaps: int, x: int) -> int:
+    """Predicted slot of one key (before clamping to the array length)."""
+    R = _u64(R)
+    return int(_load().lj_oracle_grmi_pslot(_ptr(R), rmi.L, int(rmi.fp64), _ptr(rmi.root_dep),
+                                            _ptr(rmi.leaf_lo), _ptr(rmi.leaf_dep), gaps, int(x)))
+
+
+def grmi_build(R, rmi: RMI, gaps: int) -> GRMI:
+    """Model-based insertion of sorted R into the gapped arrays."""
+    R = _u64(R)
+    lib = _load()
+    args = (_ptr(R), R.size, rmi.L, int(rmi.fp64), _ptr(rmi.root_dep), _ptr(rmi.leaf_lo),
+            _ptr(rmi.leaf_dep), gaps)
+    C = lib.lj_oracle_grmi_build(*args, None, None, 0, None)
+    if C == -1:
+        raise OracleError("R is not sorted non-decreasing")
+    if C < 0:
+        raise MemoryError("oracle ran out of memory")
+    keys = np.zeros(C, dtype=np.uint64)
+    pos = np.zeros(C + 1, dtype=np.uint32)
+    slot = np.zeros(R.size, dtype=np.uint64)
+    rc = lib.lj_oracle_grmi_build(*args, _ptr(keys), _ptr(pos), C, _ptr(slot))
+    if rc != C:
+        raise OracleError(f"gapped build failed ({rc})")
+    return GRMI(rmi, gaps, keys, pos, slot)
+
+
+def grmi_join(R, g: GRMI, S) -> tuple[np.ndarray, np.ndarray, int, np.ndarray]:
+    """Per-probe match ranges [lo_j, hi_j) found through the GRMI, |J|, and
+    the number of keys each probe's searches read."""
+    R, S = _u64(R), _u64(S)
+    lo = np.zeros(S.size, dtype=np.uint64)
+    hi = np.zeros(S.size, dtype=np.uint64)
+    loads = np.zeros(S.size, dtype=np.uint64)
+    r = g.rmi
+    total = _load().lj_oracle_grmi_join_ranges(
+        _ptr(R), r.L, int(r.fp64), _ptr(r.root_dep), _ptr(r.leaf_lo), _ptr(r.leaf_dep), g.gaps,
+        _ptr(g.keys), _ptr(g.pos), g.keys.size, _ptr(S), S.size, _ptr(lo), _ptr(hi), _ptr(loads))
+    return lo, hi, int(total), loads

@@ -320,3 +320,143 @@ uint32_t lj_oracle_rmi_lookup(const uint64_t* R, uint64_t n, uint32_t L, int fp6
   (void)n;
   return l;
 }
+
+/* ------------------------------------------------- gapped RMI (3.A) ---- */
+/*
+ * Gapped RMI (Section 3.A, "Gapped RMI (GRMI)"): a typical RMI fitted over R
+ * places every tuple of R, in key order, by model-based insertion into two
+ * gapped arrays, one of keys and one of payloads; a lookup predicts a slot
+ * with the same RMI and finishes with an exponential search.  The payload of
+ * a key is its position in the sorted R (the join's r_idx).  Readings (the
+ * paper gives no formulas):
+ *   slots:     (1 + gaps) per key of R; the predicted slot of key x is
+ *              (1 + gaps) * p(x), p(x) the RMI's predicted position (root ->
+ *              leaf -> leaf model, the arithmetic of rmi_fit/rmi_lookup)
+ *              clamped to the leaf's positions [lo_l, hi_l];
+ *   insertion: keys in sorted order; a key takes its predicted slot when that
+ *              slot comes after the slot of the previous key, else the first
+ *              slot after it; the arrays have C = max((1 + gaps) * n,
+ *              last slot + 1) slots;
+ *   gaps:      a gap holds a copy of the next filled slot's key and payload
+ *              (slots after the last key hold 2^64-1 and n), so the key array
+ *              is sorted and a search needs no bitmap; pos[C] = n;
+ *   lookup:    no key >= x is ever placed before x's predicted slot q (the
+ *              model is monotone and insertion only moves keys to later
+ *              slots), so the search runs from q to later slots: keys at
+ *              q, q+1, q+3, q+7, ... until one is >= x, then a binary search
+ *              in the last gap of that sequence.  The first slot with a key
+ *              >= x holds, as payload, the position of the first key of R
+ *              that is >= x (the lower bound); the first slot with a key > x
+ *              gives the upper bound.
+ */
+
+/* Predicted slot of key x (before clamping to C). */
+uint64_t lj_oracle_grmi_pslot(const uint64_t* R, uint32_t L, int fp64, const double* root_dep,
+                              const uint64_t* leaf_lo, const double* leaf_dep, uint32_t gaps,
+                              uint64_t x) {
+  uint32_t l = root_leaf(x, root_dep[0], root_dep[1], L, fp64);
+  int64_t lo = (int64_t)leaf_lo[l], hi = (int64_t)leaf_lo[l + 1];
+  int64_t p = lo;
+  if (hi > lo) p = lo + leaf_pred(x, R[lo], leaf_dep[2 * l], leaf_dep[2 * l + 1], fp64);
+  if (p < lo) p = lo;
+  if (p > hi) p = hi;
+  return (uint64_t)p * (uint64_t)(1 + gaps);
+}
+
+/*
+ * Model-based insertion of the n keys of sorted R.  Returns C, the number of
+ * slots (with keys == NULL only C is computed); fills keys[C] and pos[C + 1]
+ * when cap >= C and, if slot_of_key is not NULL, the slot of every key.
+ * Returns -1 if R is not sorted, -2 if memory runs out, -3 if cap < C.
+ */
+int64_t lj_oracle_grmi_build(const uint64_t* R, uint64_t n, uint32_t L, int fp64,
+                             const double* root_dep, const uint64_t* leaf_lo,
+                             const double* leaf_dep, uint32_t gaps, uint64_t* keys,
+                             uint32_t* pos, uint64_t cap, uint64_t* slot_of_key) {
+  if (!lj_oracle_is_sorted(R, n)) return -1;
+  uint64_t* slot = (uint64_t*)malloc(sizeof(uint64_t) * (n ? n : 1));
+  if (!slot) return -2;
+  /* insert in key order: predicted slot, or the first slot after the previous key */
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t s = lj_oracle_grmi_pslot(R, L, fp64, root_dep, leaf_lo, leaf_dep, gaps, R[i]);
+    if (i > 0 && s <= slot[i - 1]) s = slot[i - 1] + 1;
+    slot[i] = s;
+  }
+  uint64_t C = (uint64_t)(1 + gaps) * n;
+  if (n > 0 && slot[n - 1] + 1 > C) C = slot[n - 1] + 1;
+  if (keys) {
+    if (cap < C) {
+      free(slot);
+      return -3;
+    }
+    /* from the end: every slot takes the next filled slot's key and payload */
+    uint64_t next_key = UINT64_MAX;
+    uint32_t next_pos = (uint32_t)n;
+    uint64_t i = n;
+    for (uint64_t s = C; s-- > 0;) {
+      if (i > 0 && slot[i - 1] == s) {
+        --i;
+        next_key = R[i];
+        next_pos = (uint32_t)i;
+      }
+      keys[s] = next_key;
+      pos[s] = next_pos;
+    }
+    pos[C] = (uint32_t)n;
+  }
+  if (slot_of_key) memcpy(slot_of_key, slot, sizeof(uint64_t) * n);
+  free(slot);
+  return (int64_t)C;
+}
+
+/* First slot at or after q whose key is >= x (strict: > x), or C. */
+static uint64_t grmi_first(const uint64_t* keys, uint64_t C, uint64_t x, uint64_t q, int strict,
+                           uint64_t* loads) {
+  if (q >= C) return C;
+  uint64_t lo = q, hi = C, off = 0;
+  for (;;) { /* exponential phase: q, q+1, q+3, q+7, ... */
+    uint64_t t = q + off;
+    if (t >= C) break;
+    ++*loads;
+    if (strict ? keys[t] > x : keys[t] >= x) {
+      hi = t;
+      break;
+    }
+    lo = t + 1;
+    off = 2 * off + 1;
+  }
+  while (lo < hi) { /* binary search in [lo, hi) */
+    uint64_t mid = lo + (hi - lo) / 2;
+    ++*loads;
+    if (strict ? keys[mid] > x : keys[mid] >= x)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+/*
+ * Join of S against a GRMI: for every probe j, [lo[j], hi[j]) = positions of
+ * R with key S[j] (payloads of the first slots >= and > S[j]); loads[j]
+ * (optional) = keys read by the two searches.  Returns |J|.
+ */
+int64_t lj_oracle_grmi_join_ranges(const uint64_t* R, uint32_t L, int fp64,
+                                   const double* root_dep, const uint64_t* leaf_lo,
+                                   const double* leaf_dep, uint32_t gaps, const uint64_t* keys,
+                                   const uint32_t* pos, uint64_t C, const uint64_t* S,
+                                   uint64_t m, uint64_t* lo, uint64_t* hi, uint64_t* loads) {
+  int64_t total = 0;
+  for (uint64_t j = 0; j < m; ++j) {
+    uint64_t q = lj_oracle_grmi_pslot(R, L, fp64, root_dep, leaf_lo, leaf_dep, gaps, S[j]);
+    uint64_t nl = 0;
+    uint64_t lb = grmi_first(keys, C, S[j], q, 0, &nl);
+    uint64_t ub = lb;
+    if (lb < C && keys[lb] == S[j]) ub = grmi_first(keys, C, S[j], lb, 1, &nl);
+    lo[j] = pos[lb];
+    hi[j] = pos[ub];
+    if (loads) loads[j] = nl;
+    total += (int64_t)(hi[j] - lo[j]);
+  }
+  return total;
+}
