@@ -11,6 +11,9 @@ round(1e9 * LogNormal(0, 2)), sorted; S = 400M keys, half Zipf(0.99) hits
 over R's ranks, half true misses uniform in [min R, max R]; two-level
 linear RMI with 2^20 leaves, single-precision model evaluation.
 
+--index grmi probes through a gapped RMI (Section 3.A) built on the same
+RMI (--gaps per key) instead of the bounded search in R.
+
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle
 (sort-merge join) on bounded samples of the same workload instead.
 """
@@ -174,6 +177,7 @@ def _overrides(args) -> dict:
 def _config(args, wl):
     return {"workload": wl.name, "n": int(wl.R.size), "m": int(wl.S.size),
             "leaves": int(wl.leaves), "precision": wl.precision, "seed": args.seed,
+            "index": args.index if args.index == "rmi" else f"grmi, {args.gaps} gaps per key",
             "l2": "inputs larger than L2 (S = %.1f GB, R = %.1f GB)" % (
                 wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
 
@@ -446,6 +450,9 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override |R| (profiling runs)")
     ap.add_argument("--m", type=int, default=None, help="override |S| (profiling runs)")
     ap.add_argument("--leaves", type=int, default=None, help="override L (profiling runs)")
+    ap.add_argument("--index", default="rmi", choices=["rmi", "grmi"],
+                    help="rmi: bounded search in R; grmi: gapped RMI (exponential search)")
+    ap.add_argument("--gaps", type=int, default=4, help="gapped RMI: gaps per key")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -487,6 +494,7 @@ def main():
         s2 = st if prec == wl.precision else lj.rmi_build(Rd, L, prec).stats()
         windows[prec] = {"mean_window": s2["mean_window"], "max_window": s2["max_window"],
                          "build_ms": s2["build_ms"]}
+    grmi = lj.grmi_build(idx, args.gaps) if args.index == "grmi" else None
     stream = torch.cuda.current_stream()
 
     if unique:
@@ -556,6 +564,7 @@ def main():
     peak, peak_kind = _peaks()
     alg = {
         "probe_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,   # S, R once, leaves, 4-B result
+        "gapped_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,  # the same join, gapped index
         "scan_kernel": 4 * m + (8 * total if unique else 8 * (m + 1)),
         "probe_single_pass_kernel": 8 * m + 8 * n + 32 * L + 8 * total,
         "emit_kernel": 8 * m + 8 * n + 32 * L + 8 * (m + 1) + 8 * total,
@@ -575,6 +584,7 @@ def main():
         "paper_metric_tuples_per_s": world * (n + m) / (ms_per_step / 1e3),
         "build_ms": st["build_ms"], "mean_window": st["mean_window"],
         "max_window": st["max_window"], "windows_by_precision": windows,
+        "grmi": grmi,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " copy bandwidth (hbm_gbs)",

@@ -122,6 +122,55 @@ int rmi_stats(const lj_index* index, lj_index_stats* out);
 int rmi_export(const lj_index* index, double* root_host, uint64_t* leaf_lo,
                double* leaf_ab, int64_t* leaf_err);
 
+/* -------------------------------------------------------- gapped RMI ---- */
+
+/* Statistics of an index's gapped arrays (grmi_build). */
+typedef struct {
+  uint64_t slots;           /* C: length of the gapped key array */
+  uint32_t gaps;            /* gaps per key */
+  uint32_t reserved;
+  double mean_disp;         /* mean of (slot - predicted slot) over R's keys */
+  uint64_t max_disp;        /* largest such displacement */
+  double build_ms;          /* device time of grmi_build, CUDA events */
+} lj_grmi_stats;
+
+/*
+ * grmi_build -- Gapped RMI (Section 3.A): model-based insertion of every key
+ * of R, in key order, into a gapped key array and a gapped payload array
+ * attached to `index` (payload = the key's position in R).
+ *   index   built by rmi_build; its model predicts the slots
+ *   gaps    gaps per key, 0 .. 16 (the paper's default is 4): the arrays
+ *           have C = max((1 + gaps) * n, last slot + 1) slots, C < 2^32 - 1
+ * Predicted slot of key x: (1 + gaps) * p(x), p(x) the RMI's predicted
+ * position clamped to its leaf's positions [lo_l, hi_l].  A key takes its
+ * predicted slot, or the first slot after the previous key's if that is
+ * later.  A gap holds a copy of the next key and its payload (after the last
+ * key: 2^64-1 and n), so the key array is sorted and no bitmap is needed.
+ * From then on join_count, join_emit and join_host on this index look keys
+ * up by exponential search from the predicted slot (keys at q, q+1, q+3,
+ * q+7, ... then a binary search); results are identical to the plain RMI's.
+ * The batched and serving paths and join_count_noalloc reject a gapped index
+ * (LJ_E_INVAL).  Rebuilding replaces the arrays.  Not safe while a join on
+ * the index is in flight.  Synchronises `stream`.
+ * Errors: LJ_E_INVAL (NULL index, gaps > 16, C too large), LJ_E_NOMEM,
+ * LJ_E_CUDA.
+ */
+int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream);
+
+/* Release the gapped arrays; joins go back to the RMI's bounded search. */
+int grmi_drop(lj_index* index);
+
+/* Statistics of the gapped arrays; LJ_E_STATE if the index has none. */
+int grmi_stats(const lj_index* index, lj_grmi_stats* out);
+
+/*
+ * grmi_export -- copy the gapped arrays to host memory.
+ *   keys_host  C uint64 (grmi_stats().slots), may be NULL
+ *   pos_host   C + 1 uint32 (pos_host[C] = n), may be NULL
+ * Synchronises.  LJ_E_STATE if the index has no gapped arrays.
+ */
+int grmi_export(const lj_index* index, uint64_t* keys_host, uint32_t* pos_host);
+
 /* ------------------------------------------------------------- join ----- */
 
 /*

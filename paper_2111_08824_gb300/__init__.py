@@ -8,7 +8,8 @@ library `libljoin` (hand-written sm_103a kernels, C ABI in include/ljoin.h);
 this package is its thin Python binding.  The library is loaded on first
 use; there is no CPU fallback.
 """
-from ._native import (LJ_FP32, LJ_FP64, BatchPlan, Index, LJoinError, Server, join_batch,
+from ._native import (LJ_FP32, LJ_FP64, BatchPlan, Index, LJoinError, Server, grmi_build,
+                      grmi_drop, grmi_export, grmi_stats, join_batch,
                       join_batch_plan, join_count, join_count_noalloc, join_emit, join_host,
                       rmi_autotune, rmi_autotune_clear,
                       library_path, lj_get_option, lj_last_error, lj_profile_report,
@@ -16,7 +17,8 @@ from ._native import (LJ_FP32, LJ_FP64, BatchPlan, Index, LJoinError, Server, jo
                       lj_version, load, rmi_build, rmi_export,
                       rmi_free, rmi_stats)
 
-__all__ = ["LJ_FP32", "LJ_FP64", "BatchPlan", "Index", "LJoinError", "Server", "join_batch",
+__all__ = ["LJ_FP32", "LJ_FP64", "BatchPlan", "Index", "LJoinError", "Server", "grmi_build",
+           "grmi_drop", "grmi_export", "grmi_stats", "join_batch",
            "join_batch_plan", "join_count", "join_count_noalloc", "join_emit", "join_host",
            "rmi_autotune", "rmi_autotune_clear",
            "library_path", "lj_get_option", "lj_last_error", "lj_profile_report",

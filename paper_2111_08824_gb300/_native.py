@@ -38,6 +38,12 @@ class lj_index_stats(ctypes.Structure):
                 ("build_ms", ctypes.c_double)]
 
 
+class lj_grmi_stats(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint64), ("gaps", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("mean_disp", ctypes.c_double),
+                ("max_disp", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
+
+
 class lj_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("streams", ctypes.c_uint32),
                 ("max_batch", ctypes.c_uint32)]
@@ -69,6 +75,10 @@ SIGNATURES = {
     "rmi_free": ([_P], None),
     "rmi_stats": ([_P, _P], _I),
     "rmi_export": ([_P, _P, _P, _P, _P], _I),
+    "grmi_build": ([_P, _U32, _P], _I),
+    "grmi_drop": ([_P], _I),
+    "grmi_stats": ([_P, _P], _I),
+    "grmi_export": ([_P, _P, _P], _I),
     "join_count": ([_P, _P, _U64, _P, _P, _P, _P], _I),
     "join_count_noalloc": ([_P, _P, _U64, _P, _P, _P, _P], _I),
     "join_emit": ([_P, _P, _U64, _P, _P, _U64, _P, _P, _P], _I),
@@ -198,6 +208,33 @@ def rmi_export(index: Index) -> dict:
     err = np.zeros((L, 2), dtype=np.int64)
     _check(load().rmi_export(index.handle, _ptr(root), _ptr(lo), _ptr(ab), _ptr(err)))
     return {"root": root, "leaf_lo": lo, "leaf_ab": ab, "err": err}
+
+
+def grmi_build(index: Index, gaps: int = 4, stream=None) -> dict:
+    """Attach the gapped arrays of a GRMI (Section 3.A) to the index; joins on
+    it then use the exponential search from the predicted slot.  Returns the
+    statistics of the arrays."""
+    _check(load().grmi_build(index.handle, gaps, _stream_ptr(stream)))
+    return grmi_stats(index)
+
+
+def grmi_drop(index: Index):
+    _check(load().grmi_drop(index.handle))
+
+
+def grmi_stats(index: Index) -> dict:
+    st = lj_grmi_stats()
+    _check(load().grmi_stats(index.handle, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+
+def grmi_export(index: Index) -> tuple[np.ndarray, np.ndarray]:
+    """The gapped key array (C uint64) and payload array (C + 1 uint32)."""
+    C = grmi_stats(index)["slots"]
+    keys = np.zeros(C, dtype=np.uint64)
+    pos = np.zeros(C + 1, dtype=np.uint32)
+    _check(load().grmi_export(index.handle, _ptr(keys), _ptr(pos)))
+    return keys, pos
 
 
 def join_count(index: Index, S, counts=None, offsets=None, want_total: bool = True,

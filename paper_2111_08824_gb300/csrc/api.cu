@@ -212,6 +212,7 @@ const char* lj_version(void) { return "ljoin-gb300 0.1 (sm_103a)"; }
 
 void rmi_free(lj_index* index) {
   if (!index) return;
+  lj::grmi_release(index);
   if (index->leaves) cudaFree(index->leaves);
   delete index;
 }

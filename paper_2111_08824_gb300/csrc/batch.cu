@@ -408,8 +408,9 @@ int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, ch
   item0_host[0] = comp0_host[0] = 0;
   for (uint32_t j = 0; j < k; ++j) {
     const lj_index* x = jobs[j].idx;
-    if (!x->unique || x->precision != prec)
-      return fail(LJ_E_INVAL, "dynamic batch: job %u needs a unique R of the batch's precision", j);
+    if (!x->unique || x->precision != prec || x->gkeys)
+      return fail(LJ_E_INVAL, "dynamic batch: job %u needs a unique R of the batch's precision "
+                              "without gapped arrays", j);
     JoinDesc& d = hd[j];
     d.R = x->R;
     d.leaves = x->leaves;
@@ -497,6 +498,9 @@ int join_batch_plan(const lj_index* const* indexes, const uint64_t* const* S_dev
     if (!x->unique)
       return fail(LJ_E_NOTUNIQUE, "join_batch_plan: join %u: batched joins need an R without "
                                   "duplicate keys", j);
+    if (x->gkeys)
+      return fail(LJ_E_INVAL, "join_batch_plan: join %u: gapped indexes (grmi_build) are not "
+                              "supported in batches", j);
     if (x->precision != prec)
       return fail(LJ_E_INVAL, "join_batch_plan: all indexes of a batch need one precision");
     if (x->device != dev) return fail(LJ_E_INVAL, "join_batch_plan: index %u on another device", j);

@@ -158,6 +158,21 @@ __device__ __forceinline__ void window(const typename Model::Leaf& lf, uint64_t 
   if (pred_pos) *pred_pos = (uint32_t)(p < a ? a : (p >= b ? (b > a ? b - 1 : a) : p));
 }
 
+// Predicted slot of key x in the gapped arrays of a GRMI (Section 3.A):
+// (1 + gaps) times the leaf's predicted position clamped to the leaf's
+// positions [lo, hi].  The build places R's keys and the probes start their
+// searches with this one function, so both sides agree bit for bit.  It is
+// monotone in x: the root and the leaf models are, and leaf ranges follow
+// each other.
+template <class Model>
+__device__ __forceinline__ uint64_t gapped_pslot(const typename Model::Leaf& lf, uint64_t x,
+                                                 uint32_t scale) {
+  const int64_t lo = lf.lo, hi = lf.hi;
+  int64_t p = lo + Model::pred(lf, x);
+  p = p < lo ? lo : (p > hi ? hi : p);
+  return (uint64_t)p * scale;
+}
+
 __device__ __forceinline__ uint64_t ldg_key(const uint64_t* R, uint32_t i) {
 #if LJ_L2HINT
   unsigned long long v;

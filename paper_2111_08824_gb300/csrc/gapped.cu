@@ -1,0 +1,328 @@
+// Gapped RMI (Section 3.A of Sabek and Kraska, "The Case for Learned
+// In-Memory Joins"): the RMI already fitted over R places every tuple of R,
+// in key order, by model-based insertion into a gapped key array and a
+// gapped payload array; a lookup then starts at the predicted slot and
+// finishes with an exponential search (probe side: gapped_search_kernel).
+//
+// Model-based insertion in key order puts key i at its predicted slot, or at
+// the first slot after key i-1 if that one is later:
+//     slot_i = max(pslot_i, slot_{i-1} + 1) = i + max_{j <= i} (pslot_j - j),
+// an inclusive max-scan of d_j = pslot_j - j.  The build is three passes:
+//   grmi_dmax_kernel     per tile of 2048 keys: max of d over the tile
+//   grmi_prefix_kernel   exclusive max-scan of the tile maxima (one block)
+//   grmi_fill_kernel     per tile: slots of its keys (block max-scan seeded
+//                        with the tile prefix), then every slot the tile owns,
+//                        (slot of the previous tile's last key, slot of its
+//                        own last key], takes the key and position of the
+//                        first key placed at or after it: gaps hold copies of
+//                        the next key, so the key array stays sorted
+//   grmi_tail_kernel     slots after the last key: 2^64-1 and n; pos[C] = n
+// Each slot is written once, with coalesced stores.
+#include <algorithm>
+#include <climits>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace lj {
+namespace {
+
+constexpr int kGThreads = 256;
+constexpr int kGItems = 8;
+constexpr int kGTile = kGThreads * kGItems;   // keys per tile
+
+template <class Model>
+__device__ __forceinline__ int64_t key_pslot(const typename Model::Leaf* leaves, const Model& m,
+                                             uint64_t x, uint32_t scale) {
+  return (int64_t)gapped_pslot<Model>(Model::load_leaf(leaves, m.leaf(x)), x, scale);
+}
+
+__device__ __forceinline__ int64_t warp_max(int64_t v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v = max(v, (int64_t)__shfl_xor_sync(0xffffffffu, v, d));
+  return v;
+}
+
+template <class Model>
+__global__ void __launch_bounds__(kGThreads)
+    grmi_dmax_kernel(const uint64_t* __restrict__ R, uint64_t n, const typename Model::Leaf* leaves,
+                     Model model, uint32_t scale, int64_t* __restrict__ tile_max) {
+  __shared__ int64_t s_w[kGThreads / 32];
+  const uint64_t i0 = (uint64_t)blockIdx.x * kGTile;
+  int64_t mx = LLONG_MIN;
+#pragma unroll 1
+  for (int k = 0; k < kGItems; ++k) {
+    const uint64_t i = i0 + (uint64_t)k * kGThreads + threadIdx.x;
+    if (i < n) mx = max(mx, key_pslot(leaves, model, R[i], scale) - (int64_t)i);
+  }
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = LLONG_MIN;
+    for (int w = 0; w < kGThreads / 32; ++w) t = max(t, s_w[w]);
+    tile_max[blockIdx.x] = t;
+  }
+}
+
+// Exclusive max-scan of `tiles` values in one block of 1024 threads (each
+// thread a contiguous run of tiles); all_max[0] = the maximum of all.
+__global__ void __launch_bounds__(1024)
+    grmi_prefix_kernel(const int64_t* __restrict__ tile_max, uint32_t tiles,
+                       int64_t* __restrict__ tile_prefix, int64_t* __restrict__ all_max) {
+  __shared__ int64_t s[1024];
+  const uint32_t per = (tiles + 1023) / 1024;
+  const uint32_t b = threadIdx.x * per, e = min(tiles, b + per);
+  int64_t mx = LLONG_MIN;
+  for (uint32_t t = b; t < e; ++t) mx = max(mx, tile_max[t]);
+  s[threadIdx.x] = mx;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {   // inclusive Hillis-Steele max-scan
+    const int64_t v = threadIdx.x >= (unsigned)d ? s[threadIdx.x - d] : LLONG_MIN;
+    __syncthreads();
+    s[threadIdx.x] = max(s[threadIdx.x], v);
+    __syncthreads();
+  }
+  int64_t run = threadIdx.x ? s[threadIdx.x - 1] : LLONG_MIN;
+  for (uint32_t t = b; t < e; ++t) {
+    tile_prefix[t] = run;
+    run = max(run, tile_max[t]);
+  }
+  if (threadIdx.x == 1023) all_max[0] = s[1023];
+}
+
+template <class Model>
+__global__ void __launch_bounds__(kGThreads)
+    grmi_fill_kernel(const uint64_t* __restrict__ R, uint64_t n, const typename Model::Leaf* leaves,
+                     Model model, uint32_t scale, const int64_t* __restrict__ tile_prefix,
+                     uint64_t* __restrict__ gkeys, uint32_t* __restrict__ gpos,
+                     unsigned long long* __restrict__ disp_stats) {
+  __shared__ uint64_t s_key[kGTile];
+  __shared__ uint32_t s_slot[kGTile];
+  __shared__ int64_t s_w[kGThreads / 32];
+  __shared__ unsigned long long s_sum[kGThreads / 32], s_max[kGThreads / 32];
+  const uint64_t i0 = (uint64_t)blockIdx.x * kGTile;
+  const uint32_t cnt = (uint32_t)(n - i0 < (uint64_t)kGTile ? n - i0 : (uint64_t)kGTile);
+  for (uint32_t k = threadIdx.x; k < cnt; k += kGThreads) s_key[k] = R[i0 + k];
+  __syncthreads();
+  // this thread's kGItems consecutive keys: d = pslot - i and its running max
+  const uint32_t k0 = threadIdx.x * kGItems;
+  int64_t d[kGItems], ps[kGItems];
+  int64_t mx = LLONG_MIN;
+#pragma unroll
+  for (int k = 0; k < kGItems; ++k) {
+    ps[k] = 0;
+    d[k] = LLONG_MIN;
+    if (k0 + k < cnt) {
+      ps[k] = key_pslot(leaves, model, s_key[k0 + k], scale);
+      d[k] = ps[k] - (int64_t)(i0 + k0 + k);
+    }
+    mx = max(mx, d[k]);
+  }
+  // exclusive max-scan of the threads' maxima across the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t inc = mx;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc = max(inc, v);
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  int64_t run = tile_prefix[blockIdx.x];
+  for (int w = 0; w < warp; ++w) run = max(run, s_w[w]);
+  const int64_t excl_lane = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane > 0) run = max(run, excl_lane);
+  unsigned long long dsum = 0, dmax = 0;
+#pragma unroll
+  for (int k = 0; k < kGItems; ++k)
+    if (k0 + k < cnt) {
+      run = max(run, d[k]);
+      const int64_t slot = (int64_t)(i0 + k0 + k) + run;
+      s_slot[k0 + k] = (uint32_t)slot;
+      const unsigned long long disp = (unsigned long long)(slot - ps[k]);
+      dsum += disp;
+      dmax = max(dmax, disp);
+    }
+  // displacement statistics (sum and max over R's keys)
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  }
+  if (lane == 0) {
+    s_sum[warp] = dsum;
+    s_max[warp] = dmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0;
+    for (int w = 0; w < kGThreads / 32; ++w) {
+      a += s_sum[w];
+      b = max(b, s_max[w]);
+    }
+    atomicAdd(disp_stats, a);
+    atomicMax(disp_stats + 1, b);
+  }
+  // the slots this tile owns: (slot of key i0 - 1, slot of its last key]
+  const int64_t prev = blockIdx.x == 0 ? -1 : (int64_t)(i0 - 1) + tile_prefix[blockIdx.x];
+  const int64_t last = s_slot[cnt - 1];
+  for (int64_t sl = prev + 1 + threadIdx.x; sl <= last; sl += kGThreads) {
+    uint32_t a = 0, len = cnt;   // first key of the tile placed at or after sl
+    while (len > 0) {
+      const uint32_t half = len >> 1;
+      if ((int64_t)s_slot[a + half] < sl) {
+        a += half + 1;
+        len -= half + 1;
+      } else {
+        len = half;
+      }
+    }
+    gkeys[sl] = s_key[a];
+    gpos[sl] = (uint32_t)(i0 + a);
+  }
+}
+
+__global__ void grmi_tail_kernel(uint64_t* __restrict__ gkeys, uint32_t* __restrict__ gpos,
+                                 uint64_t from, uint64_t C, uint32_t n) {
+  for (uint64_t s = from + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < C;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    gkeys[s] = ~0ull;
+    gpos[s] = n;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) gpos[C] = n;
+}
+
+template <class Model>
+int build_gapped(lj_index* idx, Model model, uint32_t scale, cudaStream_t s) {
+  const uint64_t n = idx->n;
+  const auto* leaves = (const typename Model::Leaf*)idx->leaves;
+  const uint32_t tiles = (uint32_t)((n + kGTile - 1) / kGTile);
+  char* ws = nullptr;
+  const size_t b_tiles = ((size_t)std::max<uint32_t>(tiles, 1) * 8 + 255) / 256 * 256;
+  LJ_CUDA(scratch_alloc((void**)&ws, 256 + 2 * b_tiles, s));
+  int64_t* all_max = (int64_t*)ws;
+  unsigned long long* stats = (unsigned long long*)(ws + 64);
+  int64_t* tile_max = (int64_t*)(ws + 256);
+  int64_t* tile_prefix = (int64_t*)(ws + 256 + b_tiles);
+  int rc = 0;
+  cudaError_t ce = cudaSuccess;
+  int64_t h_max = 0;
+  unsigned long long h_stats[2] = {0, 0};
+  uint64_t C = 0;
+  do {
+    if ((ce = cudaMemsetAsync(ws, 0, 256, s)) != cudaSuccess) break;
+    if (n > 0) {
+      grmi_dmax_kernel<Model><<<tiles, kGThreads, 0, s>>>(idx->R, n, leaves, model, scale, tile_max);
+      grmi_prefix_kernel<<<1, 1024, 0, s>>>(tile_max, tiles, tile_prefix, all_max);
+      if ((ce = cudaGetLastError()) != cudaSuccess) break;
+      if ((ce = cudaMemcpyAsync(&h_max, all_max, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+      if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) break;
+    }
+    const uint64_t last = n ? (uint64_t)((int64_t)(n - 1) + h_max) : 0;   // slot of the last key
+    C = std::max<uint64_t>(n ? last + 1 : 0, (uint64_t)scale * n);
+    if (C >= 0xFFFFFFFFull) {
+      rc = fail(LJ_E_INVAL, "grmi_build: %llu slots exceed the 32-bit slot range; use fewer gaps",
+                (unsigned long long)C);
+      break;
+    }
+    grmi_release(idx);
+    if ((ce = cudaMalloc(&idx->gkeys, std::max<uint64_t>(C, 1) * 8)) != cudaSuccess) break;
+    if ((ce = cudaMalloc(&idx->gpos, (C + 1) * 4)) != cudaSuccess) break;
+    if (n > 0)
+      grmi_fill_kernel<Model><<<tiles, kGThreads, 0, s>>>(idx->R, n, leaves, model, scale, tile_prefix,
+                                                          idx->gkeys, idx->gpos, stats);
+    const uint64_t from = n ? last + 1 : 0;
+    const uint64_t rest = C - from;
+    const unsigned tb = (unsigned)std::min<uint64_t>(4096, std::max<uint64_t>(1, (rest + 255) / 256));
+    grmi_tail_kernel<<<tb, 256, 0, s>>>(idx->gkeys, idx->gpos, from, C, (uint32_t)n);
+    if ((ce = cudaGetLastError()) != cudaSuccess) break;
+    if ((ce = cudaMemcpyAsync(h_stats, stats, 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) break;
+  } while (0);
+  scratch_free(ws, s);
+  if (!rc && ce != cudaSuccess) rc = fail_cuda(ce, "grmi_build");
+  if (rc) {
+    grmi_release(idx);
+    return rc;
+  }
+  idx->gslots = (uint32_t)C;
+  idx->gscale = scale;
+  idx->gstats.slots = C;
+  idx->gstats.gaps = scale - 1;
+  idx->gstats.mean_disp = n ? (double)h_stats[0] / (double)n : 0.0;
+  idx->gstats.max_disp = h_stats[1];
+  return 0;
+}
+
+}  // namespace
+
+void grmi_release(lj_index* idx) {
+  if (idx->gkeys) cudaFree(idx->gkeys);
+  if (idx->gpos) cudaFree(idx->gpos);
+  idx->gkeys = nullptr;
+  idx->gpos = nullptr;
+  idx->gslots = 0;
+  idx->gscale = 0;
+  idx->gstats = lj_grmi_stats{};
+}
+
+}  // namespace lj
+
+extern "C" int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream) {
+  using namespace lj;
+  if (!index) return fail(LJ_E_INVAL, "grmi_build: index is NULL");
+  if (gaps > 16) return fail(LJ_E_INVAL, "grmi_build: gaps = %u must be at most 16", gaps);
+  if (current_device() != index->device)
+    return fail(LJ_E_INVAL, "grmi_build: index lives on device %d, current device is %d",
+                index->device, current_device());
+  if ((uint64_t)(1 + gaps) * index->n >= 0xFFFFFFFFull)
+    return fail(LJ_E_INVAL, "grmi_build: (1 + gaps) * n = %llu slots exceed the 32-bit slot range",
+                (unsigned long long)(1 + gaps) * index->n);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(LJ_E_CUDA, "grmi_build: cudaEventCreate failed");
+  cudaEventRecord(e0, s);
+  int rc;
+  if (index->precision == LJ_FP64)
+    rc = build_gapped(index, ModelF64{index->root_f64[0], index->root_f64[1], index->L}, 1 + gaps, s);
+  else
+    rc = build_gapped(index, ModelF32{index->root_f32[0], index->root_f32[1], index->L}, 1 + gaps, s);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (int r2 = take_device_errors(index->device, s)) {
+    grmi_release(index);
+    return r2;
+  }
+  index->gstats.build_ms = ms;
+  return LJ_OK;
+}
+
+extern "C" int grmi_drop(lj_index* index) {
+  if (!index) return lj::fail(LJ_E_INVAL, "grmi_drop: index is NULL");
+  lj::grmi_release(index);
+  return LJ_OK;
+}
+
+extern "C" int grmi_stats(const lj_index* index, lj_grmi_stats* out) {
+  if (!index || !out) return lj::fail(LJ_E_INVAL, "grmi_stats: NULL argument");
+  if (!index->gpos) return lj::fail(LJ_E_STATE, "grmi_stats: the index has no gapped arrays");
+  *out = index->gstats;
+  return LJ_OK;
+}
+
+extern "C" int grmi_export(const lj_index* index, uint64_t* keys_host, uint32_t* pos_host) {
+  using namespace lj;
+  if (!index) return fail(LJ_E_INVAL, "grmi_export: index is NULL");
+  if (!index->gpos) return fail(LJ_E_STATE, "grmi_export: the index has no gapped arrays");
+  const uint64_t C = index->gslots;
+  if (keys_host && C) LJ_CUDA(cudaMemcpy(keys_host, index->gkeys, C * 8, cudaMemcpyDeviceToHost));
+  if (pos_host) LJ_CUDA(cudaMemcpy(pos_host, index->gpos, (C + 1) * 4, cudaMemcpyDeviceToHost));
+  return LJ_OK;
+}

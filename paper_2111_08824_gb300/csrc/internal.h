@@ -21,6 +21,12 @@ struct lj_index {
   double root_f64[2] = {0, 0};   // deployed double-precision root
   int unique = 1;
   lj_index_stats stats{};
+  // gapped arrays (grmi_build): C slots of keys, C + 1 payloads (positions)
+  uint64_t* gkeys = nullptr;
+  uint32_t* gpos = nullptr;
+  uint32_t gslots = 0;           // C
+  uint32_t gscale = 0;           // 1 + gaps
+  lj_grmi_stats gstats{};
 };
 
 namespace lj {
@@ -91,6 +97,9 @@ size_t dyn_batch_scratch_bytes(const BatchJob* jobs, uint32_t k);
 // job's |J| to written_dev[k].  No allocation, no synchronisation.
 int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, char* scratch,
                       uint64_t* written_dev, cudaStream_t s);
+
+// Release the gapped arrays of an index (no-op without them).
+void grmi_release(lj_index* idx);
 
 // Probe keys per chunk of join_host.
 void set_host_chunk(uint64_t v);

@@ -24,6 +24,10 @@
 //   spent almost half its time waiting in the look-back for tiles whose
 //   searches were slower; the pipeline's extra 8 bytes per probe of
 //   streaming traffic cost far less.
+//   gapped_search_kernel: the search kernel with the lookup of a gapped RMI
+//     (Section 3.A: exponential search from the predicted slot in the gapped
+//     key array, position read from the payload array); an index with
+//     gapped arrays always takes the pipeline.
 //   emit_kernel<Model>: two-pass emit from join_count's offsets; recomputes
 //     each probe's lower bound and lets each warp write the contiguous
 //     output range of its 32 probes with coalesced 8-byte stores.
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(kBlock, LJ_MINB) probe_single_pass_kernel(Prob
 }
 
 // Two-pass emit: warp w of block b handles probes [b*256 + 32w, +32).
-template <class Model>
+template <class Model, bool GAPPED>
 __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
   __shared__ uint64_t s_off[kWarps][33];
   __shared__ uint32_t s_lb[kWarps][32];
@@ -135,13 +139,20 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
   if (j < P.m) {
     const uint64_t key = __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j);
     const typename Model::Leaf lf = Model::load_leaf(P.leaves, P.model.leaf(key));
-    uint32_t wl, wh;
-    window<Model>(lf, key, wl, wh);
     uint64_t xk[1] = {key};
-    uint32_t b[1] = {wl}, l[1] = {wh - wl};
-    uint64_t cv[1];
-    search_last<1, true>(P.R, P.n, P.r32, xk, b, l, cv);
-    lb = b[0];
+    if constexpr (GAPPED) {
+      uint32_t q[1] = {gapped_start(P, lf, key)};
+      uint64_t v[1];
+      gallop_first<1, false>(P.gkeys, P.gslots, xk, q, v);
+      lb = __ldg(P.gpos + q[0]);
+    } else {
+      uint32_t wl, wh;
+      window<Model>(lf, key, wl, wh);
+      uint32_t b[1] = {wl}, l[1] = {wh - wl};
+      uint64_t cv[1];
+      search_last<1, true>(P.R, P.n, P.r32, xk, b, l, cv);
+      lb = b[0];
+    }
     off = P.offsets[j];
     end = P.offsets[j + 1];
   }
@@ -175,10 +186,9 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
 // At the end of the chunk the block adds its probes' match count to the
 // count of their compaction tile (a chunk never straddles two): one barrier
 // and one atomic per chunk (per-warp atomics contended badly).
-template <class Model, int MODE, int CHUNK, bool VEC>
-__global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
-    probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
-                        unsigned long long* __restrict__ tile_counts) {
+template <class Model, int MODE, int CHUNK, bool VEC, bool GAPPED>
+__device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32_t* __restrict__ out,
+                                             unsigned long long* __restrict__ tile_counts) {
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * CHUNK;
   static_assert(kCompactTile % kChunkProbes == 0, "a chunk must lie in one compaction tile");
   __shared__ unsigned long long s_count[kSearchBlock / 32];
@@ -190,7 +200,10 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     if (j0 >= P.m) break;
     uint32_t r_idx[2], cnt[2];
     bool valid[2];
-    lookup_probes<Model, MODE, 1, VEC, LJ_ENDGAME, LJ_GUIDED, LJ_CANON>(P, j0, 0, r_idx, cnt, valid);
+    if constexpr (GAPPED)
+      lookup_gapped<Model, MODE, VEC>(P, j0, r_idx, cnt, valid);
+    else
+      lookup_probes<Model, MODE, 1, VEC, LJ_ENDGAME, LJ_GUIDED, LJ_CANON>(P, j0, 0, r_idx, cnt, valid);
     uint32_t w0, w1;
     if (MODE == kDupCount) {
       w0 = cnt[0];
@@ -217,6 +230,22 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     for (int w = 0; w < kSearchBlock / 32; ++w) tot += s_count[w];
     if (tot) atomicAdd(tile_counts + first / kCompactTile, tot);
   }
+}
+
+template <class Model, int MODE, int CHUNK, bool VEC>
+__global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
+    probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
+                        unsigned long long* __restrict__ tile_counts) {
+  search_chunk<Model, MODE, CHUNK, VEC, false>(P, out, tile_counts);
+}
+
+// The same with the GRMI lookup (Section 3.A): exponential search in the
+// gapped key array from the predicted slot.
+template <class Model, int MODE, int CHUNK, bool VEC>
+__global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
+    gapped_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
+                         unsigned long long* __restrict__ tile_counts) {
+  search_chunk<Model, MODE, CHUNK, VEC, true>(P, out, tile_counts);
 }
 
 // Compaction kernel of the pipeline: tiles of 256 threads x 16 words
@@ -360,6 +389,10 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.m = m;
   P.s_base = s_base;
   P.err = device_error_word(idx->device);
+  P.gkeys = idx->gkeys;
+  P.gpos = idx->gpos;
+  P.gslots = idx->gslots;
+  P.gscale = idx->gscale;
   return P;
 }
 
@@ -443,23 +476,22 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
   {
-    if (LJ_CARVEOUT >= 0) {
-      static bool once = [] {
-        cudaFuncSetAttribute(probe_search_kernel<Model, kDupCount, kSearchChunk, true>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
-        cudaFuncSetAttribute(probe_search_kernel<Model, kDupCount, kSearchChunk, false>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
-        cudaFuncSetAttribute(probe_search_kernel<Model, kUniqueCount, kSearchChunk, true>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
-        cudaFuncSetAttribute(probe_search_kernel<Model, kUniqueCount, kSearchChunk, false>, cudaFuncAttributePreferredSharedMemoryCarveout, LJ_CARVEOUT);
-        return true;
-      }();
-      (void)once;
+    KernelTimer kt(P.gkeys ? "gapped_search_kernel" : "probe_search_kernel", s);
+#define LJ_SEARCH(KERNEL, MODE)                                                              \
+  (vec ? KERNEL<Model, MODE, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts) \
+       : KERNEL<Model, MODE, kSearchChunk, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts))
+    if (P.gkeys) {
+      if (dup)
+        LJ_SEARCH(gapped_search_kernel, kDupCount);
+      else
+        LJ_SEARCH(gapped_search_kernel, kUniqueCount);
+    } else {
+      if (dup)
+        LJ_SEARCH(probe_search_kernel, kDupCount);
+      else
+        LJ_SEARCH(probe_search_kernel, kUniqueCount);
     }
-    KernelTimer kt("probe_search_kernel", s);
-    if (dup)
-      vec ? probe_search_kernel<Model, kDupCount, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
-          : probe_search_kernel<Model, kDupCount, kSearchChunk, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
-    else
-      vec ? probe_search_kernel<Model, kUniqueCount, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts)
-          : probe_search_kernel<Model, kUniqueCount, kSearchChunk, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts);
+#undef LJ_SEARCH
   }
   LJ_CUDA(cudaGetLastError());
   {
@@ -510,7 +542,7 @@ template <class Model>
 int launch_probe(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
                  lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
                  uint64_t* total_dev, uint64_t* total_host, uint32_t s_base, cudaStream_t s) {
-  if (m <= g_single_pass_max)
+  if (m <= g_single_pass_max && !idx->gkeys)   // the GRMI lookup runs in the pipeline only
     return launch_single_pass(idx, model, mode, S, m, pairs, cap, counts, offsets, total_dev,
                               total_host, s_base, s);
   return launch_pipeline(idx, model, mode, S, m, pairs, cap, counts, offsets, total_dev,
@@ -529,7 +561,10 @@ int launch_emit(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
   const uint64_t blocks = (m + kBlock - 1) / kBlock;
   {
     KernelTimer kt("emit_kernel", s);
-    emit_kernel<Model><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+    if (P.gkeys)
+      emit_kernel<Model, true><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+    else
+      emit_kernel<Model, false><<<(unsigned)blocks, kBlock, 0, s>>>(P);
   }
   LJ_CUDA(cudaGetLastError());
   return 0;
@@ -729,6 +764,9 @@ extern "C" int join_count_noalloc(const lj_index* idx, const uint64_t* S_dev, ui
                                   uint64_t* total_host, lj_stream_t stream) {
   using namespace lj;
   if (int rc = check_common(idx, S_dev, m, "join_count_noalloc")) return rc;
+  if (idx->gkeys)
+    return fail(LJ_E_INVAL, "join_count_noalloc: a gapped index (grmi_build) is not supported; "
+                            "use join_count or grmi_drop");
   if (m > kNoAllocMaxProbes)
     return fail(LJ_E_INVAL,
                 "join_count_noalloc: m = %llu exceeds the limit of %llu probes per call set by "

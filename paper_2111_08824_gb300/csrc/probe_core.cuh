@@ -36,6 +36,11 @@ struct ProbeParams {
   TileState st;
   uint32_t* err;
   uint32_t num_tiles;
+  // gapped arrays of a GRMI (Section 3.A); gkeys == nullptr: plain RMI lookup
+  const uint64_t* gkeys;
+  const uint32_t* gpos;   // gslots + 1 payloads (positions in R)
+  uint32_t gslots;        // C
+  uint32_t gscale;        // 1 + gaps
 };
 
 // Tunables (fixed at compile time; the defaults are the measured best).
@@ -63,9 +68,6 @@ struct ProbeParams {
 #endif
 #ifndef LJ_GUIDED
 #define LJ_GUIDED false    // search kernel: model-guided search (measured 2.6x slower: pivots no longer shared)
-#endif
-#ifndef LJ_CARVEOUT
-#define LJ_CARVEOUT -1     // search kernel: preferred shared-memory carveout in percent (-1: driver default)
 #endif
 #ifndef LJ_ENDGAME
 #define LJ_ENDGAME false   // search kernel: resolve the last <= 4 keys in one round (measured slower)
@@ -348,6 +350,152 @@ __device__ __forceinline__ void search_canon(const uint64_t* __restrict__ R,
   for (int p = 0; p < NP; ++p) {
     base[p] = (uint32_t)(pos[p] + 1);
     len[p] = wl[p];   // keep the window start for the caller
+  }
+}
+
+// Exponential search of a GRMI (Section 3.A), NP probes interleaved: for
+// each probe p the first slot s >= pos[p] of the sorted gapped key array K
+// (C slots) with K[s] >= x[p] (STRICT: K[s] > x[p]), or C.  Keys at pos,
+// pos+1, pos+3, pos+7, ... until one passes, then a binary search in the
+// last stretch.  pos[p] receives s and val[p] = K[s] (when s < C).  No key
+// that passes lies before the predicted slot, so the search only moves to
+// later slots.
+template <int NP, bool STRICT>
+__device__ __forceinline__ void gallop_first(const uint64_t* __restrict__ K, uint32_t C,
+                                             const uint64_t (&x)[NP], uint32_t (&pos)[NP],
+                                             uint64_t (&val)[NP]) {
+  uint32_t lo[NP], hi[NP], off[NP];
+  bool open[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    lo[p] = pos[p];
+    hi[p] = C;
+    off[p] = 0;
+    open[p] = pos[p] < C;
+    val[p] = 0;
+  }
+  while (true) {   // exponential phase
+    bool any = false;
+    uint32_t t[NP];
+    uint64_t v[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (open[p]) {
+        const uint64_t tt = (uint64_t)pos[p] + off[p];
+        if (tt >= C) {
+          open[p] = false;
+        } else {
+          t[p] = (uint32_t)tt;
+          v[p] = ldg_key(K, t[p]);
+          any = true;
+        }
+      }
+    if (!any) break;
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (open[p]) {
+        const bool pass = STRICT ? v[p] > x[p] : v[p] >= x[p];
+        if (pass) {
+          hi[p] = t[p];
+          val[p] = v[p];
+          open[p] = false;
+        } else {
+          lo[p] = t[p] + 1;
+          off[p] = 2 * off[p] + 1;
+        }
+      }
+  }
+  uint32_t len[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) len[p] = hi[p] - lo[p];
+  while (true) {   // binary search in [lo, hi)
+    bool any = false;
+    uint64_t v[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (len[p] > 0) {
+        any = true;
+        v[p] = ldg_key(K, lo[p] + (len[p] >> 1));
+      }
+    if (!any) break;
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (len[p] > 0) {
+        const uint32_t half = len[p] >> 1;
+        const bool pass = STRICT ? v[p] > x[p] : v[p] >= x[p];
+        if (pass) {
+          val[p] = v[p];
+          len[p] = half;
+        } else {
+          lo[p] += half + 1;
+          len[p] -= half + 1;
+        }
+      }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) pos[p] = lo[p];
+}
+
+// Predicted slot of x, at most C.
+template <class Model>
+__device__ __forceinline__ uint32_t gapped_start(const ProbeParams<Model>& P,
+                                                 const typename Model::Leaf& lf, uint64_t x) {
+  const uint64_t q = gapped_pslot<Model>(lf, x, P.gscale);
+  return q < P.gslots ? (uint32_t)q : P.gslots;
+}
+
+// GRMI lookups of the two probes j0, j0 + 1 (Section 3.A): root -> leaf ->
+// predicted slot -> exponential search for the first slot holding a key
+// >= x; its payload is the lower bound of x in R.  With duplicates a second
+// search from there finds the first key > x, and cnt is the difference of
+// the two payloads.
+template <class Model, int MODE, bool VEC>
+__device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint64_t j0,
+                                              uint32_t (&r_idx)[2], uint32_t (&cnt)[2],
+                                              bool (&valid)[2]) {
+  uint64_t x[2];
+  if (VEC && j0 + 1 < P.m) {
+    const ulonglong2 v = ldg_stream_u64x2(P.S + j0);
+    x[0] = v.x;
+    x[1] = v.y;
+    valid[0] = valid[1] = true;
+  } else {
+    valid[0] = j0 < P.m;
+    valid[1] = j0 + 1 < P.m;
+    x[0] = valid[0] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0) : 0;
+    x[1] = valid[1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
+  }
+  uint32_t pos[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    pos[p] = P.gslots;
+    if (valid[p]) pos[p] = gapped_start(P, Model::load_leaf(P.leaves, P.model.leaf(x[p])), x[p]);
+  }
+  uint64_t val[2];
+  gallop_first<2, false>(P.gkeys, P.gslots, x, pos, val);
+  bool hit[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) hit[p] = valid[p] && pos[p] < P.gslots && val[p] == x[p];
+  if (MODE == kDupCount) {
+    uint32_t ub[2] = {hit[0] ? pos[0] : P.gslots, hit[1] ? pos[1] : P.gslots};
+    uint64_t v2[2];
+    gallop_first<2, true>(P.gkeys, P.gslots, x, ub, v2);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const uint32_t a = hit[p] ? __ldg(P.gpos + pos[p]) : 0u;
+      const uint32_t b = hit[p] ? __ldg(P.gpos + ub[p]) : 0u;
+      cnt[p] = b - a;
+      r_idx[p] = a;
+    }
+  } else {
+    // slots after R's last key hold 2^64-1 with payload n: a probe 2^64-1
+    // that is not in R lands there, so a match also needs a payload below n
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const uint32_t r = hit[p] ? __ldg(P.gpos + pos[p]) : P.n;
+      cnt[p] = r < P.n ? 1u : 0u;
+      r_idx[p] = r;
+    }
   }
 }
 

@@ -229,6 +229,7 @@ int join_server_add_relation(lj_server* sv, const lj_index* index, uint32_t* rel
   using namespace lj;
   if (!sv || !index || !rel_id) return fail(LJ_E_INVAL, "join_server_add_relation: NULL argument");
   if (!index->unique) return fail(LJ_E_NOTUNIQUE, "served relations need an R without duplicates");
+  if (index->gkeys) return fail(LJ_E_INVAL, "served relations cannot have gapped arrays (grmi_build)");
   if (index->device != sv->device) return fail(LJ_E_INVAL, "relation on another device");
   std::lock_guard<std::mutex> lk(sv->mu);
   if (!sv->rels.empty() && sv->rels[0]->precision != index->precision)

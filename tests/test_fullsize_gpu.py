@@ -121,3 +121,65 @@ def test_dup_seqh_50m_full_properties_and_samples():
         blk = pairs[a:b].cpu().numpy().view(np.uint32)
         assert np.array_equal(blk[:, 0], np.arange(lo[k], hi[k], dtype=np.uint32))
         assert np.all(blk[:, 1] == j)
+
+
+def test_lognormal_100m_gapped_full():
+    """Gapped RMI (Section 3.A, 4 gaps per key, the paper's default) at full
+    size: the 500M-slot arrays equal the oracle's model-based insertion slot
+    for slot, and the join through the exponential search has the workload's
+    properties and matches the oracle on 2^20 sampled probes."""
+    lj = _lj()
+    w = datagen.lognormal_100m(seed=0)
+    Rd, Sd = _dev(w.R), _dev(w.S)
+    m = w.S.size
+    idx = lj.rmi_build(Rd, w.leaves, "fp32")
+    st = lj.grmi_build(idx, 4)
+    keys, pos = lj.grmi_export(idx)
+    want = oracle.grmi_build(w.R, oracle.rmi_fit(w.R, w.leaves, fp64=False), 4)
+    assert st["slots"] == want.keys.size
+    assert np.array_equal(keys, want.keys) and np.array_equal(pos, want.pos)
+    del keys, pos
+    pairs = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+    total = lj.join_emit(idx, Sd, pairs)
+    assert total == w.meta["hits"]
+    _pairs_equal_keys(Rd, Sd, pairs, total)
+    s_idx = pairs[:total, 1].to(torch.int64) & 0xFFFFFFFF
+    mask = torch.zeros(m, dtype=torch.bool, device="cuda")
+    mask[s_idx] = True
+    assert torch.equal(mask.cpu(), torch.from_numpy(w.meta["hit_mask"]))
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(m, 1 << 20, replace=False))
+    lo, hi, _ = oracle.grmi_join(w.R, want, w.S[sample])[:3]
+    lo2, hi2, _ = oracle.join_ranges(w.R, w.S[sample])
+    assert np.array_equal(lo, lo2) and np.array_equal(hi, hi2)
+    p = pairs[:total].cpu().numpy().view(np.uint32)
+    r_of_s = np.full(m, -1, dtype=np.int64)
+    r_of_s[p[:, 1]] = p[:, 0]
+    assert np.array_equal(r_of_s[sample], np.where(hi > lo, lo.astype(np.int64), -1))
+
+
+def test_dup_seqh_50m_gapped_counts_and_samples():
+    lj = _lj()
+    w = datagen.dup_seqh_50m(seed=0)
+    Rd, Sd = _dev(w.R), _dev(w.S)
+    m = w.S.size
+    idx = lj.rmi_build(Rd, w.leaves, w.precision)
+    lj.grmi_build(idx, 4)
+    counts = torch.empty(m, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    total = lj.join_count(idx, Sd, counts=counts, offsets=offsets)
+    assert total == w.meta["expected_pairs"]
+    _, vals_pos = np.unique(w.R, return_index=True)
+    mult = np.diff(np.append(vals_pos, w.R.size))
+    key_rank = np.searchsorted(w.R[vals_pos], w.S)
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), mult[key_rank])
+    # emit a sampled slice of probes through the two-pass path and check them
+    rng = np.random.default_rng(8)
+    sample = np.sort(rng.choice(m, 1 << 16, replace=False))
+    Ss = _dev(w.S[sample])
+    off_s = torch.empty(sample.size + 1, dtype=torch.int64, device="cuda")
+    tot_s = lj.join_count(idx, Ss, offsets=off_s)
+    pairs = torch.empty((tot_s, 2), dtype=torch.int32, device="cuda")
+    assert lj.join_emit(idx, Ss, pairs, offsets=off_s) == tot_s
+    got = pairs.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, oracle.join_pairs(w.R, w.S[sample]))
