@@ -7,7 +7,7 @@
 // r-ascending.
 //
 // Two execution paths, chosen by the size of the probe batch:
-//   single pass (m <= single_pass_max, default 2^20):
+//   single pass (m <= single_pass_max, default 0, i.e. on request only):
 //     probe_single_pass_kernel<Model, MODE, K, VEC>: block tiles of 256
 //     threads x K rounds x 2 probes; lookups, block scan, decoupled look-back
 //     and writes in one launch.
@@ -42,8 +42,12 @@
 namespace lj {
 namespace {
 
-// probe batches up to this size take the single-pass kernel (one launch)
-uint64_t g_single_pass_max = 1ull << 20;
+// Probe batches up to this size take the single-pass kernel (one launch).
+// Default 0: with the L2 flushed, 2^14 .. 2^22 probes took 24-100 us through
+// the pipeline against 28-170 us in the single-pass kernel, whose blocks of
+// 2048 probes leave most SMs idle on small batches and wait in the
+// look-back on large ones.
+uint64_t g_single_pass_max = 0;
 
 // Writes of one round: pairs (kUniqueEmit) or counts / offsets.
 template <class Model, int MODE, bool VEC>
