@@ -195,12 +195,14 @@ def _config(args, wl):
 KERNEL_SOURCES = ("device_common.cuh", "probe_core.cuh", "probe.cu")
 
 
-def _ncu_traffic(kernel: str):
+def _ncu_traffic(kernel: str, args) -> float | None:
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+    was taken on the current kernel sources for this workload (the default
+    lognormal_100m sizes), else None."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(p):
+    if (not os.path.exists(p) or args.workload != "lognormal_100m"
+            or any(v is not None for v in (args.n, args.m, args.leaves))):
         return None
     with open(p) as f:
         d = json.load(f)
@@ -515,13 +517,16 @@ def main():
             lj.join_emit(idx, Sd, pairs, written=written, want_total=False)
         launches_per_step = 1
     else:
+        # duplicates: locate each probe's range of R (count pass), then expand
+        # the ranges into pairs without searching again
         offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
-        total0 = lj.join_count(idx, Sd, offsets=offsets)
+        first = torch.empty(m, dtype=torch.int32, device="cuda")
+        total0 = lj.join_locate(idx, Sd, first, offsets=offsets)
         pairs = torch.empty((max(total0, 1), 2), dtype=torch.int32, device="cuda")
 
         def step():
-            lj.join_count(idx, Sd, offsets=offsets, want_total=False)
-            lj.join_emit(idx, Sd, pairs, offsets=offsets, want_total=False)
+            lj.join_locate(idx, Sd, first, offsets=offsets, want_total=False)
+            lj.join_expand(first, offsets, pairs, want_total=False)
         launches_per_step = 2
 
     for _ in range(args.warmup):
@@ -590,17 +595,19 @@ def main():
     # ---- roofline of the dominant kernel (algorithmic bytes per launch)
     peak, peak_kind = _peaks()
     alg = {
-        "probe_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,   # S, R once, leaves, 4-B result
+        # S, R once, leaves, 4-B result (+ 4-B first match when locating duplicates)
+        "probe_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
         "gapped_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,  # the same join, gapped index
         "scan_kernel": 4 * m + (8 * total if unique else 8 * (m + 1)),
         "probe_single_pass_kernel": 8 * m + 8 * n + 32 * L + 8 * total,
         "emit_kernel": 8 * m + 8 * n + 32 * L + 8 * (m + 1) + 8 * total,
+        "expand_kernel": 4 * m + 8 * (m + 1) + 8 * total,    # first, offsets, pairs
     }
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     dom_ms = kernels[dom]["total_ms"] / kernels[dom]["launches"]
     achieved = alg[dom] / (dom_ms / 1e3) / 1e9
     pass_bytes = 8 * m + 8 * n + 8 * total + 32 * L
-    traffic = _ncu_traffic(dom)
+    traffic = _ncu_traffic(dom, args)
     line = {
         "metric": "probe_keys_per_s", "value": value, "unit": "keys/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

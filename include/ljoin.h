@@ -236,6 +236,36 @@ int join_emit(const lj_index* index, const uint64_t* S_dev, uint64_t m,
               uint64_t* written_dev, uint64_t* written_host, lj_stream_t stream);
 
 /*
+ * join_locate -- join_count that also records where each probe's matches
+ * start (Section 2.A; Section 6.B: the matches of a key are one contiguous
+ * run of the sorted R, so a probe's result is the range
+ * [first[j], first[j] + counts[j]) of R's positions).
+ *   first_dev    m uint32 (required): position of the first key of R equal to
+ *                S[j]; unspecified when S[j] has no match
+ *   counts_dev, offsets_dev, total_host   as join_count
+ * With join_expand this is a two-pass join whose second pass searches
+ * nothing.  Errors: as join_count.
+ */
+int join_locate(const lj_index* index, const uint64_t* S_dev, uint64_t m, uint32_t* first_dev,
+                uint32_t* counts_dev, uint64_t* offsets_dev, uint64_t* total_host,
+                lj_stream_t stream);
+
+/*
+ * join_expand -- write the pairs of located ranges: for every probe j the
+ * pairs (first[j] + t, j), t < offsets[j+1] - offsets[j], at positions
+ * offsets[j] + t (s-major, r-ascending: the order join_emit writes).
+ *   first_dev    m uint32 from join_locate
+ *   offsets_dev  m+1 uint64 from join_locate
+ *   pairs_dev, capacity, written_dev, written_host   as join_emit
+ * Streams first and offsets once and writes the pairs with coalesced stores;
+ * needs neither the index nor S.  Errors: LJ_E_INVAL, LJ_E_CUDA,
+ * LJ_E_CAPACITY.
+ */
+int join_expand(const uint32_t* first_dev, const uint64_t* offsets_dev, uint64_t m,
+                lj_pair* pairs_dev, uint64_t capacity, uint64_t* written_dev,
+                uint64_t* written_host, lj_stream_t stream);
+
+/*
  * join_host -- the whole join from host buffers: copies S (host, ideally
  * pinned) to the device in chunks, runs the lookup on each chunk while the
  * next one is in flight, and copies the pairs back into pairs_host

@@ -9,7 +9,8 @@ this package is its thin Python binding.  The library is loaded on first
 use; there is no CPU fallback.
 """
 from ._native import (LJ_FP32, LJ_FP64, BatchPlan, Index, LJoinError, Server, grmi_build,
-                      grmi_drop, grmi_export, grmi_stats, join_batch,
+                      grmi_drop, grmi_export, grmi_stats, join_batch, join_expand,
+                      join_locate,
                       join_batch_plan, join_count, join_count_noalloc, join_emit, join_host,
                       rmi_autotune, rmi_autotune_clear,
                       library_path, lj_get_option, lj_last_error, lj_profile_report,
@@ -18,7 +19,8 @@ from ._native import (LJ_FP32, LJ_FP64, BatchPlan, Index, LJoinError, Server, gr
                       rmi_free, rmi_stats)
 
 __all__ = ["LJ_FP32", "LJ_FP64", "BatchPlan", "Index", "LJoinError", "Server", "grmi_build",
-           "grmi_drop", "grmi_export", "grmi_stats", "join_batch",
+           "grmi_drop", "grmi_export", "grmi_stats", "join_batch", "join_expand",
+           "join_locate",
            "join_batch_plan", "join_count", "join_count_noalloc", "join_emit", "join_host",
            "rmi_autotune", "rmi_autotune_clear",
            "library_path", "lj_get_option", "lj_last_error", "lj_profile_report",

@@ -83,6 +83,8 @@ SIGNATURES = {
     "join_count_noalloc": ([_P, _P, _U64, _P, _P, _P, _P], _I),
     "join_emit": ([_P, _P, _U64, _P, _P, _U64, _P, _P, _P], _I),
     "join_host": ([_P, _P, _U64, _P, _U64, _P, _P], _I),
+    "join_locate": ([_P, _P, _U64, _P, _P, _P, _P, _P], _I),
+    "join_expand": ([_P, _P, _U64, _P, _U64, _P, _P, _P], _I),
     "join_batch_plan": ([_P, _P, _P, _U32, _P, _P, _P, _P], _I),
     "join_batch_run": ([_P, _P, _P, _P], _I),
     "join_batch_capture": ([_P, _P], _I),
@@ -272,6 +274,29 @@ def join_emit(index: Index, S, pairs, offsets=None, written=None, want_total: bo
     _check(load().join_emit(index.handle, _ptr(S), S.numel(), _ptr(offsets), _ptr(pairs), cap,
                             _ptr(written), ctypes.byref(total) if want_total else None,
                             _stream_ptr(stream)))
+    return total.value if want_total else None
+
+
+def join_locate(index: Index, S, first, counts=None, offsets=None, want_total: bool = True,
+                stream=None) -> int | None:
+    """join_count that also writes each probe's first match position into
+    `first` (uint32/int32 tensor of m); returns |J| when want_total."""
+    _require_cuda_u64(S, "S")
+    total = ctypes.c_uint64()
+    _check(load().join_locate(index.handle, _ptr(S), S.numel(), _ptr(first), _ptr(counts),
+                              _ptr(offsets), ctypes.byref(total) if want_total else None,
+                              _stream_ptr(stream)))
+    return total.value if want_total else None
+
+
+def join_expand(first, offsets, pairs, written=None, want_total: bool = True,
+                stream=None) -> int | None:
+    """Pairs of the ranges located by join_locate (no index, no S needed)."""
+    m = offsets.numel() - 1
+    cap = pairs.shape[0] if pairs is not None else 0
+    total = ctypes.c_uint64()
+    _check(load().join_expand(_ptr(first), _ptr(offsets), m, _ptr(pairs), cap, _ptr(written),
+                              ctypes.byref(total) if want_total else None, _stream_ptr(stream)))
     return total.value if want_total else None
 
 

@@ -8,7 +8,8 @@
 // When S is page-locked host memory the GPU reads it in place (over
 // NVLink-C2C on Grace-Blackwell, at a cost the latency-bound lookups hide) and
 // no copy-in is issued.
-// R with duplicates: per chunk, count (offsets) -> emit -> copy out.
+// R with duplicates: per chunk, locate (first match and offsets per probe)
+// -> expand the ranges into pairs -> copy out.
 #include <algorithm>
 #include <vector>
 
@@ -17,8 +18,10 @@
 
 namespace lj {
 int probe_count_impl(const lj_index* idx, const uint64_t* S, uint64_t m, uint32_t* counts,
-                     uint64_t* offsets, uint64_t* total_dev, uint64_t* total_host,
+                     uint64_t* offsets, uint32_t* first, uint64_t* total_dev, uint64_t* total_host,
                      cudaStream_t s);
+int probe_expand_impl(const uint32_t* first, const uint64_t* offsets, uint64_t m, lj_pair* pairs,
+                      uint64_t cap, uint32_t s_base, cudaStream_t s);
 int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const uint64_t* offsets,
                     lj_pair* pairs, uint64_t cap, uint64_t* total_dev, uint64_t* total_host,
                     uint32_t s_base, cudaStream_t s);
@@ -143,9 +146,10 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
     if (rc) return rc;
   } else {
     char* ws = nullptr;
-    LJ_CUDA(scratch_alloc((void**)&ws, chunk * 8 + (chunk + 1) * 8 + 256, s));
+    LJ_CUDA(scratch_alloc((void**)&ws, chunk * 8 + (chunk + 1) * 8 + chunk * 4 + 512, s));
     uint64_t* Sd = (uint64_t*)ws;
     uint64_t* off_d = (uint64_t*)(ws + chunk * 8);
+    uint32_t* first_d = (uint32_t*)(ws + ((chunk * 16 + 8 + 255) & ~255ull));
     int rc = 0;
     for (uint64_t c = 0; c < nchunks && !rc; ++c) {
       const uint64_t off = c * chunk, len = std::min(chunk, m - off);
@@ -158,7 +162,7 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
         break;
       }
       uint64_t cnt = 0;
-      if ((rc = probe_count_impl(idx, Sc, len, nullptr, off_d, nullptr, &cnt, s))) break;
+      if ((rc = probe_count_impl(idx, Sc, len, nullptr, off_d, first_d, nullptr, &cnt, s))) break;
       const uint64_t room = capacity > written ? capacity - written : 0;
       const uint64_t take = std::min(cnt, room);
       if (take) {
@@ -167,9 +171,7 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
           rc = fail(LJ_E_NOMEM, "join_host: no room for %llu pairs", (unsigned long long)take);
           break;
         }
-        if ((rc = probe_emit_impl(idx, Sc, len, off_d, Pd, take, nullptr, nullptr, (uint32_t)off,
-                                  s)))
-          break;
+        if ((rc = probe_expand_impl(first_d, off_d, len, Pd, take, (uint32_t)off, s))) break;
         cudaMemcpyAsync(pairs_host + written, Pd, take * 8, cudaMemcpyDeviceToHost, s);
         scratch_free(Pd, s);
       }

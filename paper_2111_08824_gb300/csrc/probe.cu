@@ -28,6 +28,8 @@
 //     (Section 3.A: exponential search from the predicted slot in the gapped
 //     key array, position read from the payload array); an index with
 //     gapped arrays always takes the pipeline.
+//   expand_kernel: pairs of the ranges located by join_locate (first match
+//     and offsets per probe); no second search.
 //   emit_kernel<Model>: two-pass emit from join_count's offsets; recomputes
 //     each probe's lower bound and lets each warp write the contiguous
 //     output range of its 32 probes with coalesced 8-byte stores.
@@ -61,14 +63,17 @@ __device__ __forceinline__ void write_round(const ProbeParams<Model>& P, uint64_
   } else if (VEC && v1) {
     if (P.offsets) *reinterpret_cast<ulonglong2*>(P.offsets + j0) = make_ulonglong2(o0, o1);
     if (P.counts) *reinterpret_cast<uint2*>(P.counts + j0) = make_uint2(c0, c1);
+    if (P.first) *reinterpret_cast<uint2*>(P.first + j0) = make_uint2(r0, r1);
   } else {
     if (v0) {
       if (P.offsets) P.offsets[j0] = o0;
       if (P.counts) P.counts[j0] = c0;
+      if (P.first) P.first[j0] = r0;
     }
     if (v1) {
       if (P.offsets) P.offsets[j0 + 1] = o1;
       if (P.counts) P.counts[j0 + 1] = c1;
+      if (P.first) P.first[j0 + 1] = r1;
     }
   }
 }
@@ -180,6 +185,44 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
   }
 }
 
+// Expansion of located ranges (join_expand): warp w of block b handles
+// probes [b*256 + 32w, +32) like emit_kernel, with each probe's first match
+// read from `first` instead of searched again.
+__global__ void __launch_bounds__(kBlock)
+    expand_kernel(const uint32_t* __restrict__ first, const uint64_t* __restrict__ offsets,
+                  uint64_t m, lj_pair* __restrict__ pairs, uint64_t capacity, uint32_t s_base,
+                  uint32_t* err) {
+  __shared__ uint64_t s_off[kWarps][33];
+  __shared__ uint32_t s_lb[kWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t j = blockIdx.x * (uint64_t)kBlock + threadIdx.x;
+  const uint64_t j_warp = j - lane;
+  uint32_t lb = 0;
+  uint64_t off = 0, end = 0;
+  if (j < m) {
+    off = offsets[j];
+    end = offsets[j + 1];
+    if (end > off) lb = first[j];
+  }
+  const uint64_t rem = m > j_warp ? m - 1 - j_warp : 0;
+  const uint64_t last = rem < 31 ? rem : 31;
+  s_off[warp][lane] = off;
+  s_lb[warp][lane] = lb;
+  const uint64_t warp_end = __shfl_sync(0xffffffffu, end, (int)last);
+  if (lane == 0) s_off[warp][32] = warp_end;
+  __syncwarp();
+  if (j_warp >= m) return;
+  const uint64_t warp_start = s_off[warp][0];
+  if (lane == 0 && warp_end > capacity) atomicOr(err, kErrCapacity);
+  const uint64_t stop = min(warp_end, capacity);
+  int p = 0;
+  for (uint64_t q = warp_start + lane; q < stop; q += 32) {
+    while (p < (int)last && s_off[warp][p + 1] <= q) ++p;
+    pairs[q] = lj_pair{s_lb[warp][p] + (uint32_t)(q - s_off[warp][p]),
+                       (uint32_t)(j_warp + p + s_base)};
+  }
+}
+
 // Search kernel of the count-scan-emit pipeline: block b looks up the CHUNK
 // consecutive tiles of 2*kSearchBlock probes starting at probe
 // b * CHUNK * 2 * kSearchBlock, two probes per thread and tile, and writes one
@@ -221,6 +264,14 @@ __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32
     } else {
       if (valid[0]) out[j0] = w0;
       if (valid[1]) out[j0 + 1] = w1;
+    }
+    if (P.first) {   // join_locate: where each probe's matches start
+      if (VEC && valid[1]) {
+        st_stream_u32x2(P.first + j0, r_idx[0], r_idx[1]);
+      } else {
+        if (valid[0]) P.first[j0] = r_idx[0];
+        if (valid[1]) P.first[j0 + 1] = r_idx[1];
+      }
     }
     c += (unsigned long long)cnt[0] + cnt[1];
   }
@@ -406,8 +457,8 @@ inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintp
 template <class Model>
 int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
                        lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
-                       uint64_t* total_dev, uint64_t* total_host, uint32_t s_base,
-                       cudaStream_t s) {
+                       uint32_t* first, uint64_t* total_dev, uint64_t* total_host,
+                       uint32_t s_base, cudaStream_t s) {
   constexpr uint64_t tile = (uint64_t)kBlock * 2 * kRounds;
   Workspace w;
   if (int rc = ws_acquire(w, (uint32_t)((m + tile - 1) / tile), 0, s)) return rc;
@@ -417,11 +468,13 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
   P.capacity = cap;
   P.counts = counts;
   P.offsets = offsets;
+  P.first = first;
   P.total_out = total_dev;
   P.total_ws = w.total;
   P.st = w.st;
   P.num_tiles = w.tiles;
-  const bool vec = aligned(S, 16) && (!offsets || aligned(offsets, 16)) && (!counts || aligned(counts, 8));
+  const bool vec = aligned(S, 16) && (!offsets || aligned(offsets, 16)) &&
+                   (!counts || aligned(counts, 8)) && (!first || aligned(first, 8));
   KernelTimer kt("probe_single_pass_kernel", s);
 #define LJ_LAUNCH(MODE)                                                                     \
   (vec ? probe_single_pass_kernel<Model, MODE, kRounds, true><<<w.tiles, kBlock, 0, s>>>(P) \
@@ -448,7 +501,8 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
 template <class Model>
 int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
                     lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
-                    uint64_t* total_dev, uint64_t* total_host, uint32_t s_base, cudaStream_t s) {
+                    uint32_t* first, uint64_t* total_dev, uint64_t* total_host, uint32_t s_base,
+                    cudaStream_t s) {
   const bool dup = mode == kDupCount;
   // duplicates: the search writes counts, into the caller's buffer if given
   const bool words_in_counts = dup && counts && aligned(counts, 16);
@@ -476,7 +530,8 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
 
   ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
   if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
-  const bool vec = aligned(S, 16);
+  P.first = first;
+  const bool vec = aligned(S, 16) && (!first || aligned(first, 8));
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
   {
@@ -545,11 +600,12 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
 template <class Model>
 int launch_probe(const lj_index* idx, Model model, int mode, const uint64_t* S, uint64_t m,
                  lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
-                 uint64_t* total_dev, uint64_t* total_host, uint32_t s_base, cudaStream_t s) {
+                 uint32_t* first, uint64_t* total_dev, uint64_t* total_host, uint32_t s_base,
+                 cudaStream_t s) {
   if (m <= g_single_pass_max && !idx->gkeys)   // the GRMI lookup runs in the pipeline only
-    return launch_single_pass(idx, model, mode, S, m, pairs, cap, counts, offsets, total_dev,
-                              total_host, s_base, s);
-  return launch_pipeline(idx, model, mode, S, m, pairs, cap, counts, offsets, total_dev,
+    return launch_single_pass(idx, model, mode, S, m, pairs, cap, counts, offsets, first,
+                              total_dev, total_host, s_base, s);
+  return launch_pipeline(idx, model, mode, S, m, pairs, cap, counts, offsets, first, total_dev,
                          total_host, s_base, s);
 }
 
@@ -595,14 +651,14 @@ int check_common(const lj_index* idx, const uint64_t* S, uint64_t m, const char*
 
 // Shared with the chunked host join.
 int probe_count_impl(const lj_index* idx, const uint64_t* S, uint64_t m, uint32_t* counts,
-                     uint64_t* offsets, uint64_t* total_dev, uint64_t* total_host,
+                     uint64_t* offsets, uint32_t* first, uint64_t* total_dev, uint64_t* total_host,
                      cudaStream_t s) {
   const int mode = idx->unique ? kUniqueCount : kDupCount;
   if (idx->precision == LJ_FP64)
-    return launch_probe(idx, f64_model(idx), mode, S, m, nullptr, 0, counts, offsets, total_dev,
-                        total_host, 0, s);
-  return launch_probe(idx, f32_model(idx), mode, S, m, nullptr, 0, counts, offsets, total_dev,
-                      total_host, 0, s);
+    return launch_probe(idx, f64_model(idx), mode, S, m, nullptr, 0, counts, offsets, first,
+                        total_dev, total_host, 0, s);
+  return launch_probe(idx, f32_model(idx), mode, S, m, nullptr, 0, counts, offsets, first,
+                      total_dev, total_host, 0, s);
 }
 
 int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const uint64_t* offsets,
@@ -611,9 +667,9 @@ int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const ui
   if (!offsets) {
     if (idx->precision == LJ_FP64)
       return launch_probe(idx, f64_model(idx), kUniqueEmit, S, m, pairs, cap, nullptr, nullptr,
-                          total_dev, total_host, s_base, s);
+                          nullptr, total_dev, total_host, s_base, s);
     return launch_probe(idx, f32_model(idx), kUniqueEmit, S, m, pairs, cap, nullptr, nullptr,
-                        total_dev, total_host, s_base, s);
+                        nullptr, total_dev, total_host, s_base, s);
   }
   int rc = idx->precision == LJ_FP64
                ? launch_emit(idx, f64_model(idx), S, m, offsets, pairs, cap, s_base, s)
@@ -625,6 +681,20 @@ int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const ui
     LJ_CUDA(cudaStreamSynchronize(s));
     if (int r2 = take_device_errors(idx->device, s)) return r2;
   }
+  return 0;
+}
+
+// Pairs of located ranges (join_expand, and join_host with duplicates).
+int probe_expand_impl(const uint32_t* first, const uint64_t* offsets, uint64_t m, lj_pair* pairs,
+                      uint64_t cap, uint32_t s_base, cudaStream_t s) {
+  uint32_t* err = device_error_word(current_device());
+  if (!err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
+  const uint64_t blocks = (m + kBlock - 1) / kBlock;
+  {
+    KernelTimer kt("expand_kernel", s);
+    expand_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(first, offsets, m, pairs, cap, s_base, err);
+  }
+  LJ_CUDA(cudaGetLastError());
   return 0;
 }
 
@@ -647,7 +717,7 @@ extern "C" int join_count(const lj_index* idx, const uint64_t* S_dev, uint64_t m
     }
     return LJ_OK;
   }
-  return probe_count_impl(idx, S_dev, m, counts_dev, offsets_dev, nullptr, total_host, s);
+  return probe_count_impl(idx, S_dev, m, counts_dev, offsets_dev, nullptr, nullptr, total_host, s);
 }
 
 extern "C" int join_emit(const lj_index* idx, const uint64_t* S_dev, uint64_t m,
@@ -675,6 +745,48 @@ extern "C" int join_emit(const lj_index* idx, const uint64_t* S_dev, uint64_t m,
   if (written_host && *written_host > capacity)
     return fail(LJ_E_CAPACITY, "join_emit: %llu pairs do not fit the capacity of %llu",
                 (unsigned long long)*written_host, (unsigned long long)capacity);
+  return LJ_OK;
+}
+
+extern "C" int join_locate(const lj_index* idx, const uint64_t* S_dev, uint64_t m,
+                           uint32_t* first_dev, uint32_t* counts_dev, uint64_t* offsets_dev,
+                           uint64_t* total_host, lj_stream_t stream) {
+  using namespace lj;
+  if (int rc = check_common(idx, S_dev, m, "join_locate")) return rc;
+  if (m > 0 && !first_dev) return fail(LJ_E_INVAL, "join_locate: first is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m == 0) {
+    if (offsets_dev) LJ_CUDA(cudaMemsetAsync(offsets_dev, 0, 8, s));
+    if (total_host) {
+      *total_host = 0;
+      LJ_CUDA(cudaStreamSynchronize(s));
+    }
+    return LJ_OK;
+  }
+  return probe_count_impl(idx, S_dev, m, counts_dev, offsets_dev, first_dev, nullptr, total_host,
+                          s);
+}
+
+extern "C" int join_expand(const uint32_t* first_dev, const uint64_t* offsets_dev, uint64_t m,
+                           lj_pair* pairs_dev, uint64_t capacity, uint64_t* written_dev,
+                           uint64_t* written_host, lj_stream_t stream) {
+  using namespace lj;
+  if (m >= (1ull << 32)) return fail(LJ_E_INVAL, "join_expand: m must be below 2^32");
+  if (!offsets_dev) return fail(LJ_E_INVAL, "join_expand: offsets is NULL");
+  if (m > 0 && !first_dev) return fail(LJ_E_INVAL, "join_expand: first is NULL");
+  if (capacity > 0 && !pairs_dev) return fail(LJ_E_INVAL, "join_expand: pairs is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m > 0)
+    if (int rc = probe_expand_impl(first_dev, offsets_dev, m, pairs_dev, capacity, 0, s)) return rc;
+  if (written_dev) LJ_CUDA(cudaMemcpyAsync(written_dev, offsets_dev + m, 8, cudaMemcpyDeviceToDevice, s));
+  if (written_host) {
+    LJ_CUDA(cudaMemcpyAsync(written_host, offsets_dev + m, 8, cudaMemcpyDeviceToHost, s));
+    LJ_CUDA(cudaStreamSynchronize(s));
+    if (int rc = take_device_errors(current_device(), s)) return rc;
+    if (*written_host > capacity)
+      return fail(LJ_E_CAPACITY, "join_expand: %llu pairs do not fit the capacity of %llu",
+                  (unsigned long long)*written_host, (unsigned long long)capacity);
+  }
   return LJ_OK;
 }
 

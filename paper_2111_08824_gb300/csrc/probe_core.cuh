@@ -29,6 +29,7 @@ struct ProbeParams {
   lj_pair* pairs;
   uint64_t capacity;
   uint32_t* counts;      // optional
+  uint32_t* first;       // optional: first matching position per probe (join_locate)
   uint64_t* offsets;     // optional, m + 1
   uint64_t* total_out;   // optional, device
   uint64_t* total_ws;    // workspace copy of the total

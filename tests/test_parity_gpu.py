@@ -179,6 +179,46 @@ def test_join_duplicates_parity(prec):
         check_against_oracle(R, S, L, prec, "two_pass")
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("dups", [False, True])
+def test_locate_and_expand_parity(dups, prec):
+    """join_locate's first positions and counts, and join_expand's pairs,
+    against the oracle's ranges and pairs (unique and duplicated R)."""
+    rng = np.random.default_rng(31 + dups)
+    R = (np.sort(rng.integers(0, 4000, 120000, dtype=np.uint64)) if dups
+         else _relation("lognormal", rng, 120000))
+    S = _probe_mix(rng, R, 3 * 4096 + 555)
+    lj = _lj()
+    idx = lj.rmi_build(dev(R), 2000, prec)
+    m = S.size
+    first = torch.full((m,), -1, dtype=torch.int32, device="cuda")
+    counts = torch.empty(m, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    total = lj.join_locate(idx, dev(S), first, counts, offsets)
+    lo, hi, want_total = oracle.join_ranges(R, S)
+    assert total == want_total
+    c = counts.cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(c, hi - lo)
+    f = first.cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(f[c > 0], lo[c > 0])
+    pairs = torch.full((max(total, 1), 2), -1, dtype=torch.int32, device="cuda")
+    assert lj.join_expand(first, offsets, pairs) == total
+    assert np.array_equal(pairs[:total].cpu().numpy().view(np.uint32), oracle.join_pairs(R, S))
+    # too little room: reported, the first `capacity` pairs written
+    if total > 1:
+        small = torch.full((total // 2, 2), -1, dtype=torch.int32, device="cuda")
+        with pytest.raises(lj.LJoinError) as e:
+            lj.join_expand(first, offsets, small)
+        assert e.value.code == -5
+        assert np.array_equal(small.cpu().numpy().view(np.uint32),
+                              oracle.join_pairs(R, S)[: total // 2])
+    # empty S
+    e0 = torch.zeros(0, dtype=torch.int64, device="cuda")
+    off0 = torch.empty(1, dtype=torch.int64, device="cuda")
+    assert lj.join_locate(idx, e0, first[:0], None, off0) == 0
+    assert lj.join_expand(first[:0], off0, pairs) == 0
+
+
 def test_join_misaligned_S_uses_scalar_loads():
     rng = np.random.default_rng(22)
     R = _relation("uniform", rng, 30000)
