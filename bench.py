@@ -189,6 +189,7 @@ def _config(args, wl):
     return {"workload": wl.name, "n": int(wl.R.size), "m": int(wl.S.size),
             "leaves": int(wl.leaves), "precision": wl.precision, "seed": args.seed,
             "index": args.index if args.index == "rmi" else f"grmi, {args.gaps} gaps per key",
+            "probe_order": "bucketed" if args.probe_buckets else "as given",
             "l2": l2 + " (S = %.3f GB, R = %.3f GB)" % (wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
 
 
@@ -465,6 +466,8 @@ def main():
     ap.add_argument("--index", default="rmi", choices=["rmi", "grmi"],
                     help="rmi: bounded search in R; grmi: gapped RMI (exponential search)")
     ap.add_argument("--gaps", type=int, default=4, help="gapped RMI: gaps per key")
+    ap.add_argument("--probe-buckets", type=int, default=0, choices=[0, 1],
+                    help="1: probes looked up in bucketed order (option probe_buckets)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -507,6 +510,7 @@ def main():
         windows[prec] = {"mean_window": s2["mean_window"], "max_window": s2["max_window"],
                          "build_ms": s2["build_ms"]}
     grmi = lj.grmi_build(idx, args.gaps) if args.index == "grmi" else None
+    lj.lj_set_option("probe_buckets", args.probe_buckets)
     stream = torch.cuda.current_stream()
 
     if unique:
@@ -602,6 +606,8 @@ def main():
         "probe_single_pass_kernel": 8 * m + 8 * n + 32 * L + 8 * total,
         "emit_kernel": 8 * m + 8 * n + 32 * L + 8 * (m + 1) + 8 * total,
         "expand_kernel": 4 * m + 8 * (m + 1) + 8 * total,    # first, offsets, pairs
+        # the join's bytes again, plus the bucketed copy of S written and read
+        "bucketed_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
     }
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     dom_ms = kernels[dom]["total_ms"] / kernels[dom]["launches"]

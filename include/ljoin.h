@@ -434,6 +434,14 @@ void join_server_destroy(lj_server* server);
  *                      2^14 to 2^22 keys.  Both paths give identical results.
  *   "host_chunk"       probe keys per chunk of join_host (2^16 .. 2^32-1;
  *                      default 2^25).
+ *   "probe_buckets"    1: the pipeline first groups the probes of every
+ *                      chunk of 2^22 by the region of R their predicted
+ *                      position falls in (2^14 regions), looks them up in that
+ *                      order and writes the results back to the probes' own
+ *                      positions (same results, more locality in R; pays
+ *                      when probes spread over an R larger than L2).
+ *                      0 (default): probes in S order.  Gapped indexes
+ *                      ignore it.
  *   "profile"          1: record CUDA events around every kernel the library
  *                      launches (on the launch's stream); lj_profile_report
  *                      returns the per-kernel totals.  0 (default): off.

@@ -143,6 +143,11 @@ int lj_set_option(const char* name, int64_t value) {
     set_profiling(value != 0);
     return LJ_OK;
   }
+  if (!strcmp(name, "probe_buckets")) {
+    if (value != 0 && value != 1) return fail(LJ_E_INVAL, "probe_buckets must be 0 or 1");
+    set_probe_buckets((int)value);
+    return LJ_OK;
+  }
   if (!strcmp(name, "host_chunk")) {
     if (value < (1 << 16) || value >= (1ll << 32))
       return fail(LJ_E_INVAL, "host_chunk must be in [2^16, 2^32)");
@@ -157,6 +162,7 @@ int64_t lj_get_option(const char* name) {
   if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
   if (name && !strcmp(name, "profile")) return profiling() ? 1 : 0;
   if (name && !strcmp(name, "host_chunk")) return (int64_t)get_host_chunk();
+  if (name && !strcmp(name, "probe_buckets")) return get_probe_buckets();
   fail(LJ_E_INVAL, "lj_get_option: unknown option '%s'", name ? name : "(null)");
   return -1;
 }

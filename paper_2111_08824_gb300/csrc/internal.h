@@ -105,6 +105,10 @@ void grmi_release(lj_index* idx);
 void set_host_chunk(uint64_t v);
 uint64_t get_host_chunk();
 
+// Bucketed probe order in the count-scan-emit pipeline (0 off, 1 on).
+void set_probe_buckets(int v);
+int get_probe_buckets();
+
 // Probe batches of at most this many keys take the single-pass kernel.
 void set_single_pass_max(uint64_t v);
 uint64_t get_single_pass_max();

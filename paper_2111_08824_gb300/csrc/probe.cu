@@ -51,6 +51,11 @@ namespace {
 // look-back on large ones.
 uint64_t g_single_pass_max = 0;
 
+// Bucketed probe order in the pipeline (option "probe_buckets"; off by
+// default: it pays where probes spread over an R larger than L2, and costs
+// where they concentrate on a few hot regions).
+int g_probe_buckets = 0;
+
 // Writes of one round: pairs (kUniqueEmit) or counts / offsets.
 template <class Model, int MODE, bool VEC>
 __device__ __forceinline__ void write_round(const ProbeParams<Model>& P, uint64_t j0,
@@ -303,6 +308,128 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
   search_chunk<Model, MODE, CHUNK, VEC, true>(P, out, tile_counts);
 }
 
+// ---------------------------------------------------------------------------
+// Bucketed probe order (option "probe_buckets"): the probes of each chunk of
+// 2^22 are first grouped by the region of R their predicted position falls
+// in (2^14 buckets per chunk), then looked up bucket by bucket, so that the
+// lanes of a warp and the warps of an SM search nearby parts of R (shared
+// L1/L2 lines, TLB entries and DRAM pages).  The results go back to the
+// probes' own positions, so everything after the search is unchanged.
+//   bucket_count_kernel    bucket sizes (warp-aggregated atomics)
+//   tile_scan_kernel       bucket start positions (the scan of tile counts)
+//   bucket_scatter_kernel  (key, probe index) into bucket order
+//   bucketed_search_kernel lookups in bucket order, words written back to
+//                          the probes' positions
+//   tile_count_kernel      match count per compaction tile, from the words
+constexpr int kBucketChunkLog2 = 22;
+constexpr int kBucketsLog2 = 14;
+constexpr uint32_t kBucketsPerChunk = 1u << kBucketsLog2;
+
+template <class Model>
+__device__ __forceinline__ uint32_t bucket_of(const ProbeParams<Model>& P, uint64_t x, uint64_t j,
+                                              uint32_t shift) {
+  const typename Model::Leaf lf = Model::load_leaf(P.leaves, P.model.leaf(x));
+  const int64_t lo = lf.lo, hi = lf.hi;
+  int64_t p = lo + Model::pred(lf, x);
+  p = p < lo ? lo : (p > hi ? hi : p);   // p <= n, and n >> shift < kBucketsPerChunk
+  return (uint32_t)(j >> kBucketChunkLog2) * kBucketsPerChunk + (uint32_t)((uint64_t)p >> shift);
+}
+
+// Adds 1 to ctr[key] for every active lane, one atomic per distinct key of
+// the warp; returns the lane's own position among the increments.
+__device__ __forceinline__ unsigned long long warp_add_one(unsigned long long* ctr, uint32_t key,
+                                                           bool active) {
+  const unsigned mask = __ballot_sync(0xffffffffu, active);
+  if (!active) return 0;
+  const unsigned grp = __match_any_sync(mask, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(grp) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ctr + key, (unsigned long long)__popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  return base + __popc(grp & ((1u << lane) - 1u));
+}
+
+template <class Model, bool SCATTER>
+__global__ void __launch_bounds__(kSearchBlock)
+    bucket_kernel(ProbeParams<Model> P, uint32_t shift, unsigned long long* __restrict__ ctr,
+                  uint64_t* __restrict__ bx, uint32_t* __restrict__ bj) {
+  const uint64_t j0 = ((uint64_t)blockIdx.x * kSearchBlock + threadIdx.x) * 2;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const uint64_t j = j0 + p;
+    const bool valid = j < P.m;
+    const uint64_t x = valid ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j) : 0;
+    const uint32_t key = valid ? bucket_of(P, x, j, shift) : 0u;
+    const unsigned long long at = warp_add_one(ctr, key, valid);
+    if (SCATTER && valid) {
+      bx[at] = x;
+      bj[at] = (uint32_t)j;
+    }
+  }
+}
+
+template <class Model, int MODE>
+__global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
+    bucketed_search_kernel(ProbeParams<Model> P, const uint64_t* __restrict__ bx,
+                           const uint32_t* __restrict__ bj, uint32_t* __restrict__ out) {
+  const uint64_t i0 = ((uint64_t)blockIdx.x * kSearchBlock + threadIdx.x) * 2;
+  uint64_t x[2];
+  uint32_t j[2];
+  bool valid[2];
+  if (i0 + 1 < P.m) {
+    const ulonglong2 v = ldg_stream_u64x2(bx + i0);
+    const uint2 w = __ldg(reinterpret_cast<const uint2*>(bj + i0));
+    x[0] = v.x;
+    x[1] = v.y;
+    j[0] = w.x;
+    j[1] = w.y;
+    valid[0] = valid[1] = true;
+  } else {
+    valid[0] = i0 < P.m;
+    valid[1] = false;
+    x[0] = valid[0] ? bx[i0] : 0;
+    j[0] = valid[0] ? bj[i0] : 0;
+    x[1] = 0;
+    j[1] = 0;
+  }
+  uint32_t r_idx[2], cnt[2];
+  lookup_keys<Model, MODE, 2>(P, x, valid, r_idx, cnt);
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+    if (valid[p]) {
+      out[j[p]] = MODE == kDupCount ? cnt[p] : (cnt[p] ? r_idx[p] : kNoMatch);
+      if (P.first) P.first[j[p]] = r_idx[p];
+    }
+}
+
+// Matches per compaction tile (kCompactTile words), one block per tile.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock)
+    tile_count_kernel(const uint32_t* __restrict__ words, uint64_t m,
+                      unsigned long long* __restrict__ tile_counts) {
+  __shared__ unsigned long long s_w[kWarps];
+  const uint64_t base = (uint64_t)blockIdx.x * kCompactTile;
+  unsigned long long c = 0;
+#pragma unroll 4
+  for (uint32_t i = threadIdx.x; i < kCompactTile; i += kBlock) {
+    const uint64_t q = base + i;
+    if (q < m) {
+      const uint32_t w = words[q];
+      c += MODE == kDupCount ? w : (w != kNoMatch ? 1u : 0u);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kWarps; ++w) t += s_w[w];
+    tile_counts[blockIdx.x] = t;
+  }
+}
+
 // Compaction kernel of the pipeline: tiles of 256 threads x 16 words
 // (kCompactTile probes).  Each tile already knows its first output position
 // (tile_scan_kernel), so tiles never wait for one another: load the words,
@@ -496,6 +623,68 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
   return 0;
 }
 
+// Search step of the pipeline in bucketed probe order: bucket sizes, bucket
+// starts, scatter into bucket order, lookups, per-tile match counts.
+template <class Model>
+int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, uint32_t* words,
+                    unsigned long long* tile_counts, uint32_t tiles, cudaStream_t s) {
+  const uint64_t m = P.m;
+  const uint64_t chunks = (m + (1ull << kBucketChunkLog2) - 1) >> kBucketChunkLog2;
+  const uint64_t nb = chunks * kBucketsPerChunk;
+  uint32_t shift = 0;
+  while ((idx->n >> shift) >= kBucketsPerChunk) ++shift;
+  const uint32_t sb = (uint32_t)((nb + kTileScanSpan - 1) / kTileScanSpan);
+  const size_t b_ctr = (nb * 8 + 255) / 256 * 256;
+  const size_t b_flags = ((size_t)sb * 4 + 255) / 256 * 256;
+  const size_t b_states = ((size_t)sb * 16 + 255) / 256 * 256;
+  const size_t b_cur = ((nb + 1) * 8 + 255) / 256 * 256;
+  const size_t b_x = (m * 8 + 255) / 256 * 256;
+  char* ws = nullptr;
+  LJ_CUDA(scratch_alloc((void**)&ws, 256 + b_ctr + b_flags + b_states + b_cur + b_x + m * 4, s));
+  LJ_CUDA(cudaMemsetAsync(ws, 0, 256 + b_ctr + b_flags, s));
+  unsigned long long* ctr = (unsigned long long*)(ws + 256);
+  TileState st;
+  st.ticket = (uint32_t*)ws;
+  st.flag = (uint32_t*)(ws + 256 + b_ctr);
+  st.agg = (uint64_t*)(ws + 256 + b_ctr + b_flags);
+  st.incl = st.agg + sb;
+  uint64_t* cursor = (uint64_t*)(ws + 256 + b_ctr + b_flags + b_states);
+  uint64_t* bx = (uint64_t*)(ws + 256 + b_ctr + b_flags + b_states + b_cur);
+  uint32_t* bj = (uint32_t*)(ws + 256 + b_ctr + b_flags + b_states + b_cur + b_x);
+  const unsigned grid = (unsigned)((m + 2 * kSearchBlock - 1) / (2 * kSearchBlock));
+  {
+    KernelTimer kt("bucket_count_kernel", s);
+    bucket_kernel<Model, false><<<grid, kSearchBlock, 0, s>>>(P, shift, ctr, nullptr, nullptr);
+  }
+  {
+    KernelTimer kt("bucket_scan_kernel", s);
+    tile_scan_kernel<<<sb, kBlock, 0, s>>>(ctr, (uint32_t)nb, cursor, st, sb, (uint64_t*)(ws + 64),
+                                           nullptr, nullptr, ~0ull, P.err);
+  }
+  {
+    KernelTimer kt("bucket_scatter_kernel", s);
+    bucket_kernel<Model, true><<<grid, kSearchBlock, 0, s>>>(P, shift, (unsigned long long*)cursor,
+                                                             bx, bj);
+  }
+  {
+    KernelTimer kt("bucketed_search_kernel", s);
+    if (dup)
+      bucketed_search_kernel<Model, kDupCount><<<grid, kSearchBlock, 0, s>>>(P, bx, bj, words);
+    else
+      bucketed_search_kernel<Model, kUniqueCount><<<grid, kSearchBlock, 0, s>>>(P, bx, bj, words);
+  }
+  {
+    KernelTimer kt("tile_count_kernel", s);
+    if (dup)
+      tile_count_kernel<kDupCount><<<tiles, kBlock, 0, s>>>(words, m, tile_counts);
+    else
+      tile_count_kernel<kUniqueCount><<<tiles, kBlock, 0, s>>>(words, m, tile_counts);
+  }
+  LJ_CUDA(cudaGetLastError());
+  LJ_CUDA(scratch_free(ws, s));
+  return 0;
+}
+
 // Count-scan-emit path: search kernel (per-probe words + per-tile counts)
 // -> tile_scan_kernel (tile prefixes, total) -> compact_kernel.
 template <class Model>
@@ -534,7 +723,12 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   const bool vec = aligned(S, 16) && (!first || aligned(first, 8));
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
-  {
+  if (g_probe_buckets && !P.gkeys) {
+    if (int rc = launch_bucketed(idx, P, dup, words, tile_counts, tiles, s)) {
+      scratch_free(ws, s);
+      return rc;
+    }
+  } else {
     KernelTimer kt(P.gkeys ? "gapped_search_kernel" : "probe_search_kernel", s);
 #define LJ_SEARCH(KERNEL, MODE)                                                              \
   (vec ? KERNEL<Model, MODE, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts) \
@@ -698,6 +892,8 @@ int probe_expand_impl(const uint32_t* first, const uint64_t* offsets, uint64_t m
   return 0;
 }
 
+void set_probe_buckets(int v) { g_probe_buckets = v; }
+int get_probe_buckets() { return g_probe_buckets; }
 void set_single_pass_max(uint64_t v) { g_single_pass_max = v; }
 uint64_t get_single_pass_max() { return g_single_pass_max; }
 

@@ -504,29 +504,14 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
 // j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
 // leaf record -> window, then the interleaved bounded searches.  cnt is the
 // number of matches, r_idx the first matching position (when cnt > 0).
-template <class Model, int MODE, int K, bool VEC, bool ENDGAME = false, bool GUIDED = false,
+// Lookups of NP keys already loaded (x, valid): root -> leaf record ->
+// window, then the interleaved bounded searches; cnt = number of matches,
+// r_idx = first matching position (when cnt > 0).
+template <class Model, int MODE, int NP, bool ENDGAME = false, bool GUIDED = false,
           bool CANON = false>
-__device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
-                                              uint32_t stride, uint32_t (&r_idx)[2 * K],
-                                              uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
-  constexpr int NP = 2 * K;
-  uint64_t x[NP];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const uint64_t j0 = first + 2ull * stride * k;
-    if (VEC && j0 + 1 < P.m) {
-      const ulonglong2 v = ldg_stream_u64x2(P.S + j0);
-      x[2 * k] = v.x;
-      x[2 * k + 1] = v.y;
-      valid[2 * k] = valid[2 * k + 1] = true;
-    } else {
-      valid[2 * k] = j0 < P.m;
-      valid[2 * k + 1] = j0 + 1 < P.m;
-      x[2 * k] = valid[2 * k] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0) : 0;
-      x[2 * k + 1] =
-          valid[2 * k + 1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
-    }
-  }
+__device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const uint64_t (&x)[NP],
+                                            const bool (&valid)[NP], uint32_t (&r_idx)[NP],
+                                            uint32_t (&cnt)[NP]) {
   uint32_t base[NP], len[NP], ppos[NP];
   {
     uint32_t leaf[NP];
@@ -597,6 +582,32 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
       r_idx[p] = base[p] - 1;
     }
   }
+}
+
+template <class Model, int MODE, int K, bool VEC, bool ENDGAME = false, bool GUIDED = false,
+          bool CANON = false>
+__device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
+                                              uint32_t stride, uint32_t (&r_idx)[2 * K],
+                                              uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
+  constexpr int NP = 2 * K;
+  uint64_t x[NP];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint64_t j0 = first + 2ull * stride * k;
+    if (VEC && j0 + 1 < P.m) {
+      const ulonglong2 v = ldg_stream_u64x2(P.S + j0);
+      x[2 * k] = v.x;
+      x[2 * k + 1] = v.y;
+      valid[2 * k] = valid[2 * k + 1] = true;
+    } else {
+      valid[2 * k] = j0 < P.m;
+      valid[2 * k + 1] = j0 + 1 < P.m;
+      x[2 * k] = valid[2 * k] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0) : 0;
+      x[2 * k + 1] =
+          valid[2 * k + 1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
+    }
+  }
+  lookup_keys<Model, MODE, NP, ENDGAME, GUIDED, CANON>(P, x, valid, r_idx, cnt);
 }
 
 // Exclusive scan of the per-tile counts: blocks of 256 threads x 16 counts

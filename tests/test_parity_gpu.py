@@ -1,5 +1,7 @@
 """GPU parity: the CUDA path against the CPU oracle, element by element.
 
+Every test runs on the three execution paths of the probe (fused
+single-pass kernel, pipeline in S order, pipeline in bucketed probe order).
 Join results are compared exactly (the pairs are a set, and both sides write
 them in the same canonical order: s_idx ascending, r_idx ascending).  Index
 builds are compared through tests/_validate.py.  Sizes span several probe
@@ -22,14 +24,17 @@ pytestmark = pytest.mark.gpu
 TOP = np.uint64(2**64 - 1)
 
 
-@pytest.fixture(params=["single_pass", "pipeline"], autouse=True)
+@pytest.fixture(params=["single_pass", "pipeline", "bucketed"], autouse=True)
 def probe_path(request):
-    """Run every test on both execution paths of the probe."""
+    """Run every test on each execution path of the probe: the fused kernel,
+    the pipeline in S order, the pipeline in bucketed probe order."""
     import paper_2111_08824_gb300 as lj
-    old = lj.lj_get_option("single_pass_max")
+    old = lj.lj_get_option("single_pass_max"), lj.lj_get_option("probe_buckets")
     lj.lj_set_option("single_pass_max", 1 << 40 if request.param == "single_pass" else 0)
+    lj.lj_set_option("probe_buckets", 1 if request.param == "bucketed" else 0)
     yield request.param
-    lj.lj_set_option("single_pass_max", old)
+    lj.lj_set_option("single_pass_max", old[0])
+    lj.lj_set_option("probe_buckets", old[1])
 
 
 def _lj():
@@ -217,6 +222,16 @@ def test_locate_and_expand_parity(dups, prec):
     off0 = torch.empty(1, dtype=torch.int64, device="cuda")
     assert lj.join_locate(idx, e0, first[:0], None, off0) == 0
     assert lj.join_expand(first[:0], off0, pairs) == 0
+
+
+def test_join_many_chunks_ragged():
+    """More probes than one bucketing chunk (2^22), with a ragged tail."""
+    rng = np.random.default_rng(41)
+    R = np.sort(rng.integers(0, 3 * 10**6, 2 * 10**6, dtype=np.uint64))    # duplicates
+    S = rng.integers(0, 3 * 10**6 + 10, (1 << 22) + 12345, dtype=np.uint64)
+    check_against_oracle(R, S, 20000, "fp32", "two_pass")
+    Ru = np.unique(R)
+    check_against_oracle(Ru, S, 20000, "fp32", "fused")
 
 
 def test_join_misaligned_S_uses_scalar_loads():
