@@ -350,10 +350,12 @@ __device__ __forceinline__ unsigned long long warp_add_one(unsigned long long* c
   return base + __popc(grp & ((1u << lane) - 1u));
 }
 
-template <class Model, bool SCATTER>
+// Bucket sizes: each probe's bucket is kept in bkey for the scatter pass;
+// one reduction (no returned value) per distinct bucket of a warp.
+template <class Model>
 __global__ void __launch_bounds__(kSearchBlock)
-    bucket_kernel(ProbeParams<Model> P, uint32_t shift, unsigned long long* __restrict__ ctr,
-                  uint64_t* __restrict__ bx, uint32_t* __restrict__ bj) {
+    bucket_count_kernel(ProbeParams<Model> P, uint32_t shift, unsigned long long* __restrict__ ctr,
+                        uint32_t* __restrict__ bkey) {
   const uint64_t j0 = ((uint64_t)blockIdx.x * kSearchBlock + threadIdx.x) * 2;
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
@@ -361,9 +363,30 @@ __global__ void __launch_bounds__(kSearchBlock)
     const bool valid = j < P.m;
     const uint64_t x = valid ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j) : 0;
     const uint32_t key = valid ? bucket_of(P, x, j, shift) : 0u;
-    const unsigned long long at = warp_add_one(ctr, key, valid);
-    if (SCATTER && valid) {
-      bx[at] = x;
+    const unsigned mask = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      bkey[j] = key;
+      const unsigned grp = __match_any_sync(mask, key);
+      if ((int)(threadIdx.x & 31) == __ffs(grp) - 1)
+        atomicAdd(ctr + key, (unsigned long long)__popc(grp));
+    }
+  }
+}
+
+// Probes into bucket order: (key, probe index) at the bucket's next free slot.
+__global__ void __launch_bounds__(kSearchBlock)
+    bucket_scatter_kernel(const uint64_t* __restrict__ S, uint64_t m,
+                          const uint32_t* __restrict__ bkey, unsigned long long* __restrict__ cursor,
+                          uint64_t* __restrict__ bx, uint32_t* __restrict__ bj) {
+  const uint64_t j0 = ((uint64_t)blockIdx.x * kSearchBlock + threadIdx.x) * 2;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const uint64_t j = j0 + p;
+    const bool valid = j < m;
+    const uint32_t key = valid ? bkey[j] : 0u;
+    const unsigned long long at = warp_add_one(cursor, key, valid);
+    if (valid) {
+      bx[at] = __ldg(reinterpret_cast<const unsigned long long*>(S) + j);
       bj[at] = (uint32_t)j;
     }
   }
@@ -639,8 +662,9 @@ int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, 
   const size_t b_states = ((size_t)sb * 16 + 255) / 256 * 256;
   const size_t b_cur = ((nb + 1) * 8 + 255) / 256 * 256;
   const size_t b_x = (m * 8 + 255) / 256 * 256;
+  const size_t b_j = (m * 4 + 255) / 256 * 256;
   char* ws = nullptr;
-  LJ_CUDA(scratch_alloc((void**)&ws, 256 + b_ctr + b_flags + b_states + b_cur + b_x + m * 4, s));
+  LJ_CUDA(scratch_alloc((void**)&ws, 256 + b_ctr + b_flags + b_states + b_cur + b_x + 2 * b_j, s));
   LJ_CUDA(cudaMemsetAsync(ws, 0, 256 + b_ctr + b_flags, s));
   unsigned long long* ctr = (unsigned long long*)(ws + 256);
   TileState st;
@@ -651,10 +675,11 @@ int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, 
   uint64_t* cursor = (uint64_t*)(ws + 256 + b_ctr + b_flags + b_states);
   uint64_t* bx = (uint64_t*)(ws + 256 + b_ctr + b_flags + b_states + b_cur);
   uint32_t* bj = (uint32_t*)(ws + 256 + b_ctr + b_flags + b_states + b_cur + b_x);
+  uint32_t* bkey = (uint32_t*)(ws + 256 + b_ctr + b_flags + b_states + b_cur + b_x + b_j);
   const unsigned grid = (unsigned)((m + 2 * kSearchBlock - 1) / (2 * kSearchBlock));
   {
     KernelTimer kt("bucket_count_kernel", s);
-    bucket_kernel<Model, false><<<grid, kSearchBlock, 0, s>>>(P, shift, ctr, nullptr, nullptr);
+    bucket_count_kernel<Model><<<grid, kSearchBlock, 0, s>>>(P, shift, ctr, bkey);
   }
   {
     KernelTimer kt("bucket_scan_kernel", s);
@@ -663,8 +688,8 @@ int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, 
   }
   {
     KernelTimer kt("bucket_scatter_kernel", s);
-    bucket_kernel<Model, true><<<grid, kSearchBlock, 0, s>>>(P, shift, (unsigned long long*)cursor,
-                                                             bx, bj);
+    bucket_scatter_kernel<<<grid, kSearchBlock, 0, s>>>(P.S, m, bkey, (unsigned long long*)cursor,
+                                                         bx, bj);
   }
   {
     KernelTimer kt("bucketed_search_kernel", s);
