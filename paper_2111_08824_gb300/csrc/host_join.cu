@@ -9,7 +9,8 @@
 // NVLink-C2C on Grace-Blackwell, at a cost the latency-bound lookups hide) and
 // no copy-in is issued.
 // R with duplicates: per chunk, locate (first match and offsets per probe)
-// -> expand the ranges into pairs -> copy out.
+// -> expand the ranges into pairs -> copy out on alternating copy streams
+// while the next chunk is located.
 #include <algorithm>
 #include <vector>
 
@@ -145,6 +146,10 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
     cudaStreamSynchronize(s);
     if (rc) return rc;
   } else {
+    // per chunk: locate (first match, offsets, |J| of the chunk) -> expand the
+    // ranges into a pair buffer -> copy out on one of two copy streams while
+    // the next chunk is located; a chunk waits for the copy-out of the chunk
+    // two before it, so at most two pair buffers are in flight
     char* ws = nullptr;
     LJ_CUDA(scratch_alloc((void**)&ws, chunk * 8 + (chunk + 1) * 8 + chunk * 4 + 512, s));
     uint64_t* Sd = (uint64_t*)ws;
@@ -152,6 +157,7 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
     uint32_t* first_d = (uint32_t*)(ws + ((chunk * 16 + 8 + 255) & ~255ull));
     int rc = 0;
     for (uint64_t c = 0; c < nchunks && !rc; ++c) {
+      const int b = (int)(c & 1);
       const uint64_t off = c * chunk, len = std::min(chunk, m - off);
       const uint64_t* Sc = Sd;
       if (S_mapped) {
@@ -166,17 +172,26 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
       const uint64_t room = capacity > written ? capacity - written : 0;
       const uint64_t take = std::min(cnt, room);
       if (take) {
+        if (cudaStreamWaitEvent(s, out_done[b], 0) != cudaSuccess) {   // chunk c-2 copied out
+          rc = fail(LJ_E_CUDA, "join_host: stream wait failed");
+          break;
+        }
         lj_pair* Pd = nullptr;
         if (scratch_alloc((void**)&Pd, take * 8, s) != cudaSuccess) {
           rc = fail(LJ_E_NOMEM, "join_host: no room for %llu pairs", (unsigned long long)take);
           break;
         }
         if ((rc = probe_expand_impl(first_d, off_d, len, Pd, take, (uint32_t)off, s))) break;
-        cudaMemcpyAsync(pairs_host + written, Pd, take * 8, cudaMemcpyDeviceToHost, s);
-        scratch_free(Pd, s);
+        cudaEventRecord(comp_done[b], s);
+        cudaStreamWaitEvent(st.out[b], comp_done[b], 0);
+        cudaMemcpyAsync(pairs_host + written, Pd, take * 8, cudaMemcpyDeviceToHost, st.out[b]);
+        scratch_free(Pd, st.out[b]);
+        cudaEventRecord(out_done[b], st.out[b]);
       }
       written += cnt;
     }
+    cudaStreamSynchronize(st.out[0]);
+    cudaStreamSynchronize(st.out[1]);
     cudaStreamSynchronize(s);
     scratch_free(ws, s);
     cudaStreamSynchronize(s);

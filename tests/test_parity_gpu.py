@@ -298,6 +298,33 @@ def test_error_codes():
     assert lj.join_emit(idx, dev(R), full) == 100
 
 
+def test_join_host_chunked_duplicates_and_capacity():
+    """Host join over several chunks (copy-outs overlapping the next chunk),
+    with duplicate keys, pinned and pageable S, and too little room."""
+    import torch as _t
+    lj = _lj()
+    rng = np.random.default_rng(25)
+    R = np.sort(rng.integers(0, 20000, 150000, dtype=np.uint64))
+    S = rng.integers(0, 21000, 5 * 65536 + 321, dtype=np.uint64)
+    want = oracle.join_pairs(R, S)
+    idx = lj.rmi_build(dev(R), 2048, "fp32")
+    old = lj.lj_get_option("host_chunk")
+    lj.lj_set_option("host_chunk", 65536)
+    try:
+        pinned = _t.from_numpy(S.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        for S_in in (S, pinned):
+            pairs = np.zeros((want.shape[0], 2), np.uint32)
+            assert lj.join_host(idx, S_in, pairs) == want.shape[0]
+            assert np.array_equal(pairs, want)
+        small = np.zeros((want.shape[0] // 3, 2), np.uint32)
+        with pytest.raises(lj.LJoinError) as e:
+            lj.join_host(idx, S, small)
+        assert e.value.code == -5
+        assert np.array_equal(small, want[: small.shape[0]])
+    finally:
+        lj.lj_set_option("host_chunk", old)
+
+
 def test_join_host_matches_device_path():
     lj = _lj()
     rng = np.random.default_rng(24)
