@@ -18,6 +18,9 @@ Learned In-Memory Joins"):
   grmi_build / grmi_join     Section 3.A (gapped RMI: model-based insertion
                              into gapped key and payload arrays, lookup by
                              exponential search from the predicted slot)
+  lhash_build / lhash_join   Section 3.C (learned hash index: the CDF model as
+                             an order-preserving hash into a table of 4-slot
+                             buckets with linear probing)
 """
 from __future__ import annotations
 
@@ -80,6 +83,13 @@ def _load():
                                                        P, ctypes.c_uint32, P, P, U64, P, U64,
                                                        P, P, P]
             lib.lj_oracle_grmi_join_ranges.restype = ctypes.c_int64
+            lib.lj_oracle_lhash_build.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int, P, P, P,
+                                                  ctypes.c_uint32, P, P, U64, P, P, P]
+            lib.lj_oracle_lhash_build.restype = ctypes.c_int64
+            lib.lj_oracle_lhash_join_ranges.argtypes = [P, U64, ctypes.c_uint32, ctypes.c_int, P,
+                                                        P, P, U64, P, P, U64, P, U64, P, U64, P,
+                                                        P, P]
+            lib.lj_oracle_lhash_join_ranges.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -233,4 +243,52 @@ def grmi_join(R, g: GRMI, S) -> tuple[np.ndarray, np.ndarray, int, np.ndarray]:
     total = _load().lj_oracle_grmi_join_ranges(
         _ptr(R), r.L, int(r.fp64), _ptr(r.root_dep), _ptr(r.leaf_lo), _ptr(r.leaf_dep), g.gaps,
         _ptr(g.keys), _ptr(g.pos), g.keys.size, _ptr(S), S.size, _ptr(lo), _ptr(hi), _ptr(loads))
+    return lo, hi, int(total), loads
+
+
+@dataclass
+class LHash:
+    """Learned hash index (oracle side): C slots of keys, C+1 payloads
+    (distinct-key ranks; pos[C] = D), first[D+1] positions in R, B buckets."""
+    rmi: RMI
+    spk: int
+    keys: np.ndarray      # (C,) uint64
+    pos: np.ndarray       # (C+1,) uint32
+    first: np.ndarray     # (D+1,) uint32
+    D: int
+    B: int
+
+
+def lhash_build(R, rmi: RMI, spk: int) -> LHash:
+    R = _u64(R)
+    lib = _load()
+    args = (_ptr(R), R.size, rmi.L, int(rmi.fp64), _ptr(rmi.root_dep), _ptr(rmi.leaf_lo),
+            _ptr(rmi.leaf_dep), spk)
+    D, B = ctypes.c_uint64(), ctypes.c_uint64()
+    C = lib.lj_oracle_lhash_build(*args, None, None, 0, None, ctypes.byref(D), ctypes.byref(B))
+    if C == -1:
+        raise OracleError("R is not sorted non-decreasing")
+    if C < 0:
+        raise MemoryError("oracle ran out of memory")
+    keys = np.zeros(C, dtype=np.uint64)
+    pos = np.zeros(C + 1, dtype=np.uint32)
+    first = np.zeros(D.value + 1, dtype=np.uint32)
+    rc = lib.lj_oracle_lhash_build(*args, _ptr(keys), _ptr(pos), C, _ptr(first), None, None)
+    if rc != C:
+        raise OracleError(f"hash build failed ({rc})")
+    return LHash(rmi, spk, keys, pos, first, D.value, B.value)
+
+
+def lhash_join(R, h: LHash, S) -> tuple[np.ndarray, np.ndarray, int, np.ndarray]:
+    """Per-probe match ranges through the learned hash index, |J|, and the
+    number of table slots each lookup read."""
+    R, S = _u64(R), _u64(S)
+    lo = np.zeros(S.size, dtype=np.uint64)
+    hi = np.zeros(S.size, dtype=np.uint64)
+    loads = np.zeros(S.size, dtype=np.uint64)
+    r = h.rmi
+    total = _load().lj_oracle_lhash_join_ranges(
+        _ptr(R), R.size, r.L, int(r.fp64), _ptr(r.root_dep), _ptr(r.leaf_lo), _ptr(r.leaf_dep),
+        h.B, _ptr(h.keys), _ptr(h.pos), h.keys.size, _ptr(h.first), h.D, _ptr(S), S.size,
+        _ptr(lo), _ptr(hi), _ptr(loads))
     return lo, hi, int(total), loads

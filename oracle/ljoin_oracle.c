@@ -460,3 +460,130 @@ int64_t lj_oracle_grmi_join_ranges(const uint64_t* R, uint32_t L, int fp64,
   }
   return total;
 }
+
+/* -------------------------------------------- learned hash index (3.C) -- */
+/*
+ * Learned hash index (Section 3.C): the CDF model serves as an
+ * order-preserving hash function into a hash table; lookups hash the probe
+ * key and look in the table, with no search over R.  Readings (the paper
+ * uses a RadixSpline and gives no formulas; any monotone CDF model serves,
+ * so the RMI of rmi_fit is used):
+ *   entries:   one per distinct key of R, payload = its rank d among the
+ *              distinct keys; first[d] = position of its first copy in R,
+ *              first[D] = n, so its matches are [first[d], first[d+1]);
+ *   table:     B = max(1, ceil(spk * D / 4)) buckets of 4 slots (spk = slots
+ *              per distinct key, the inverse of the load factor);
+ *   hash:      h(x) = p(x) * B / (n + 1) (integer division), p(x) the RMI's
+ *              predicted position clamped to its leaf's positions [lo, hi];
+ *   insertion: distinct keys in key order into the first free slot at or
+ *              after slot 4 h(x) (linear probing; as h is monotone, keys stay
+ *              in order, so the slot is max(4 h(x), previous slot + 1));
+ *              C = max(4B, last slot + 1) slots; a free slot holds a copy of
+ *              the next filled slot (after the last: 2^64-1 and D);
+ *   lookup:    slots from 4 h(x) on, one by one, until a key >= x; a hit
+ *              when it equals x and its payload is below D.
+ */
+static uint64_t lhash_h(const uint64_t* R, uint64_t n, uint32_t L, int fp64,
+                        const double* root_dep, const uint64_t* leaf_lo, const double* leaf_dep,
+                        uint64_t B, uint64_t x) {
+  uint64_t p = lj_oracle_grmi_pslot(R, L, fp64, root_dep, leaf_lo, leaf_dep, 0, x);
+  return p * B / (n + 1);
+}
+
+/*
+ * Build: returns C (with keys == NULL, only C, D and B); fills keys[C],
+ * pos[C + 1], first[D + 1], *D_out and *B_out.  -1: R not sorted, -2: out of
+ * memory, -3: cap < C.
+ */
+int64_t lj_oracle_lhash_build(const uint64_t* R, uint64_t n, uint32_t L, int fp64,
+                              const double* root_dep, const uint64_t* leaf_lo,
+                              const double* leaf_dep, uint32_t spk, uint64_t* keys, uint32_t* pos,
+                              uint64_t cap, uint32_t* first, uint64_t* D_out, uint64_t* B_out) {
+  if (!lj_oracle_is_sorted(R, n)) return -1;
+  uint64_t D = 0;
+  for (uint64_t i = 0; i < n; ++i)
+    if (i == 0 || R[i] != R[i - 1]) ++D;
+  uint64_t B = (spk * D + 3) / 4;
+  if (B == 0) B = 1;
+  uint64_t* slot = (uint64_t*)malloc(sizeof(uint64_t) * (D ? D : 1));
+  uint64_t* dkey = (uint64_t*)malloc(sizeof(uint64_t) * (D ? D : 1));
+  if (!slot || !dkey) {
+    free(slot);
+    free(dkey);
+    return -2;
+  }
+  uint64_t d = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (i > 0 && R[i] == R[i - 1]) continue;
+    dkey[d] = R[i];
+    if (first) first[d] = (uint32_t)i;
+    uint64_t s = 4 * lhash_h(R, n, L, fp64, root_dep, leaf_lo, leaf_dep, B, R[i]);
+    if (d > 0 && s <= slot[d - 1]) s = slot[d - 1] + 1;   /* linear probing */
+    slot[d] = s;
+    ++d;
+  }
+  if (first) first[D] = (uint32_t)n;
+  uint64_t C = 4 * B;
+  if (D > 0 && slot[D - 1] + 1 > C) C = slot[D - 1] + 1;
+  if (keys) {
+    if (cap < C) {
+      free(slot);
+      free(dkey);
+      return -3;
+    }
+    uint64_t next_key = UINT64_MAX;
+    uint32_t next_pos = (uint32_t)D;
+    uint64_t k = D;
+    for (uint64_t s = C; s-- > 0;) {
+      if (k > 0 && slot[k - 1] == s) {
+        --k;
+        next_key = dkey[k];
+        next_pos = (uint32_t)k;
+      }
+      keys[s] = next_key;
+      pos[s] = next_pos;
+    }
+    pos[C] = (uint32_t)D;
+  }
+  if (D_out) *D_out = D;
+  if (B_out) *B_out = B;
+  free(slot);
+  free(dkey);
+  return (int64_t)C;
+}
+
+/* Join through the learned hash index: [lo[j], hi[j]) per probe, loads[j] =
+ * table slots read; returns |J|. */
+int64_t lj_oracle_lhash_join_ranges(const uint64_t* R, uint64_t n, uint32_t L, int fp64,
+                                    const double* root_dep, const uint64_t* leaf_lo,
+                                    const double* leaf_dep, uint64_t B, const uint64_t* keys,
+                                    const uint32_t* pos, uint64_t C, const uint32_t* first,
+                                    uint64_t D, const uint64_t* S, uint64_t m, uint64_t* lo,
+                                    uint64_t* hi, uint64_t* loads) {
+  int64_t total = 0;
+  for (uint64_t j = 0; j < m; ++j) {
+    uint64_t s = 4 * lhash_h(R, n, L, fp64, root_dep, leaf_lo, leaf_dep, B, S[j]);
+    uint64_t nl = 0;
+    while (s < C) {
+      ++nl;
+      if (keys[s] >= S[j]) break;
+      ++s;
+    }
+    lo[j] = hi[j] = 0;
+    if (s < C && keys[s] == S[j] && pos[s] < D) {
+      lo[j] = first[pos[s]];
+      hi[j] = first[pos[s] + 1];
+    } else {
+      /* no match: the lower bound of S[j] in R (for an empty range) */
+      uint64_t a = 0, b = n;
+      while (a < b) {
+        uint64_t mid = a + (b - a) / 2;
+        if (R[mid] < S[j]) a = mid + 1; else b = mid;
+      }
+      lo[j] = hi[j] = a;
+    }
+    if (loads) loads[j] = nl;
+    total += (int64_t)(hi[j] - lo[j]);
+  }
+  return total;
+}
