@@ -188,7 +188,8 @@ def _config(args, wl):
           % (L2_FLUSH_BYTES >> 20) if _small(wl) else "inputs larger than L2")
     return {"workload": wl.name, "n": int(wl.R.size), "m": int(wl.S.size),
             "leaves": int(wl.leaves), "precision": wl.precision, "seed": args.seed,
-            "index": args.index if args.index == "rmi" else f"grmi, {args.gaps} gaps per key",
+            "index": {"rmi": "rmi", "grmi": f"grmi, {args.gaps} gaps per key",
+                      "lhash": f"learned hash, {args.gaps} slots per distinct key"}[args.index],
             "probe_order": "bucketed" if args.probe_buckets else "as given",
             "l2": l2 + " (S = %.3f GB, R = %.3f GB)" % (wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
 
@@ -463,9 +464,11 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override |R| (profiling runs)")
     ap.add_argument("--m", type=int, default=None, help="override |S| (profiling runs)")
     ap.add_argument("--leaves", type=int, default=None, help="override L (profiling runs)")
-    ap.add_argument("--index", default="rmi", choices=["rmi", "grmi"],
-                    help="rmi: bounded search in R; grmi: gapped RMI (exponential search)")
-    ap.add_argument("--gaps", type=int, default=4, help="gapped RMI: gaps per key")
+    ap.add_argument("--index", default="rmi", choices=["rmi", "grmi", "lhash"],
+                    help="rmi: bounded search in R; grmi: gapped RMI (exponential search); "
+                         "lhash: learned hash index")
+    ap.add_argument("--gaps", type=int, default=4,
+                    help="grmi: gaps per key; lhash: slots per distinct key")
     ap.add_argument("--probe-buckets", type=int, default=0, choices=[0, 1],
                     help="1: probes looked up in bucketed order (option probe_buckets)")
     args = ap.parse_args()
@@ -509,7 +512,8 @@ def main():
         s2 = st if prec == wl.precision else lj.rmi_build(Rd, L, prec).stats()
         windows[prec] = {"mean_window": s2["mean_window"], "max_window": s2["max_window"],
                          "build_ms": s2["build_ms"]}
-    grmi = lj.grmi_build(idx, args.gaps) if args.index == "grmi" else None
+    grmi = (lj.grmi_build(idx, args.gaps) if args.index == "grmi"
+            else lj.lhash_build(idx, args.gaps) if args.index == "lhash" else None)
     lj.lj_set_option("probe_buckets", args.probe_buckets)
     stream = torch.cuda.current_stream()
 
@@ -602,6 +606,7 @@ def main():
         # S, R once, leaves, 4-B result (+ 4-B first match when locating duplicates)
         "probe_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
         "gapped_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,  # the same join, gapped index
+        "hash_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
         "scan_kernel": 4 * m + (8 * total if unique else 8 * (m + 1)),
         "probe_single_pass_kernel": 8 * m + 8 * n + 32 * L + 8 * total,
         "emit_kernel": 8 * m + 8 * n + 32 * L + 8 * (m + 1) + 8 * total,

@@ -124,14 +124,15 @@ int rmi_export(const lj_index* index, double* root_host, uint64_t* leaf_lo,
 
 /* -------------------------------------------------------- gapped RMI ---- */
 
-/* Statistics of an index's gapped arrays (grmi_build). */
+/* Statistics of an index's gapped arrays (grmi_build or lhash_build). */
 typedef struct {
   uint64_t slots;           /* C: length of the gapped key array */
-  uint32_t gaps;            /* gaps per key */
-  uint32_t reserved;
-  double mean_disp;         /* mean of (slot - predicted slot) over R's keys */
+  uint32_t gaps;            /* grmi_build: gaps per key; lhash_build: slots per distinct key */
+  uint32_t kind;            /* 0: gapped RMI (grmi_build), 1: learned hash (lhash_build) */
+  double mean_disp;         /* mean of (slot - predicted slot) over the placed keys */
   uint64_t max_disp;        /* largest such displacement */
-  double build_ms;          /* device time of grmi_build, CUDA events */
+  double build_ms;          /* device time of the build, CUDA events */
+  uint64_t distinct;        /* lhash_build: number of distinct keys of R (else 0) */
 } lj_grmi_stats;
 
 /*
@@ -157,7 +158,35 @@ typedef struct {
  */
 int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream);
 
-/* Release the gapped arrays; joins go back to the RMI's bounded search. */
+/*
+ * lhash_build -- learned hash index (Section 3.C): the RMI serves as an
+ * order-preserving hash function into a table of 4-slot buckets, one entry
+ * per distinct key of R, attached to `index` (replacing gapped arrays it
+ * may have).
+ *   spk    slots per distinct key, 1 .. 16 (the inverse load factor; the
+ *          paper's hash baselines use 4): B = max(1, ceil(spk * D / 4))
+ *          buckets for D distinct keys
+ * Hash of key x: h(x) = p(x) * B / (n + 1) (integer division), p(x) the
+ * RMI's predicted position clamped to its leaf's positions.  Distinct keys
+ * take, in key order, the first free slot at or after slot 4 h(x) (linear
+ * probing; the hash is monotone, so the table stays sorted and a free slot
+ * holds a copy of the next entry).  An entry's payload is the rank d of its
+ * key among the distinct keys; first[d] is the position of its first copy in
+ * R, first[D] = n, and its matches are R's positions [first[d], first[d+1]).
+ * Lookups hash the probe and search forward from its bucket (exponential
+ * steps, then a binary search); duplicates need no second search.  Joins on
+ * the index then behave as after grmi_build (same results, same paths).
+ * Synchronises.  Errors: LJ_E_INVAL (NULL index, spk out of range, too many
+ * slots), LJ_E_NOMEM, LJ_E_CUDA.
+ */
+int lhash_build(lj_index* index, uint32_t spk, lj_stream_t stream);
+
+/* first[D + 1] of a learned hash index (lhash_build) into host memory;
+ * LJ_E_STATE without one.  Synchronises. */
+int lhash_export_first(const lj_index* index, uint32_t* first_host);
+
+/* Release the gapped arrays (grmi_build or lhash_build); joins go back to
+ * the RMI's bounded search. */
 int grmi_drop(lj_index* index);
 
 /* Statistics of the gapped arrays; LJ_E_STATE if the index has none. */

@@ -40,8 +40,9 @@ class lj_index_stats(ctypes.Structure):
 
 class lj_grmi_stats(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint64), ("gaps", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("mean_disp", ctypes.c_double),
-                ("max_disp", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
+                ("kind", ctypes.c_uint32), ("mean_disp", ctypes.c_double),
+                ("max_disp", ctypes.c_uint64), ("build_ms", ctypes.c_double),
+                ("distinct", ctypes.c_uint64)]
 
 
 class lj_server_cfg(ctypes.Structure):
@@ -76,6 +77,8 @@ SIGNATURES = {
     "rmi_stats": ([_P, _P], _I),
     "rmi_export": ([_P, _P, _P, _P, _P], _I),
     "grmi_build": ([_P, _U32, _P], _I),
+    "lhash_build": ([_P, _U32, _P], _I),
+    "lhash_export_first": ([_P, _P], _I),
     "grmi_drop": ([_P], _I),
     "grmi_stats": ([_P, _P], _I),
     "grmi_export": ([_P, _P, _P], _I),
@@ -220,6 +223,23 @@ def grmi_build(index: Index, gaps: int = 4, stream=None) -> dict:
     return grmi_stats(index)
 
 
+def lhash_build(index: Index, spk: int = 4, stream=None) -> dict:
+    """Attach a learned hash index (Section 3.C: the RMI as an order-preserving
+    hash into 4-slot buckets, one entry per distinct key, spk slots per
+    distinct key); joins on the index then hash each probe.  Returns the
+    table's statistics."""
+    _check(load().lhash_build(index.handle, spk, _stream_ptr(stream)))
+    return grmi_stats(index)
+
+
+def lhash_export_first(index: Index) -> np.ndarray:
+    """first[D + 1]: position in R of each distinct key's first copy."""
+    D = grmi_stats(index)["distinct"]
+    first = np.zeros(D + 1, dtype=np.uint32)
+    _check(load().lhash_export_first(index.handle, _ptr(first)))
+    return first
+
+
 def grmi_drop(index: Index):
     _check(load().grmi_drop(index.handle))
 
@@ -227,7 +247,7 @@ def grmi_drop(index: Index):
 def grmi_stats(index: Index) -> dict:
     st = lj_grmi_stats()
     _check(load().grmi_stats(index.handle, ctypes.byref(st)))
-    return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+    return {f: getattr(st, f) for f, _ in st._fields_}
 
 
 def grmi_export(index: Index) -> tuple[np.ndarray, np.ndarray]:

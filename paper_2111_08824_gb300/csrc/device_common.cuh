@@ -165,13 +165,39 @@ __device__ __forceinline__ void window(const typename Model::Leaf& lf, uint64_t 
 // monotone in x: the root and the leaf models are, and leaf ranges follow
 // each other.
 template <class Model>
-__device__ __forceinline__ uint64_t gapped_pslot(const typename Model::Leaf& lf, uint64_t x,
-                                                 uint32_t scale) {
+__device__ __forceinline__ uint64_t clamped_pos(const typename Model::Leaf& lf, uint64_t x) {
   const int64_t lo = lf.lo, hi = lf.hi;
   int64_t p = lo + Model::pred(lf, x);
   p = p < lo ? lo : (p > hi ? hi : p);
-  return (uint64_t)p * scale;
+  return (uint64_t)p;
 }
+
+template <class Model>
+__device__ __forceinline__ uint64_t gapped_pslot(const typename Model::Leaf& lf, uint64_t x,
+                                                 uint32_t scale) {
+  return clamped_pos<Model>(lf, x) * scale;
+}
+
+// Slot functions of the two gapped layouts built by model-based insertion:
+//   GappedSlot  GRMI (Section 3.A): (1 + gaps) slots per key of R
+//   HashSlot    learned hash index (Section 3.C): the model as an
+//               order-preserving hash into B buckets of 4 slots,
+//               h(x) = p(x) * B / (n + 1), first slot 4 h(x)
+struct GappedSlot {
+  uint32_t scale;
+  template <class Model>
+  __device__ __forceinline__ uint64_t at(const typename Model::Leaf& lf, uint64_t x) const {
+    return clamped_pos<Model>(lf, x) * scale;
+  }
+};
+struct HashSlot {
+  uint64_t B;    // buckets
+  uint64_t n1;   // n + 1
+  template <class Model>
+  __device__ __forceinline__ uint64_t at(const typename Model::Leaf& lf, uint64_t x) const {
+    return 4 * (clamped_pos<Model>(lf, x) * B / n1);
+  }
+};
 
 __device__ __forceinline__ uint64_t ldg_key(const uint64_t* R, uint32_t i) {
 #if LJ_L2HINT

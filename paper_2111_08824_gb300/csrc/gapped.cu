@@ -31,10 +31,10 @@ constexpr int kGThreads = 256;
 constexpr int kGItems = 8;
 constexpr int kGTile = kGThreads * kGItems;   // keys per tile
 
-template <class Model>
+template <class Model, class Slot>
 __device__ __forceinline__ int64_t key_pslot(const typename Model::Leaf* leaves, const Model& m,
-                                             uint64_t x, uint32_t scale) {
-  return (int64_t)gapped_pslot<Model>(Model::load_leaf(leaves, m.leaf(x)), x, scale);
+                                             uint64_t x, const Slot& slot) {
+  return (int64_t)slot.template at<Model>(Model::load_leaf(leaves, m.leaf(x)), x);
 }
 
 __device__ __forceinline__ int64_t warp_max(int64_t v) {
@@ -43,10 +43,10 @@ __device__ __forceinline__ int64_t warp_max(int64_t v) {
   return v;
 }
 
-template <class Model>
+template <class Model, class Slot>
 __global__ void __launch_bounds__(kGThreads)
     grmi_dmax_kernel(const uint64_t* __restrict__ R, uint64_t n, const typename Model::Leaf* leaves,
-                     Model model, uint32_t scale, int64_t* __restrict__ tile_max) {
+                     Model model, Slot scale, int64_t* __restrict__ tile_max) {
   __shared__ int64_t s_w[kGThreads / 32];
   const uint64_t i0 = (uint64_t)blockIdx.x * kGTile;
   int64_t mx = LLONG_MIN;
@@ -65,36 +65,97 @@ __global__ void __launch_bounds__(kGThreads)
   }
 }
 
-// Exclusive max-scan of `tiles` values in one block of 1024 threads (each
-// thread a contiguous run of tiles); all_max[0] = the maximum of all.
+// Exclusive scan (max, or sum when SUM) of `tiles` values in one block of
+// 1024 threads (each thread a contiguous run of tiles); all[0] = the
+// reduction of all.
+template <bool SUM>
 __global__ void __launch_bounds__(1024)
     grmi_prefix_kernel(const int64_t* __restrict__ tile_max, uint32_t tiles,
                        int64_t* __restrict__ tile_prefix, int64_t* __restrict__ all_max) {
   __shared__ int64_t s[1024];
+  const int64_t id = SUM ? 0 : LLONG_MIN;
+  auto op = [](int64_t a, int64_t b) { return SUM ? a + b : max(a, b); };
   const uint32_t per = (tiles + 1023) / 1024;
   const uint32_t b = threadIdx.x * per, e = min(tiles, b + per);
-  int64_t mx = LLONG_MIN;
-  for (uint32_t t = b; t < e; ++t) mx = max(mx, tile_max[t]);
+  int64_t mx = id;
+  for (uint32_t t = b; t < e; ++t) mx = op(mx, tile_max[t]);
   s[threadIdx.x] = mx;
   __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {   // inclusive Hillis-Steele max-scan
-    const int64_t v = threadIdx.x >= (unsigned)d ? s[threadIdx.x - d] : LLONG_MIN;
+  for (int d = 1; d < 1024; d <<= 1) {   // inclusive Hillis-Steele scan
+    const int64_t v = threadIdx.x >= (unsigned)d ? s[threadIdx.x - d] : id;
     __syncthreads();
-    s[threadIdx.x] = max(s[threadIdx.x], v);
+    s[threadIdx.x] = op(s[threadIdx.x], v);
     __syncthreads();
   }
-  int64_t run = threadIdx.x ? s[threadIdx.x - 1] : LLONG_MIN;
+  int64_t run = threadIdx.x ? s[threadIdx.x - 1] : id;
   for (uint32_t t = b; t < e; ++t) {
     tile_prefix[t] = run;
-    run = max(run, tile_max[t]);
+    run = op(run, tile_max[t]);
   }
   if (threadIdx.x == 1023) all_max[0] = s[1023];
 }
 
-template <class Model>
+// Distinct keys of the sorted R (learned hash index): per tile, the number of
+// run starts (positions i with i == 0 or R[i] != R[i-1]) ...
+__global__ void __launch_bounds__(kGThreads)
+    run_count_kernel(const uint64_t* __restrict__ R, uint64_t n, int64_t* __restrict__ tile_cnt) {
+  __shared__ int64_t s_w[kGThreads / 32];
+  const uint64_t i0 = (uint64_t)blockIdx.x * kGTile;
+  int64_t c = 0;
+  for (int k = 0; k < kGItems; ++k) {
+    const uint64_t i = i0 + (uint64_t)k * kGThreads + threadIdx.x;
+    if (i < n && (i == 0 || R[i] != R[i - 1])) ++c;
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kGThreads / 32; ++w) t += s_w[w];
+    tile_cnt[blockIdx.x] = t;
+  }
+}
+
+// ... then each run start's key and position at its rank among the runs.
+__global__ void __launch_bounds__(kGThreads)
+    run_write_kernel(const uint64_t* __restrict__ R, uint64_t n,
+                     const int64_t* __restrict__ tile_off, uint64_t* __restrict__ dkey,
+                     uint32_t* __restrict__ dfirst) {
+  __shared__ int64_t s_w[kGThreads / 32];
+  const uint64_t i0 = (uint64_t)blockIdx.x * kGTile + (uint64_t)threadIdx.x * kGItems;
+  bool f[kGItems];
+  int64_t c = 0;
+#pragma unroll
+  for (int k = 0; k < kGItems; ++k) {
+    const uint64_t i = i0 + k;
+    f[k] = i < n && (i == 0 || R[i] != R[i - 1]);
+    c += f[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  int64_t d = tile_off[blockIdx.x] + inc - c;
+  for (int w = 0; w < warp; ++w) d += s_w[w];
+#pragma unroll
+  for (int k = 0; k < kGItems; ++k)
+    if (f[k]) {
+      dkey[d] = R[i0 + k];
+      dfirst[d] = (uint32_t)(i0 + k);
+      ++d;
+    }
+}
+
+template <class Model, class Slot>
 __global__ void __launch_bounds__(kGThreads)
     grmi_fill_kernel(const uint64_t* __restrict__ R, uint64_t n, const typename Model::Leaf* leaves,
-                     Model model, uint32_t scale, const int64_t* __restrict__ tile_prefix,
+                     Model model, Slot scale, const int64_t* __restrict__ tile_prefix,
                      uint64_t* __restrict__ gkeys, uint32_t* __restrict__ gpos,
                      unsigned long long* __restrict__ disp_stats) {
   __shared__ uint64_t s_key[kGTile];
@@ -193,9 +254,11 @@ __global__ void grmi_tail_kernel(uint64_t* __restrict__ gkeys, uint32_t* __restr
   if (blockIdx.x == 0 && threadIdx.x == 0) gpos[C] = n;
 }
 
-template <class Model>
-int build_gapped(lj_index* idx, Model model, uint32_t scale, cudaStream_t s) {
-  const uint64_t n = idx->n;
+// Model-based insertion of the n sorted keys src[] into the index's gapped
+// arrays, key i at max(slot(src[i]), slot of key i-1 + 1); payload = i.
+template <class Model, class Slot>
+int build_gapped(lj_index* idx, Model model, Slot scale, const uint64_t* src, uint64_t n,
+                 uint64_t min_slots, cudaStream_t s) {
   const auto* leaves = (const typename Model::Leaf*)idx->leaves;
   const uint32_t tiles = (uint32_t)((n + kGTile - 1) / kGTile);
   char* ws = nullptr;
@@ -213,25 +276,29 @@ int build_gapped(lj_index* idx, Model model, uint32_t scale, cudaStream_t s) {
   do {
     if ((ce = cudaMemsetAsync(ws, 0, 256, s)) != cudaSuccess) break;
     if (n > 0) {
-      grmi_dmax_kernel<Model><<<tiles, kGThreads, 0, s>>>(idx->R, n, leaves, model, scale, tile_max);
-      grmi_prefix_kernel<<<1, 1024, 0, s>>>(tile_max, tiles, tile_prefix, all_max);
+      grmi_dmax_kernel<Model, Slot><<<tiles, kGThreads, 0, s>>>(src, n, leaves, model, scale, tile_max);
+      grmi_prefix_kernel<false><<<1, 1024, 0, s>>>(tile_max, tiles, tile_prefix, all_max);
       if ((ce = cudaGetLastError()) != cudaSuccess) break;
       if ((ce = cudaMemcpyAsync(&h_max, all_max, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
       if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) break;
     }
     const uint64_t last = n ? (uint64_t)((int64_t)(n - 1) + h_max) : 0;   // slot of the last key
-    C = std::max<uint64_t>(n ? last + 1 : 0, (uint64_t)scale * n);
+    C = std::max<uint64_t>(n ? last + 1 : 0, min_slots);
     if (C >= 0xFFFFFFFFull) {
       rc = fail(LJ_E_INVAL, "grmi_build: %llu slots exceed the 32-bit slot range; use fewer gaps",
                 (unsigned long long)C);
       break;
     }
-    grmi_release(idx);
+    cudaFree(idx->gkeys);
+    cudaFree(idx->gpos);
+    idx->gkeys = nullptr;
+    idx->gpos = nullptr;
     if ((ce = cudaMalloc(&idx->gkeys, std::max<uint64_t>(C, 1) * 8)) != cudaSuccess) break;
     if ((ce = cudaMalloc(&idx->gpos, (C + 1) * 4)) != cudaSuccess) break;
     if (n > 0)
-      grmi_fill_kernel<Model><<<tiles, kGThreads, 0, s>>>(idx->R, n, leaves, model, scale, tile_prefix,
-                                                          idx->gkeys, idx->gpos, stats);
+      grmi_fill_kernel<Model, Slot><<<tiles, kGThreads, 0, s>>>(src, n, leaves, model, scale,
+                                                                tile_prefix, idx->gkeys, idx->gpos,
+                                                                stats);
     const uint64_t from = n ? last + 1 : 0;
     const uint64_t rest = C - from;
     const unsigned tb = (unsigned)std::min<uint64_t>(4096, std::max<uint64_t>(1, (rest + 255) / 256));
@@ -247,11 +314,47 @@ int build_gapped(lj_index* idx, Model model, uint32_t scale, cudaStream_t s) {
     return rc;
   }
   idx->gslots = (uint32_t)C;
-  idx->gscale = scale;
   idx->gstats.slots = C;
-  idx->gstats.gaps = scale - 1;
   idx->gstats.mean_disp = n ? (double)h_stats[0] / (double)n : 0.0;
   idx->gstats.max_disp = h_stats[1];
+  return 0;
+}
+
+// Distinct keys of R: dkey[D] (scratch, caller frees) and the index's
+// dfirst[D + 1] (dfirst[D] = n).
+int distinct_keys(lj_index* idx, uint64_t** dkey_out, uint64_t* D_out, cudaStream_t s) {
+  const uint64_t n = idx->n;
+  const uint32_t tiles = (uint32_t)((n + kGTile - 1) / kGTile);
+  const size_t b_tiles = ((size_t)std::max<uint32_t>(tiles, 1) * 8 + 255) / 256 * 256;
+  char* ws = nullptr;
+  LJ_CUDA(scratch_alloc((void**)&ws, 256 + 2 * b_tiles, s));
+  int64_t* total = (int64_t*)ws;
+  int64_t* tile_cnt = (int64_t*)(ws + 256);
+  int64_t* tile_off = (int64_t*)(ws + 256 + b_tiles);
+  int64_t D = 0;
+  cudaError_t ce = cudaMemsetAsync(ws, 0, 256, s);
+  if (ce == cudaSuccess && n > 0) {
+    run_count_kernel<<<tiles, kGThreads, 0, s>>>(idx->R, n, tile_cnt);
+    grmi_prefix_kernel<true><<<1, 1024, 0, s>>>(tile_cnt, tiles, tile_off, total);
+    ce = cudaMemcpyAsync(&D, total, 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  }
+  uint64_t* dkey = nullptr;
+  if (ce == cudaSuccess) ce = scratch_alloc((void**)&dkey, std::max<int64_t>(D, 1) * 8, s);
+  if (ce == cudaSuccess) ce = cudaMalloc(&idx->dfirst, (D + 1) * 4);
+  if (ce == cudaSuccess && n > 0)
+    run_write_kernel<<<tiles, kGThreads, 0, s>>>(idx->R, n, tile_off, dkey, idx->dfirst);
+  const uint32_t n32 = (uint32_t)n;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(idx->dfirst + D, &n32, 4, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  scratch_free(ws, s);
+  if (ce != cudaSuccess) {
+    if (dkey) scratch_free(dkey, s);
+    return fail_cuda(ce, "lhash_build: distinct keys");
+  }
+  *dkey_out = dkey;
+  *D_out = (uint64_t)D;
   return 0;
 }
 
@@ -260,10 +363,15 @@ int build_gapped(lj_index* idx, Model model, uint32_t scale, cudaStream_t s) {
 void grmi_release(lj_index* idx) {
   if (idx->gkeys) cudaFree(idx->gkeys);
   if (idx->gpos) cudaFree(idx->gpos);
+  if (idx->dfirst) cudaFree(idx->dfirst);
   idx->gkeys = nullptr;
   idx->gpos = nullptr;
+  idx->dfirst = nullptr;
   idx->gslots = 0;
   idx->gscale = 0;
+  idx->gkind = 0;
+  idx->ndistinct = 0;
+  idx->hbuckets = 0;
   idx->gstats = lj_grmi_stats{};
 }
 
@@ -285,10 +393,21 @@ extern "C" int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream) {
     return fail(LJ_E_CUDA, "grmi_build: cudaEventCreate failed");
   cudaEventRecord(e0, s);
   int rc;
+  grmi_release(index);
+  const GappedSlot slot{1 + gaps};
+  const uint64_t min_slots = (uint64_t)(1 + gaps) * index->n;
   if (index->precision == LJ_FP64)
-    rc = build_gapped(index, ModelF64{index->root_f64[0], index->root_f64[1], index->L}, 1 + gaps, s);
+    rc = build_gapped(index, ModelF64{index->root_f64[0], index->root_f64[1], index->L}, slot,
+                      index->R, index->n, min_slots, s);
   else
-    rc = build_gapped(index, ModelF32{index->root_f32[0], index->root_f32[1], index->L}, 1 + gaps, s);
+    rc = build_gapped(index, ModelF32{index->root_f32[0], index->root_f32[1], index->L}, slot,
+                      index->R, index->n, min_slots, s);
+  if (!rc) {
+    index->gscale = 1 + gaps;
+    index->gstats.gaps = gaps;
+    index->gstats.kind = 0;
+    index->gstats.distinct = 0;
+  }
   cudaEventRecord(e1, s);
   cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -301,6 +420,67 @@ extern "C" int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream) {
     return r2;
   }
   index->gstats.build_ms = ms;
+  return LJ_OK;
+}
+
+extern "C" int lhash_build(lj_index* index, uint32_t spk, lj_stream_t stream) {
+  using namespace lj;
+  if (!index) return fail(LJ_E_INVAL, "lhash_build: index is NULL");
+  if (spk < 1 || spk > 16) return fail(LJ_E_INVAL, "lhash_build: spk = %u must be in [1, 16]", spk);
+  if (current_device() != index->device)
+    return fail(LJ_E_INVAL, "lhash_build: index lives on device %d, current device is %d",
+                index->device, current_device());
+  if ((uint64_t)spk * index->n + 8 >= 0xFFFFFFFFull)
+    return fail(LJ_E_INVAL, "lhash_build: spk * n exceeds the 32-bit slot range");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(LJ_E_CUDA, "lhash_build: cudaEventCreate failed");
+  cudaEventRecord(e0, s);
+  grmi_release(index);
+  uint64_t* dkey = nullptr;
+  uint64_t D = 0;
+  int rc = distinct_keys(index, &dkey, &D, s);
+  if (!rc) {
+    const uint64_t B = std::max<uint64_t>(1, ((uint64_t)spk * D + 3) / 4);
+    const HashSlot slot{B, index->n + 1};
+    if (index->precision == LJ_FP64)
+      rc = build_gapped(index, ModelF64{index->root_f64[0], index->root_f64[1], index->L}, slot,
+                        dkey, D, 4 * B, s);
+    else
+      rc = build_gapped(index, ModelF32{index->root_f32[0], index->root_f32[1], index->L}, slot,
+                        dkey, D, 4 * B, s);
+    if (!rc) {
+      index->gkind = 1;
+      index->ndistinct = D;
+      index->hbuckets = B;
+      index->gstats.gaps = spk;
+      index->gstats.kind = 1;
+      index->gstats.distinct = D;
+    }
+  }
+  if (dkey) scratch_free(dkey, s);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc) rc = take_device_errors(index->device, s);
+  if (rc) {
+    grmi_release(index);
+    return rc;
+  }
+  index->gstats.build_ms = ms;
+  return LJ_OK;
+}
+
+extern "C" int lhash_export_first(const lj_index* index, uint32_t* first_host) {
+  using namespace lj;
+  if (!index || !first_host) return fail(LJ_E_INVAL, "lhash_export_first: NULL argument");
+  if (index->gkind != 1 || !index->dfirst)
+    return fail(LJ_E_STATE, "lhash_export_first: the index has no learned hash table");
+  LJ_CUDA(cudaMemcpy(first_host, index->dfirst, (index->ndistinct + 1) * 4, cudaMemcpyDeviceToHost));
   return LJ_OK;
 }
 

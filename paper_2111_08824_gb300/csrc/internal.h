@@ -25,7 +25,11 @@ struct lj_index {
   uint64_t* gkeys = nullptr;
   uint32_t* gpos = nullptr;
   uint32_t gslots = 0;           // C
-  uint32_t gscale = 0;           // 1 + gaps
+  uint32_t gscale = 0;           // 1 + gaps (gapped RMI)
+  int gkind = 0;                 // 0: gapped RMI over R's keys, 1: learned hash over distinct keys
+  uint32_t* dfirst = nullptr;    // learned hash: first position of each distinct key, D + 1
+  uint64_t ndistinct = 0;        // learned hash: D
+  uint64_t hbuckets = 0;         // learned hash: B
   lj_grmi_stats gstats{};
 };
 

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kBlock, LJ_MINB) probe_single_pass_kernel(Prob
 }
 
 // Two-pass emit: warp w of block b handles probes [b*256 + 32w, +32).
-template <class Model, bool GAPPED>
+template <class Model, int GAP>
 __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
   __shared__ uint64_t s_off[kWarps][33];
   __shared__ uint32_t s_lb[kWarps][32];
@@ -154,11 +154,12 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
     const uint64_t key = __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j);
     const typename Model::Leaf lf = Model::load_leaf(P.leaves, P.model.leaf(key));
     uint64_t xk[1] = {key};
-    if constexpr (GAPPED) {
-      uint32_t q[1] = {gapped_start(P, lf, key)};
+    if constexpr (GAP != 0) {
+      uint32_t q[1] = {gapped_start<Model, GAP == 2>(P, lf, key)};
       uint64_t v[1];
       gallop_first<1, false>(P.gkeys, P.gslots, xk, q, v);
-      lb = __ldg(P.gpos + q[0]);
+      lb = __ldg(P.gpos + q[0]);                    // GAP 2: the distinct-key rank
+      if (GAP == 2) lb = __ldg(P.dfirst + lb);      // (rank D: dfirst[D] = n, unused)
     } else {
       uint32_t wl, wh;
       window<Model>(lf, key, wl, wh);
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kBlock)
 // At the end of the chunk the block adds its probes' match count to the
 // count of their compaction tile (a chunk never straddles two): one barrier
 // and one atomic per chunk (per-warp atomics contended badly).
-template <class Model, int MODE, int CHUNK, bool VEC, bool GAPPED>
+template <class Model, int MODE, int CHUNK, bool VEC, int GAP>
 __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32_t* __restrict__ out,
                                              unsigned long long* __restrict__ tile_counts) {
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * CHUNK;
@@ -252,8 +253,8 @@ __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32
     if (j0 >= P.m) break;
     uint32_t r_idx[2], cnt[2];
     bool valid[2];
-    if constexpr (GAPPED)
-      lookup_gapped<Model, MODE, VEC>(P, j0, r_idx, cnt, valid);
+    if constexpr (GAP != 0)
+      lookup_gapped<Model, MODE, VEC, GAP == 2>(P, j0, r_idx, cnt, valid);
     else
       lookup_probes<Model, MODE, 1, VEC, LJ_ENDGAME, LJ_GUIDED, LJ_CANON>(P, j0, 0, r_idx, cnt, valid);
     uint32_t w0, w1;
@@ -296,7 +297,7 @@ template <class Model, int MODE, int CHUNK, bool VEC>
 __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
                         unsigned long long* __restrict__ tile_counts) {
-  search_chunk<Model, MODE, CHUNK, VEC, false>(P, out, tile_counts);
+  search_chunk<Model, MODE, CHUNK, VEC, 0>(P, out, tile_counts);
 }
 
 // The same with the GRMI lookup (Section 3.A): exponential search in the
@@ -305,7 +306,16 @@ template <class Model, int MODE, int CHUNK, bool VEC>
 __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     gapped_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
                          unsigned long long* __restrict__ tile_counts) {
-  search_chunk<Model, MODE, CHUNK, VEC, true>(P, out, tile_counts);
+  search_chunk<Model, MODE, CHUNK, VEC, 1>(P, out, tile_counts);
+}
+
+// The same with the learned hash index (Section 3.C): search from the first
+// slot of the probe's bucket; the entry gives the whole range of matches.
+template <class Model, int MODE, int CHUNK, bool VEC>
+__global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
+    hash_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
+                       unsigned long long* __restrict__ tile_counts) {
+  search_chunk<Model, MODE, CHUNK, VEC, 2>(P, out, tile_counts);
 }
 
 // ---------------------------------------------------------------------------
@@ -598,6 +608,10 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.gpos = idx->gpos;
   P.gslots = idx->gslots;
   P.gscale = idx->gscale;
+  P.dfirst = idx->dfirst;
+  P.ndistinct = (uint32_t)idx->ndistinct;
+  P.hB = idx->hbuckets;
+  P.hn1 = idx->n + 1;
   return P;
 }
 
@@ -754,11 +768,17 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
       return rc;
     }
   } else {
-    KernelTimer kt(P.gkeys ? "gapped_search_kernel" : "probe_search_kernel", s);
+    KernelTimer kt(!P.gkeys ? "probe_search_kernel"
+                   : idx->gkind == 1 ? "hash_search_kernel" : "gapped_search_kernel", s);
 #define LJ_SEARCH(KERNEL, MODE)                                                              \
   (vec ? KERNEL<Model, MODE, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts) \
        : KERNEL<Model, MODE, kSearchChunk, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts))
-    if (P.gkeys) {
+    if (P.gkeys && idx->gkind == 1) {
+      if (dup)
+        LJ_SEARCH(hash_search_kernel, kDupCount);
+      else
+        LJ_SEARCH(hash_search_kernel, kUniqueCount);
+    } else if (P.gkeys) {
       if (dup)
         LJ_SEARCH(gapped_search_kernel, kDupCount);
       else
@@ -840,10 +860,12 @@ int launch_emit(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
   const uint64_t blocks = (m + kBlock - 1) / kBlock;
   {
     KernelTimer kt("emit_kernel", s);
-    if (P.gkeys)
-      emit_kernel<Model, true><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+    if (P.gkeys && idx->gkind == 1)
+      emit_kernel<Model, 2><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+    else if (P.gkeys)
+      emit_kernel<Model, 1><<<(unsigned)blocks, kBlock, 0, s>>>(P);
     else
-      emit_kernel<Model, false><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+      emit_kernel<Model, 0><<<(unsigned)blocks, kBlock, 0, s>>>(P);
   }
   LJ_CUDA(cudaGetLastError());
   return 0;

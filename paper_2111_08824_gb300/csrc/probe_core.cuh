@@ -42,6 +42,12 @@ struct ProbeParams {
   const uint32_t* gpos;   // gslots + 1 payloads (positions in R)
   uint32_t gslots;        // C
   uint32_t gscale;        // 1 + gaps
+  // learned hash index (Section 3.C): payload = distinct-key rank d,
+  // matches of d = [dfirst[d], dfirst[d+1])
+  const uint32_t* dfirst;
+  uint32_t ndistinct;     // D
+  uint64_t hB;            // buckets
+  uint64_t hn1;           // n + 1
 };
 
 // Tunables (fixed at compile time; the defaults are the measured best).
@@ -509,11 +515,13 @@ __device__ __forceinline__ void gallop_first(const uint64_t* __restrict__ K, uin
   for (int p = 0; p < NP; ++p) pos[p] = lo[p];
 }
 
-// Predicted slot of x, at most C.
-template <class Model>
+// Predicted slot of x, at most C: the gapped RMI's, or the first slot of
+// x's bucket in the learned hash table (HASH).
+template <class Model, bool HASH = false>
 __device__ __forceinline__ uint32_t gapped_start(const ProbeParams<Model>& P,
                                                  const typename Model::Leaf& lf, uint64_t x) {
-  const uint64_t q = gapped_pslot<Model>(lf, x, P.gscale);
+  const uint64_t q = HASH ? HashSlot{P.hB, P.hn1}.template at<Model>(lf, x)
+                          : gapped_pslot<Model>(lf, x, P.gscale);
   return q < P.gslots ? (uint32_t)q : P.gslots;
 }
 
@@ -522,7 +530,7 @@ __device__ __forceinline__ uint32_t gapped_start(const ProbeParams<Model>& P,
 // >= x; its payload is the lower bound of x in R.  With duplicates a second
 // search from there finds the first key > x, and cnt is the difference of
 // the two payloads.
-template <class Model, int MODE, bool VEC>
+template <class Model, int MODE, bool VEC, bool HASH = false>
 __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint64_t j0,
                                               uint32_t (&r_idx)[2], uint32_t (&cnt)[2],
                                               bool (&valid)[2]) {
@@ -542,14 +550,27 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     pos[p] = P.gslots;
-    if (valid[p]) pos[p] = gapped_start(P, Model::load_leaf(P.leaves, P.model.leaf(x[p])), x[p]);
+    if (valid[p])
+      pos[p] = gapped_start<Model, HASH>(P, Model::load_leaf(P.leaves, P.model.leaf(x[p])), x[p]);
   }
   uint64_t val[2];
   gallop_first<2, false>(P.gkeys, P.gslots, x, pos, val);
   bool hit[2];
 #pragma unroll
   for (int p = 0; p < 2; ++p) hit[p] = valid[p] && pos[p] < P.gslots && val[p] == x[p];
-  if (MODE == kDupCount) {
+  if (HASH) {
+    // the entry's distinct-key rank gives the whole range of matches (the
+    // copies after the last key carry rank D: no match)
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const uint32_t d = hit[p] ? __ldg(P.gpos + pos[p]) : P.ndistinct;
+      const bool h = d < P.ndistinct;
+      const uint32_t a = h ? __ldg(P.dfirst + d) : 0u;
+      const uint32_t b = (h && MODE == kDupCount) ? __ldg(P.dfirst + d + 1) : a + 1u;
+      cnt[p] = h ? b - a : 0u;
+      r_idx[p] = a;
+    }
+  } else if (MODE == kDupCount) {
     uint32_t ub[2] = {hit[0] ? pos[0] : P.gslots, hit[1] ? pos[1] : P.gslots};
     uint64_t v2[2];
     gallop_first<2, true>(P.gkeys, P.gslots, x, ub, v2);

@@ -183,3 +183,35 @@ def test_dup_seqh_50m_gapped_counts_and_samples():
     assert lj.join_emit(idx, Ss, pairs, offsets=off_s) == tot_s
     got = pairs.cpu().numpy().view(np.uint32)
     assert np.array_equal(got, oracle.join_pairs(w.R, w.S[sample]))
+
+
+def test_dup_seqh_50m_learned_hash():
+    """Learned hash index (Section 3.C, 4 slots per distinct key) on the
+    duplicate workload: the table equals the oracle's, counts equal the
+    generated multiplicities, sampled probes' pairs equal the oracle's."""
+    lj = _lj()
+    w = datagen.dup_seqh_50m(seed=0)
+    Rd, Sd = _dev(w.R), _dev(w.S)
+    m = w.S.size
+    idx = lj.rmi_build(Rd, w.leaves, w.precision)
+    lj.lhash_build(idx, 4)
+    keys, pos = lj.grmi_export(idx)
+    want = oracle.lhash_build(w.R, oracle.rmi_fit(w.R, w.leaves, fp64=False), 4)
+    assert np.array_equal(keys, want.keys) and np.array_equal(pos, want.pos)
+    assert np.array_equal(lj.lhash_export_first(idx), want.first)
+    counts = torch.empty(m, dtype=torch.int32, device="cuda")
+    total = lj.join_count(idx, Sd, counts=counts)
+    assert total == w.meta["expected_pairs"]
+    _, vals_pos = np.unique(w.R, return_index=True)
+    mult = np.diff(np.append(vals_pos, w.R.size))
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64),
+                          mult[np.searchsorted(w.R[vals_pos], w.S)])
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(m, 1 << 16, replace=False))
+    Ss = _dev(w.S[sample])
+    first = torch.empty(sample.size, dtype=torch.int32, device="cuda")
+    off = torch.empty(sample.size + 1, dtype=torch.int64, device="cuda")
+    tot_s = lj.join_locate(idx, Ss, first, offsets=off)
+    pairs = torch.empty((tot_s, 2), dtype=torch.int32, device="cuda")
+    assert lj.join_expand(first, off, pairs) == tot_s
+    assert np.array_equal(pairs.cpu().numpy().view(np.uint32), oracle.join_pairs(w.R, w.S[sample]))
