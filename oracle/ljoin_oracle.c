@@ -323,7 +323,7 @@ uint32_t lj_oracle_rmi_lookup(const uint64_t* R, uint64_t n, uint32_t L, int fp6
 
 /* ------------------------------------------------- gapped RMI (3.A) ---- */
 /*
- * Gapped RMI (Section 3.A, "Gapped RMI (GRMI)"): a typical RMI fitted over R
+ * Gapped RMI (Section 3.A): a typical RMI fitted over R
  * places every tuple of R, in key order, by model-based insertion into two
  * gapped arrays, one of keys and one of payloads; a lookup predicts a slot
  * with the same RMI and finishes with an exponential search.  The payload of

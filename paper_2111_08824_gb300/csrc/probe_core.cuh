@@ -565,7 +565,8 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
     for (int p = 0; p < 2; ++p) {
       const uint32_t d = hit[p] ? __ldg(P.gpos + pos[p]) : P.ndistinct;
       const bool h = d < P.ndistinct;
-      const uint32_t a = h ? __ldg(P.dfirst + d) : 0u;
+      // a unique R has first[d] = d: no second load
+      const uint32_t a = h ? (P.ndistinct == P.n ? d : __ldg(P.dfirst + d)) : 0u;
       const uint32_t b = (h && MODE == kDupCount) ? __ldg(P.dfirst + d + 1) : a + 1u;
       cnt[p] = h ? b - a : 0u;
       r_idx[p] = a;

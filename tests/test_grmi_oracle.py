@@ -1,4 +1,4 @@
-"""Pins for the oracle's gapped RMI (Section 3.A, "Gapped RMI (GRMI)").
+"""Pins for the oracle's gapped RMI (Section 3.A).
 
 The gapped arrays and the GRMI lookup are pinned to things other than the
 oracle's own code:
