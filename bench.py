@@ -189,7 +189,8 @@ def _config(args, wl):
     return {"workload": wl.name, "n": int(wl.R.size), "m": int(wl.S.size),
             "leaves": int(wl.leaves), "precision": wl.precision, "seed": args.seed,
             "index": {"rmi": "rmi", "grmi": f"grmi, {args.gaps} gaps per key",
-                      "lhash": f"learned hash, {args.gaps} slots per distinct key"}[args.index],
+                      "lhash": f"learned hash, {args.gaps} slots per distinct key",
+                      "auto": "chosen by index_autotune"}[args.index],
             "probe_order": "bucketed" if args.probe_buckets else "as given",
             "l2": l2 + " (S = %.3f GB, R = %.3f GB)" % (wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
 
@@ -464,9 +465,9 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override |R| (profiling runs)")
     ap.add_argument("--m", type=int, default=None, help="override |S| (profiling runs)")
     ap.add_argument("--leaves", type=int, default=None, help="override L (profiling runs)")
-    ap.add_argument("--index", default="rmi", choices=["rmi", "grmi", "lhash"],
+    ap.add_argument("--index", default="rmi", choices=["rmi", "grmi", "lhash", "auto"],
                     help="rmi: bounded search in R; grmi: gapped RMI (exponential search); "
-                         "lhash: learned hash index")
+                         "lhash: learned hash index; auto: index_autotune on 2^22 probes")
     ap.add_argument("--gaps", type=int, default=4,
                     help="grmi: gaps per key; lhash: slots per distinct key")
     ap.add_argument("--probe-buckets", type=int, default=0, choices=[0, 1],
@@ -512,9 +513,15 @@ def main():
         s2 = st if prec == wl.precision else lj.rmi_build(Rd, L, prec).stats()
         windows[prec] = {"mean_window": s2["mean_window"], "max_window": s2["max_window"],
                          "build_ms": s2["build_ms"]}
+    lj.lj_set_option("probe_buckets", args.probe_buckets)
+    autotune = None
+    if args.index == "auto":
+        choice, ns = lj.index_autotune(idx, Sd[: min(m, 1 << 22)])
+        autotune = {"choice": choice, "ns_per_probe": ns, "sample": min(m, 1 << 22)}
     grmi = (lj.grmi_build(idx, args.gaps) if args.index == "grmi"
             else lj.lhash_build(idx, args.gaps) if args.index == "lhash" else None)
-    lj.lj_set_option("probe_buckets", args.probe_buckets)
+    if autotune and autotune["choice"] in ("grmi", "lhash"):
+        grmi = lj.grmi_stats(idx)
     stream = torch.cuda.current_stream()
 
     if unique:
@@ -630,6 +637,7 @@ def main():
         "build_ms": st["build_ms"], "mean_window": st["mean_window"],
         "max_window": st["max_window"], "windows_by_precision": windows,
         "grmi": grmi,
+        "index_autotune": autotune,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " copy bandwidth (hbm_gbs)",

@@ -189,6 +189,30 @@ int lhash_export_first(const lj_index* index, uint32_t* first_host);
  * the RMI's bounded search. */
 int grmi_drop(lj_index* index);
 
+/* Lookup structures index_autotune chooses from. */
+enum {
+  LJ_LOOKUP_RMI = 0,            /* bounded search in R, probes in S order */
+  LJ_LOOKUP_RMI_BUCKETED = 1,   /* bounded search in R, bucketed probe order */
+  LJ_LOOKUP_GRMI = 2,           /* gapped RMI, 4 gaps per key (grmi_build) */
+  LJ_LOOKUP_LHASH = 3           /* learned hash index, 4 slots per key (lhash_build) */
+};
+
+/*
+ * index_autotune -- choose the lookup structure for joins on `index`: builds
+ * each of LJ_LOOKUP_* in turn, times the count pass of the join on the
+ * sample S_sample_dev (m_sample probes, device; a uniform sample of the
+ * probes to come, ideally at least 2^22 of them) with CUDA events (best of
+ * three after a warm-up), and leaves the fastest in place: its gapped arrays
+ * if any, and the index's own probe order (which overrides the process-wide
+ * "probe_buckets" option for this index).  The RMI itself is unchanged, so
+ * results are the same whatever the choice (Sections 2.D, 3.A, 3.B, 3.C).
+ *   choice       receives LJ_LOOKUP_*
+ *   ns_per_key   optional: receives the four timings (ns per probe)
+ * Synchronises.  Errors: those of grmi_build, lhash_build and join_count.
+ */
+int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uint64_t m_sample,
+                   lj_stream_t stream, int* choice, double* ns_per_key);
+
 /* Statistics of the gapped arrays; LJ_E_STATE if the index has none. */
 int grmi_stats(const lj_index* index, lj_grmi_stats* out);
 

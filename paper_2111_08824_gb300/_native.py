@@ -79,6 +79,7 @@ SIGNATURES = {
     "grmi_build": ([_P, _U32, _P], _I),
     "lhash_build": ([_P, _U32, _P], _I),
     "lhash_export_first": ([_P, _P], _I),
+    "index_autotune": ([_P, _P, _U64, _P, _P, _P], _I),
     "grmi_drop": ([_P], _I),
     "grmi_stats": ([_P, _P], _I),
     "grmi_export": ([_P, _P, _P], _I),
@@ -238,6 +239,20 @@ def lhash_export_first(index: Index) -> np.ndarray:
     first = np.zeros(D + 1, dtype=np.uint32)
     _check(load().lhash_export_first(index.handle, _ptr(first)))
     return first
+
+
+LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash")
+
+
+def index_autotune(index: Index, S_sample, stream=None) -> tuple[str, dict]:
+    """Time the four lookup structures on a probe sample and keep the fastest;
+    returns its name and every candidate's ns per probe."""
+    _require_cuda_u64(S_sample, "S_sample")
+    choice = ctypes.c_int()
+    ns = np.zeros(4)
+    _check(load().index_autotune(index.handle, _ptr(S_sample), S_sample.numel(),
+                                 _stream_ptr(stream), ctypes.byref(choice), _ptr(ns)))
+    return LOOKUPS[choice.value], dict(zip(LOOKUPS, ns.tolist()))
 
 
 def grmi_drop(index: Index):

@@ -506,3 +506,61 @@ extern "C" int grmi_export(const lj_index* index, uint64_t* keys_host, uint32_t*
   if (pos_host) LJ_CUDA(cudaMemcpy(pos_host, index->gpos, (C + 1) * 4, cudaMemcpyDeviceToHost));
   return LJ_OK;
 }
+
+namespace lj {
+int probe_count_impl(const lj_index* idx, const uint64_t* S, uint64_t m, uint32_t* counts,
+                     uint64_t* offsets, uint32_t* first, uint64_t* total_dev, uint64_t* total_host,
+                     cudaStream_t s);
+}  // namespace lj
+
+extern "C" int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uint64_t m_sample,
+                              lj_stream_t stream, int* choice, double* ns_per_key) {
+  using namespace lj;
+  if (!index || !choice) return fail(LJ_E_INVAL, "index_autotune: NULL argument");
+  if (m_sample == 0 || !S_sample_dev) return fail(LJ_E_INVAL, "index_autotune: empty sample");
+  if (m_sample >= (1ull << 32)) return fail(LJ_E_INVAL, "index_autotune: sample too large");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  LJ_CUDA(cudaEventCreate(&e0));
+  LJ_CUDA(cudaEventCreate(&e1));
+  auto setup = [&](int c) -> int {
+    index->probe_order = c == LJ_LOOKUP_RMI_BUCKETED ? 1 : 0;
+    if (c == LJ_LOOKUP_GRMI) return grmi_build(index, 4, stream);
+    if (c == LJ_LOOKUP_LHASH) return lhash_build(index, 4, stream);
+    grmi_release(index);
+    return 0;
+  };
+  double best = 1e300;
+  int best_c = LJ_LOOKUP_RMI, rc = 0;
+  for (int c = LJ_LOOKUP_RMI; c <= LJ_LOOKUP_LHASH && !rc; ++c) {
+    if ((rc = setup(c))) break;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 4 && !rc; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = probe_count_impl(index, S_sample_dev, m_sample, nullptr, nullptr, nullptr, nullptr,
+                            nullptr, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(LJ_E_CUDA, "index_autotune: sync");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) ms = std::min(ms, t);   // the first run warms up
+    }
+    const double ns = (double)ms * 1e6 / (double)m_sample;
+    if (ns_per_key) ns_per_key[c] = ns;
+    if (!rc && ns < best) {
+      best = ns;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc) rc = take_device_errors(index->device, s);
+  if (!rc) rc = setup(best_c);
+  if (rc) {
+    grmi_release(index);
+    index->probe_order = -1;
+    return rc;
+  }
+  *choice = best_c;
+  return LJ_OK;
+}

@@ -20,6 +20,7 @@ struct lj_index {
   float root_f32[2] = {0, 0};    // deployed single-precision root
   double root_f64[2] = {0, 0};   // deployed double-precision root
   int unique = 1;
+  int probe_order = -1;          // bucketed probe order: -1 follow the option, 0 off, 1 on
   lj_index_stats stats{};
   // gapped arrays (grmi_build): C slots of keys, C + 1 payloads (positions)
   uint64_t* gkeys = nullptr;

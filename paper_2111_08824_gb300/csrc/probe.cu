@@ -762,7 +762,8 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   const bool vec = aligned(S, 16) && (!first || aligned(first, 8));
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
-  if (g_probe_buckets && !P.gkeys) {
+  const bool bucketed = idx->probe_order >= 0 ? idx->probe_order == 1 : g_probe_buckets != 0;
+  if (bucketed && !P.gkeys) {
     if (int rc = launch_bucketed(idx, P, dup, words, tile_counts, tiles, s)) {
       scratch_free(ws, s);
       return rc;

@@ -152,3 +152,22 @@ def test_degenerate_relations_and_host_join():
     with pytest.raises(lj.LJoinError) as e:
         lj.lhash_build(idx, 0)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("kind", ["lognormal", "seq_holes"])
+def test_index_autotune_keeps_results(kind):
+    """The autotuner times the four lookup structures and keeps the fastest;
+    whichever it keeps, the join equals the oracle's."""
+    lj = _lj()
+    rng = np.random.default_rng(12)
+    R = _relation(kind, 200000, rng)
+    S = _probes(R, 300000, rng)
+    want = oracle.join_pairs(R, S)
+    idx = lj.rmi_build(dev(R), 2048, "fp32")
+    choice, ns = lj.index_autotune(idx, dev(S[: 1 << 17]))
+    assert choice in lj._native.LOOKUPS and set(ns) == set(lj._native.LOOKUPS)
+    assert all(v > 0 for v in ns.values())
+    assert ns[choice] == min(ns.values())
+    for how in ("two_pass", "locate"):
+        got, total = _join(lj, idx, dev(S), S.size, how)
+        assert np.array_equal(got, want), (choice, how)
