@@ -1,13 +1,23 @@
-// Gapped RMI (Section 3.A of Sabek and Kraska, "The Case for Learned
-// In-Memory Joins"): the RMI already fitted over R places every tuple of R,
-// in key order, by model-based insertion into a gapped key array and a
-// gapped payload array; a lookup then starts at the predicted slot and
-// finishes with an exponential search (probe side: gapped_search_kernel).
+// Gapped layouts built by model-based insertion, and the choice among the
+// lookup structures (Sabek and Kraska, "The Case for Learned In-Memory
+// Joins"):
+//   gapped RMI (Section 3.A, grmi_build): the RMI already fitted over R
+//     places every tuple of R, in key order, into a gapped key array and a
+//     gapped payload array, (1 + gaps) slots per key; a lookup starts at the
+//     predicted slot and finishes with an exponential search (probe side:
+//     gapped_search_kernel);
+//   learned hash index (Section 3.C, lhash_build): the RMI as an
+//     order-preserving hash into buckets of 4 slots, one entry per distinct
+//     key of R whose payload gives its whole range of matches (probe side:
+//     hash_search_kernel);
+//   index_autotune: times the lookup structures on a probe sample and keeps
+//     the fastest.
 //
 // Model-based insertion in key order puts key i at its predicted slot, or at
 // the first slot after key i-1 if that one is later:
 //     slot_i = max(pslot_i, slot_{i-1} + 1) = i + max_{j <= i} (pslot_j - j),
-// an inclusive max-scan of d_j = pslot_j - j.  The build is three passes:
+// an inclusive max-scan of d_j = pslot_j - j (the predicted slot comes from
+// a GappedSlot or a HashSlot).  The build is three passes:
 //   grmi_dmax_kernel     per tile of 2048 keys: max of d over the tile
 //   grmi_prefix_kernel   exclusive max-scan of the tile maxima (one block)
 //   grmi_fill_kernel     per tile: slots of its keys (block max-scan seeded
@@ -16,8 +26,11 @@
 //                        own last key], takes the key and position of the
 //                        first key placed at or after it: gaps hold copies of
 //                        the next key, so the key array stays sorted
-//   grmi_tail_kernel     slots after the last key: 2^64-1 and n; pos[C] = n
-// Each slot is written once, with coalesced stores.
+//   grmi_tail_kernel     slots after the last key: 2^64-1 and the key count;
+//                        pos[C] = the key count
+// Each slot is written once, with coalesced stores.  The learned hash first
+// extracts the distinct keys of R (run_count_kernel, a sum-scan,
+// run_write_kernel) and places those.
 #include <algorithm>
 #include <climits>
 
