@@ -193,12 +193,25 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
 
 // Expansion of located ranges (join_expand): warp w of block b handles
 // probes [b*256 + 32w, +32) like emit_kernel, with each probe's first match
-// read from `first` instead of searched again.
+// read from `first` instead of searched again.  The warp's output range is
+// written in aligned groups of 4 pairs (one 32-byte store per lane), with
+// 32-bit offsets relative to the warp's first pair; a lane walks forward
+// through the warp's probes as its positions grow.
+__device__ __forceinline__ void st_pairs4(lj_pair* p, const uint32_t (&r)[4], const uint32_t (&j)[4]) {
+  const unsigned long long a = ((unsigned long long)j[0] << 32) | r[0];
+  const unsigned long long b = ((unsigned long long)j[1] << 32) | r[1];
+  const unsigned long long c = ((unsigned long long)j[2] << 32) | r[2];
+  const unsigned long long d = ((unsigned long long)j[3] << 32) | r[3];
+  asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
+               : "memory");
+}
+
 __global__ void __launch_bounds__(kBlock)
     expand_kernel(const uint32_t* __restrict__ first, const uint64_t* __restrict__ offsets,
                   uint64_t m, lj_pair* __restrict__ pairs, uint64_t capacity, uint32_t s_base,
                   uint32_t* err) {
   __shared__ uint64_t s_off[kWarps][33];
+  __shared__ uint32_t s_rel[kWarps][33];
   __shared__ uint32_t s_lb[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t j = blockIdx.x * (uint64_t)kBlock + threadIdx.x;
@@ -211,21 +224,59 @@ __global__ void __launch_bounds__(kBlock)
     if (end > off) lb = first[j];
   }
   const uint64_t rem = m > j_warp ? m - 1 - j_warp : 0;
-  const uint64_t last = rem < 31 ? rem : 31;
+  const int last = rem < 31 ? (int)rem : 31;
   s_off[warp][lane] = off;
   s_lb[warp][lane] = lb;
-  const uint64_t warp_end = __shfl_sync(0xffffffffu, end, (int)last);
+  const uint64_t warp_end = __shfl_sync(0xffffffffu, end, last);
   if (lane == 0) s_off[warp][32] = warp_end;
   __syncwarp();
   if (j_warp >= m) return;
   const uint64_t warp_start = s_off[warp][0];
   if (lane == 0 && warp_end > capacity) atomicOr(err, kErrCapacity);
   const uint64_t stop = min(warp_end, capacity);
+  if (stop <= warp_start) return;
+  const uint32_t sj = (uint32_t)(j_warp + s_base);
+  if (stop - warp_start >= (1ull << 31) ||
+      (reinterpret_cast<uintptr_t>(pairs) & 31) != 0) {   // huge ranges or an unaligned output:
+                                                           // 64-bit positions, one pair at a time
+    int p = 0;
+    for (uint64_t q = warp_start + lane; q < stop; q += 32) {
+      while (p < last && s_off[warp][p + 1] <= q) ++p;
+      pairs[q] = lj_pair{s_lb[warp][p] + (uint32_t)(q - s_off[warp][p]), sj + p};
+    }
+    return;
+  }
+  // positions relative to warp_start (32-bit); probes past `last` start at the end
+  s_rel[warp][lane] = lane <= last ? (uint32_t)(s_off[warp][lane] - warp_start)
+                                   : (uint32_t)(warp_end - warp_start);
+  if (lane == 0) s_rel[warp][32] = (uint32_t)(warp_end - warp_start);
+  __syncwarp();
+  const uint32_t total = (uint32_t)(stop - warp_start);
+  const uint32_t head = (uint32_t)((4 - (warp_start & 3)) & 3);   // pairs before the first aligned group
+  lj_pair* out = pairs + warp_start;
   int p = 0;
-  for (uint64_t q = warp_start + lane; q < stop; q += 32) {
-    while (p < (int)last && s_off[warp][p + 1] <= q) ++p;
-    pairs[q] = lj_pair{s_lb[warp][p] + (uint32_t)(q - s_off[warp][p]),
-                       (uint32_t)(j_warp + p + s_base)};
+  if ((uint32_t)lane < head && (uint32_t)lane < total) {
+    const uint32_t t = lane;
+    while (p < last && s_rel[warp][p + 1] <= t) ++p;
+    out[t] = lj_pair{s_lb[warp][p] + (t - s_rel[warp][p]), sj + p};
+  }
+  p = 0;
+  for (uint32_t t0 = head + 4u * lane; t0 < total; t0 += 128u) {
+    uint32_t r[4], jj[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t t = t0 + k;
+      while (p < last && s_rel[warp][p + 1] <= t) ++p;
+      r[k] = s_lb[warp][p] + (t - s_rel[warp][p]);
+      jj[k] = sj + p;
+    }
+    if (t0 + 4 <= total) {
+      st_pairs4(out + t0, r, jj);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (t0 + k < total) out[t0 + k] = lj_pair{r[k], jj[k]};
+    }
   }
 }
 

@@ -209,6 +209,10 @@ def test_locate_and_expand_parity(dups, prec):
     pairs = torch.full((max(total, 1), 2), -1, dtype=torch.int32, device="cuda")
     assert lj.join_expand(first, offsets, pairs) == total
     assert np.array_equal(pairs[:total].cpu().numpy().view(np.uint32), oracle.join_pairs(R, S))
+    # an output that is not 32-byte aligned takes the pair-at-a-time path
+    shifted = torch.full((total + 1, 2), -1, dtype=torch.int32, device="cuda")[1:]
+    assert lj.join_expand(first, offsets, shifted) == total
+    assert np.array_equal(shifted.cpu().numpy().view(np.uint32), oracle.join_pairs(R, S))
     # too little room: reported, the first `capacity` pairs written
     if total > 1:
         small = torch.full((total // 2, 2), -1, dtype=torch.int32, device="cuda")
