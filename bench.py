@@ -191,7 +191,7 @@ def _config(args, wl):
             "index": {"rmi": "rmi", "grmi": f"grmi, {args.gaps} gaps per key",
                       "lhash": f"learned hash, {args.gaps} slots per distinct key",
                       "auto": "chosen by index_autotune"}[args.index],
-            "probe_order": "bucketed" if args.probe_buckets else "as given",
+            "probe_order": ["as given", "bucketed", "learned sort-merge"][args.probe_buckets],
             "l2": l2 + " (S = %.3f GB, R = %.3f GB)" % (wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
 
 
@@ -470,8 +470,9 @@ def main():
                          "lhash: learned hash index; auto: index_autotune on 2^22 probes")
     ap.add_argument("--gaps", type=int, default=4,
                     help="grmi: gaps per key; lhash: slots per distinct key")
-    ap.add_argument("--probe-buckets", type=int, default=0, choices=[0, 1],
-                    help="1: probes looked up in bucketed order (option probe_buckets)")
+    ap.add_argument("--probe-buckets", type=int, default=0, choices=[0, 1, 2],
+                    help="1: probes looked up in bucketed order; 2: learned sort-merge order "
+                         "(option probe_buckets)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
@@ -620,6 +621,7 @@ def main():
         "expand_kernel": 4 * m + 8 * (m + 1) + 8 * total,    # first, offsets, pairs
         # the join's bytes again, plus the bucketed copy of S written and read
         "bucketed_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
+        "sortmerge_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
     }
     dom = max((k for k in kernels if k in alg), key=lambda k: kernels[k]["total_ms"])
     dom_ms = kernels[dom]["total_ms"] / kernels[dom]["launches"]

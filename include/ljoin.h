@@ -194,7 +194,8 @@ enum {
   LJ_LOOKUP_RMI = 0,            /* bounded search in R, probes in S order */
   LJ_LOOKUP_RMI_BUCKETED = 1,   /* bounded search in R, bucketed probe order */
   LJ_LOOKUP_GRMI = 2,           /* gapped RMI, 4 gaps per key (grmi_build) */
-  LJ_LOOKUP_LHASH = 3           /* learned hash index, 4 slots per key (lhash_build) */
+  LJ_LOOKUP_LHASH = 3,          /* learned hash index, 4 slots per key (lhash_build) */
+  LJ_LOOKUP_SORTMERGE = 4       /* bounded search in R, learned sort-merge order (Section 4) */
 };
 
 /*
@@ -207,7 +208,7 @@ enum {
  * "probe_buckets" option for this index).  The RMI itself is unchanged, so
  * results are the same whatever the choice (Sections 2.D, 3.A, 3.B, 3.C).
  *   choice       receives LJ_LOOKUP_*
- *   ns_per_key   optional: receives the four timings (ns per probe)
+ *   ns_per_key   optional: receives the five timings (ns per probe)
  * Synchronises.  Errors: those of grmi_build, lhash_build and join_count.
  */
 int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uint64_t m_sample,
@@ -493,6 +494,10 @@ void join_server_destroy(lj_server* server);
  *                      order and writes the results back to the probes' own
  *                      positions (same results, more locality in R; pays
  *                      when probes spread over an R larger than L2).
+ *                      2: learned sort-merge order (Section 4): the same
+ *                      buckets, each sorted in shared memory and merged with
+ *                      the part of R it spans (buckets above 1024 probes
+ *                      are searched probe by probe).
  *                      0 (default): probes in S order.  Gapped indexes
  *                      ignore it.
  *   "profile"          1: record CUDA events around every kernel the library

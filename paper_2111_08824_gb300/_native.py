@@ -241,15 +241,15 @@ def lhash_export_first(index: Index) -> np.ndarray:
     return first
 
 
-LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash")
+LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge")
 
 
 def index_autotune(index: Index, S_sample, stream=None) -> tuple[str, dict]:
-    """Time the four lookup structures on a probe sample and keep the fastest;
+    """Time the five lookup structures on a probe sample and keep the fastest;
     returns its name and every candidate's ns per probe."""
     _require_cuda_u64(S_sample, "S_sample")
     choice = ctypes.c_int()
-    ns = np.zeros(4)
+    ns = np.zeros(len(LOOKUPS))
     _check(load().index_autotune(index.handle, _ptr(S_sample), S_sample.numel(),
                                  _stream_ptr(stream), ctypes.byref(choice), _ptr(ns)))
     return LOOKUPS[choice.value], dict(zip(LOOKUPS, ns.tolist()))

@@ -537,7 +537,7 @@ extern "C" int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uin
   LJ_CUDA(cudaEventCreate(&e0));
   LJ_CUDA(cudaEventCreate(&e1));
   auto setup = [&](int c) -> int {
-    index->probe_order = c == LJ_LOOKUP_RMI_BUCKETED ? 1 : 0;
+    index->probe_order = c == LJ_LOOKUP_RMI_BUCKETED ? 1 : c == LJ_LOOKUP_SORTMERGE ? 2 : 0;
     if (c == LJ_LOOKUP_GRMI) return grmi_build(index, 4, stream);
     if (c == LJ_LOOKUP_LHASH) return lhash_build(index, 4, stream);
     grmi_release(index);
@@ -545,7 +545,7 @@ extern "C" int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uin
   };
   double best = 1e300;
   int best_c = LJ_LOOKUP_RMI, rc = 0;
-  for (int c = LJ_LOOKUP_RMI; c <= LJ_LOOKUP_LHASH && !rc; ++c) {
+  for (int c = LJ_LOOKUP_RMI; c <= LJ_LOOKUP_SORTMERGE && !rc; ++c) {
     if ((rc = setup(c))) break;
     float ms = 1e30f;
     for (int rep = 0; rep < 4 && !rc; ++rep) {

@@ -453,10 +453,16 @@ __global__ void __launch_bounds__(kSearchBlock)
   }
 }
 
-template <class Model, int MODE>
+constexpr uint32_t kSortMergeMax = 1024;   // largest bucket sorted and merged in shared memory
+
+// LARGE_ONLY (sort-merge order): only the entries of buckets too large for
+// sortmerge_kernel are looked up here; the others are skipped.
+template <class Model, int MODE, bool LARGE_ONLY = false>
 __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     bucketed_search_kernel(ProbeParams<Model> P, const uint64_t* __restrict__ bx,
-                           const uint32_t* __restrict__ bj, uint32_t* __restrict__ out) {
+                           const uint32_t* __restrict__ bj, uint32_t* __restrict__ out,
+                           const uint32_t* __restrict__ bkey = nullptr,
+                           const uint64_t* __restrict__ bend = nullptr) {
   const uint64_t i0 = ((uint64_t)blockIdx.x * kSearchBlock + threadIdx.x) * 2;
   uint64_t x[2];
   uint32_t j[2];
@@ -477,6 +483,16 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     x[1] = 0;
     j[1] = 0;
   }
+  if (LARGE_ONLY) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+      if (valid[p]) {
+        const uint32_t b = bkey[j[p]];
+        const uint64_t size = bend[b] - (b ? bend[b - 1] : 0);
+        valid[p] = size > kSortMergeMax;
+      }
+    if (!valid[0] && !valid[1]) return;
+  }
   uint32_t r_idx[2], cnt[2];
   lookup_keys<Model, MODE, 2>(P, x, valid, r_idx, cnt);
 #pragma unroll
@@ -485,6 +501,108 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
       out[j[p]] = MODE == kDupCount ? cnt[p] : (cnt[p] ? r_idx[p] : kNoMatch);
       if (P.first) P.first[j[p]] = r_idx[p];
     }
+}
+
+// Learned sort-merge order (Section 4, option "probe_buckets" = 2): block b
+// takes bucket b (a range of R's predicted positions within one chunk of
+// probes), sorts its keys in shared memory with a bitonic network, finds the
+// part of R the bucket spans from the lower bound of its smallest key to the
+// upper bound of its largest, and merges: each sorted key's lower (and upper)
+// bound is searched inside that part only.  Buckets larger than
+// kSortMergeMax are left to bucketed_search_kernel<..., true>.
+constexpr int kSortMergeBlock = 256;
+
+template <class Model, int MODE>
+__global__ void __launch_bounds__(kSortMergeBlock)
+    sortmerge_kernel(ProbeParams<Model> P, const uint64_t* __restrict__ bend,
+                     const uint64_t* __restrict__ bx, const uint32_t* __restrict__ bj,
+                     uint32_t* __restrict__ out) {
+  __shared__ uint64_t s_key[kSortMergeMax];
+  __shared__ uint32_t s_idx[kSortMergeMax];
+  __shared__ uint32_t s_lo, s_hi;
+  const uint32_t b = blockIdx.x;
+  const uint64_t start = b ? bend[b - 1] : 0;
+  const uint64_t k = bend[b] - start;
+  if (k == 0 || k > kSortMergeMax) return;
+  uint32_t N = 2;
+  while (N < k) N <<= 1;
+  for (uint32_t i = threadIdx.x; i < N; i += kSortMergeBlock) {   // padding sorts last,
+    s_key[i] = i < k ? bx[start + i] : ~0ull;                      // even after keys 2^64-1
+    s_idx[i] = i < k ? bj[start + i] : ~0u;
+  }
+  __syncthreads();
+  for (uint32_t size = 2; size <= N; size <<= 1) {   // bitonic sort by (key, probe), ascending
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < N / 2; i += kSortMergeBlock) {
+        const uint32_t lo = 2 * i - (i & (stride - 1));
+        const uint32_t hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t a = s_key[lo], c = s_key[hi];
+        const bool greater = a > c || (a == c && s_idx[lo] > s_idx[hi]);
+        if (greater == up) {
+          s_key[lo] = c;
+          s_key[hi] = a;
+          const uint32_t t = s_idx[lo];
+          s_idx[lo] = s_idx[hi];
+          s_idx[hi] = t;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < 2) {   // the part of R the bucket spans
+    const uint64_t x = threadIdx.x == 0 ? s_key[0] : s_key[k - 1];
+    const typename Model::Leaf lf = Model::load_leaf(P.leaves, P.model.leaf(x));
+    uint32_t wl, wh;
+    window<Model>(lf, x, wl, wh);
+    uint64_t xk[1] = {x};
+    uint32_t base[1] = {wl}, len[1] = {wh - wl};
+    uint64_t cv[1];
+    if (threadIdx.x == 0) {
+      search_last<1, true>(P.R, P.n, P.r32, xk, base, len, cv);   // lower bound of the smallest key
+      s_lo = base[0];
+    } else {
+      search_last<1, false>(P.R, P.n, P.r32, xk, base, len, cv);  // upper bound of the largest key
+      s_hi = base[0];
+    }
+  }
+  __syncthreads();
+  const uint32_t lo = s_lo, hi = s_hi;
+  auto key_at = [&](uint32_t q) -> uint64_t {
+    return __ldg(reinterpret_cast<const unsigned long long*>(P.R) + q);
+  };
+  for (uint32_t i = threadIdx.x; i < k; i += kSortMergeBlock) {
+    const uint64_t x = s_key[i];
+    uint32_t a = lo, len = hi - lo;   // lower bound in [lo, hi)
+    while (len > 0) {
+      const uint32_t half = len >> 1;
+      if (key_at(a + half) < x) {
+        a += half + 1;
+        len -= half + 1;
+      } else {
+        len = half;
+      }
+    }
+    uint32_t c = 0;
+    if (MODE == kDupCount) {
+      uint32_t u = a, ulen = hi - a;   // upper bound in [a, hi)
+      while (ulen > 0) {
+        const uint32_t half = ulen >> 1;
+        if (key_at(u + half) <= x) {
+          u += half + 1;
+          ulen -= half + 1;
+        } else {
+          ulen = half;
+        }
+      }
+      c = u - a;
+    } else {
+      c = (a < hi && key_at(a) == x) ? 1u : 0u;
+    }
+    const uint32_t j = s_idx[i];
+    out[j] = MODE == kDupCount ? c : (c ? a : kNoMatch);
+    if (P.first) P.first[j] = a;
+  }
 }
 
 // Matches per compaction tile (kCompactTile words), one block per tile.
@@ -715,7 +833,8 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
 // starts, scatter into bucket order, lookups, per-tile match counts.
 template <class Model>
 int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, uint32_t* words,
-                    unsigned long long* tile_counts, uint32_t tiles, cudaStream_t s) {
+                    unsigned long long* tile_counts, uint32_t tiles, bool sortmerge,
+                    cudaStream_t s) {
   const uint64_t m = P.m;
   const uint64_t chunks = (m + (1ull << kBucketChunkLog2) - 1) >> kBucketChunkLog2;
   const uint64_t nb = chunks * kBucketsPerChunk;
@@ -756,7 +875,24 @@ int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, 
     bucket_scatter_kernel<<<grid, kSearchBlock, 0, s>>>(P.S, m, bkey, (unsigned long long*)cursor,
                                                          bx, bj);
   }
-  {
+  if (sortmerge) {
+    {
+      KernelTimer kt("sortmerge_kernel", s);
+      if (dup)
+        sortmerge_kernel<Model, kDupCount>
+            <<<(unsigned)nb, kSortMergeBlock, 0, s>>>(P, cursor, bx, bj, words);
+      else
+        sortmerge_kernel<Model, kUniqueCount>
+            <<<(unsigned)nb, kSortMergeBlock, 0, s>>>(P, cursor, bx, bj, words);
+    }
+    KernelTimer kt("bucketed_search_kernel", s);   // buckets too large to sort in shared memory
+    if (dup)
+      bucketed_search_kernel<Model, kDupCount, true>
+          <<<grid, kSearchBlock, 0, s>>>(P, bx, bj, words, bkey, cursor);
+    else
+      bucketed_search_kernel<Model, kUniqueCount, true>
+          <<<grid, kSearchBlock, 0, s>>>(P, bx, bj, words, bkey, cursor);
+  } else {
     KernelTimer kt("bucketed_search_kernel", s);
     if (dup)
       bucketed_search_kernel<Model, kDupCount><<<grid, kSearchBlock, 0, s>>>(P, bx, bj, words);
@@ -813,9 +949,9 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   const bool vec = aligned(S, 16) && (!first || aligned(first, 8));
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
-  const bool bucketed = idx->probe_order >= 0 ? idx->probe_order == 1 : g_probe_buckets != 0;
-  if (bucketed && !P.gkeys) {
-    if (int rc = launch_bucketed(idx, P, dup, words, tile_counts, tiles, s)) {
+  const int order = idx->probe_order >= 0 ? idx->probe_order : g_probe_buckets;
+  if (order != 0 && !P.gkeys) {
+    if (int rc = launch_bucketed(idx, P, dup, words, tile_counts, tiles, order == 2, s)) {
       scratch_free(ws, s);
       return rc;
     }

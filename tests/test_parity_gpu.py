@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path against the CPU oracle, element by element.
 
-Every test runs on the three execution paths of the probe (fused
-single-pass kernel, pipeline in S order, pipeline in bucketed probe order).
+Every test runs on the four execution paths of the probe (fused
+single-pass kernel, pipeline in S order, in bucketed probe order, in learned
+sort-merge order).
 Join results are compared exactly (the pairs are a set, and both sides write
 them in the same canonical order: s_idx ascending, r_idx ascending).  Index
 builds are compared through tests/_validate.py.  Sizes span several probe
@@ -24,14 +25,15 @@ pytestmark = pytest.mark.gpu
 TOP = np.uint64(2**64 - 1)
 
 
-@pytest.fixture(params=["single_pass", "pipeline", "bucketed"], autouse=True)
+@pytest.fixture(params=["single_pass", "pipeline", "bucketed", "sortmerge"], autouse=True)
 def probe_path(request):
     """Run every test on each execution path of the probe: the fused kernel,
-    the pipeline in S order, the pipeline in bucketed probe order."""
+    the pipeline in S order, in bucketed probe order and in learned
+    sort-merge order."""
     import paper_2111_08824_gb300 as lj
     old = lj.lj_get_option("single_pass_max"), lj.lj_get_option("probe_buckets")
     lj.lj_set_option("single_pass_max", 1 << 40 if request.param == "single_pass" else 0)
-    lj.lj_set_option("probe_buckets", 1 if request.param == "bucketed" else 0)
+    lj.lj_set_option("probe_buckets", {"bucketed": 1, "sortmerge": 2}.get(request.param, 0))
     yield request.param
     lj.lj_set_option("single_pass_max", old[0])
     lj.lj_set_option("probe_buckets", old[1])
@@ -233,6 +235,9 @@ def test_join_many_chunks_ragged():
     rng = np.random.default_rng(41)
     R = np.sort(rng.integers(0, 3 * 10**6, 2 * 10**6, dtype=np.uint64))    # duplicates
     S = rng.integers(0, 3 * 10**6 + 10, (1 << 22) + 12345, dtype=np.uint64)
+    # a third of the probes on a few hot keys: buckets far above 1024 probes
+    hot = rng.random(S.size) < 0.33
+    S[hot] = R[rng.integers(0, 5, hot.sum()) * 1000]
     check_against_oracle(R, S, 20000, "fp32", "two_pass")
     Ru = np.unique(R)
     check_against_oracle(Ru, S, 20000, "fp32", "fused")
