@@ -606,7 +606,7 @@ def main():
             got = lj.join_host(idx, S_np, P_np)
             times.append(time.perf_counter() - t0)
             assert got == total
-        e2e_s = sorted(times)[len(times) // 2]  # median step
+        e2e_s = statistics.median(times)
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch)
     peak, peak_kind = _peaks()

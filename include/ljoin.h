@@ -57,7 +57,7 @@ enum {
   LJ_E_CAPACITY = -5,   /* output buffer smaller than the join result */
   LJ_E_TIMEOUT = -6,    /* a bounded device wait or a host wait ran out */
   LJ_E_BUDGET = -7,     /* request larger than the server's memory budget */
-  LJ_E_NOTUNIQUE = -8,  /* single-pass path asked for on an R with duplicates */
+  LJ_E_NOTUNIQUE = -8,  /* direct path (no offsets) asked for on an R with duplicates */
   LJ_E_STATE = -9       /* object used in a state that does not allow it */
 };
 
@@ -274,10 +274,10 @@ int join_count_noalloc(const lj_index* index, const uint64_t* S_dev, uint64_t m,
  * join_emit -- write the join pairs (Section 2.A; Section 6.B).
  *   offsets_dev   m+1 offsets from join_count (two-pass path), or NULL for
  *                 the direct path, which needs an index whose R has no
- *                 duplicate key (else LJ_E_NOTUNIQUE): lookup, scan and
- *                 write in one kernel for batches up to "single_pass_max"
- *                 keys, else a search kernel and a scan kernel that writes
- *                 the pairs.
+ *                 duplicate key (else LJ_E_NOTUNIQUE): a search kernel, a
+ *                 scan of per-tile counts and a kernel that writes the
+ *                 pairs (or, for batches up to "single_pass_max" keys, one
+ *                 fused kernel).
  *   pairs_dev     capacity pairs; pairs beyond capacity are not written.
  *   written_dev   optional device uint64: |J| (stream-ordered, no sync)
  *   written_host  optional host uint64: |J|; if given the call synchronises
@@ -323,9 +323,11 @@ int join_expand(const uint32_t* first_dev, const uint64_t* offsets_dev, uint64_t
  * join_host -- the whole join from host buffers: copies S (host, ideally
  * pinned) to the device in chunks, runs the lookup on each chunk while the
  * next one is in flight, and copies the pairs back into pairs_host
- * (capacity pairs).  s_idx values are positions in the whole S.  Uses the
- * single-pass path when R is unique, else count + emit per chunk.
- * Synchronises.  Errors: as join_emit.
+ * (capacity pairs).  s_idx values are positions in the whole S.  Per chunk:
+ * the direct path when R is unique, else join_locate + join_expand, with the
+ * pairs of one chunk copied out while the next is looked up.  Page-locked S
+ * is read in place by the kernels.  The lookup structure, probe order and
+ * options of the index apply.  Synchronises.  Errors: as join_emit.
  */
 int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
               lj_pair* pairs_host, uint64_t capacity, uint64_t* written_host,
