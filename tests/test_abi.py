@@ -43,3 +43,42 @@ def test_binding_rejects_host_tensors():
     import paper_2111_08824_gb300 as lj
     with pytest.raises(TypeError):
         lj.rmi_build(torch.zeros(4, dtype=torch.int64), 4)
+
+
+def test_options_are_validated_without_a_gpu():
+    """Process-wide options round-trip and reject out-of-range values (host
+    state only: no device call is made)."""
+    import paper_2111_08824_gb300 as lj
+    saved = {k: lj.lj_get_option(k) for k in ("single_pass_max", "host_chunk", "probe_buckets")}
+    try:
+        for v in (0, 1, 2):
+            lj.lj_set_option("probe_buckets", v)
+            assert lj.lj_get_option("probe_buckets") == v
+        lj.lj_set_option("host_chunk", 1 << 20)
+        assert lj.lj_get_option("host_chunk") == 1 << 20
+        lj.lj_set_option("single_pass_max", 12345)
+        assert lj.lj_get_option("single_pass_max") == 12345
+        for name, bad in (("probe_buckets", 3), ("probe_buckets", -1), ("host_chunk", 100),
+                          ("host_chunk", 1 << 33), ("single_pass_max", -1), ("no_such_option", 1)):
+            with pytest.raises(lj.LJoinError) as e:
+                lj.lj_set_option(name, bad)
+            assert e.value.code == -1
+        with pytest.raises(lj.LJoinError):
+            lj.lj_get_option("no_such_option")
+    finally:
+        for k, v in saved.items():
+            lj.lj_set_option(k, v)
+
+
+def test_null_arguments_are_rejected_without_a_gpu():
+    """Entry points check their arguments before touching the device."""
+    from paper_2111_08824_gb300 import _native
+    lib = _native.load()
+    assert lib.grmi_build(None, 4, None) == -1
+    assert lib.lhash_build(None, 4, None) == -1
+    assert lib.grmi_drop(None) == -1
+    assert lib.grmi_stats(None, None) == -1
+    assert lib.index_autotune(None, None, 0, None, None, None) == -1
+    assert lib.join_expand(None, None, 0, None, 0, None, None, None) == -1
+    assert lib.join_host(None, None, 0, None, 0, None, None) == -1
+    assert b"NULL" in lib.lj_last_error() or b"null" in lib.lj_last_error().lower()
