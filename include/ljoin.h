@@ -481,7 +481,8 @@ void join_server_destroy(lj_server* server);
 /* ------------------------------------------------------ diagnostics ----- */
 
 /*
- * lj_set_option / lj_get_option -- process-wide tuning knobs.
+ * lj_set_option / lj_get_option -- process-wide tuning knobs (atomic: a call
+ * in flight uses the value it read when it started).
  *   "single_pass_max"  probe batches of at most this many keys use the
  *                      single-pass kernel (lookup + scan + write in one
  *                      launch); larger ones use the count-scan-emit pipeline

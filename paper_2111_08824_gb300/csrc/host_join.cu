@@ -12,6 +12,7 @@
 // -> expand the ranges into pairs -> copy out on alternating copy streams
 // while the next chunk is located.
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "device_common.cuh"
@@ -46,7 +47,7 @@ struct Streams {
 
 namespace lj {
 // probe keys per chunk of a host join (option "host_chunk")
-uint64_t g_host_chunk = 1ull << 25;
+std::atomic<uint64_t> g_host_chunk{1ull << 25};
 void set_host_chunk(uint64_t v) { g_host_chunk = v; }
 uint64_t get_host_chunk() { return g_host_chunk; }
 }  // namespace lj
@@ -76,7 +77,7 @@ extern "C" int join_host(const lj_index* idx, const uint64_t* S_host, uint64_t m
   cudaEvent_t* in_done = st.ev;        // [2]
   cudaEvent_t* comp_done = st.ev + 2;  // [2]
   cudaEvent_t* out_done = st.ev + 4;   // [2]
-  const uint64_t chunk = std::min<uint64_t>(m, std::max<uint64_t>(g_host_chunk, 1u << 16));
+  const uint64_t chunk = std::min<uint64_t>(m, std::max<uint64_t>(g_host_chunk.load(), 1u << 16));
   const uint64_t nchunks = (m + chunk - 1) / chunk;
   uint64_t written = 0;
   // page-locked (or registered) S can be read by the kernels in place

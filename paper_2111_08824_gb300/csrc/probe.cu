@@ -34,6 +34,7 @@
 //     each probe's lower bound and lets each warp write the contiguous
 //     output range of its 32 probes with coalesced 8-byte stores.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -49,12 +50,12 @@ namespace {
 // the pipeline against 28-170 us in the single-pass kernel, whose blocks of
 // 2048 probes leave most SMs idle on small batches and wait in the
 // look-back on large ones.
-uint64_t g_single_pass_max = 0;
+std::atomic<uint64_t> g_single_pass_max{0};
 
 // Bucketed probe order in the pipeline (option "probe_buckets"; off by
 // default: it pays where probes spread over an R larger than L2, and costs
 // where they concentrate on a few hot regions).
-int g_probe_buckets = 0;
+std::atomic<int> g_probe_buckets{0};
 
 // Writes of one round: pairs (kUniqueEmit) or counts / offsets.
 template <class Model, int MODE, bool VEC>
@@ -949,7 +950,7 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   const bool vec = aligned(S, 16) && (!first || aligned(first, 8));
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
-  const int order = idx->probe_order >= 0 ? idx->probe_order : g_probe_buckets;
+  const int order = idx->probe_order >= 0 ? idx->probe_order : g_probe_buckets.load();
   if (order != 0 && !P.gkeys) {
     if (int rc = launch_bucketed(idx, P, dup, words, tile_counts, tiles, order == 2, s)) {
       scratch_free(ws, s);
@@ -1029,7 +1030,7 @@ int launch_probe(const lj_index* idx, Model model, int mode, const uint64_t* S, 
                  lj_pair* pairs, uint64_t cap, uint32_t* counts, uint64_t* offsets,
                  uint32_t* first, uint64_t* total_dev, uint64_t* total_host, uint32_t s_base,
                  cudaStream_t s) {
-  if (m <= g_single_pass_max && !idx->gkeys)   // the GRMI lookup runs in the pipeline only
+  if (m <= g_single_pass_max.load() && !idx->gkeys)   // the GRMI lookup runs in the pipeline only
     return launch_single_pass(idx, model, mode, S, m, pairs, cap, counts, offsets, first,
                               total_dev, total_host, s_base, s);
   return launch_pipeline(idx, model, mode, S, m, pairs, cap, counts, offsets, first, total_dev,
