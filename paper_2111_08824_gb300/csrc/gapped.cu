@@ -257,6 +257,20 @@ __global__ void __launch_bounds__(kGThreads)
   }
 }
 
+// Learned hash: every slot's range (first position | count << 32) from its
+// payload (the distinct-key rank d): [first[d], first[d+1]); rank D: none.
+__global__ void lhash_range_kernel(const uint32_t* __restrict__ gpos,
+                                   const uint32_t* __restrict__ dfirst, uint64_t C, uint32_t D,
+                                   uint64_t* __restrict__ hrange) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < C;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t d = gpos[s];
+    const uint32_t a = dfirst[d];   // d <= D, dfirst[D] = n
+    const uint32_t c = d < D ? dfirst[d + 1] - a : 0u;
+    hrange[s] = ((uint64_t)c << 32) | a;
+  }
+}
+
 __global__ void grmi_tail_kernel(uint64_t* __restrict__ gkeys, uint32_t* __restrict__ gpos,
                                  uint64_t from, uint64_t C, uint32_t n) {
   for (uint64_t s = from + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < C;
@@ -377,9 +391,11 @@ void grmi_release(lj_index* idx) {
   if (idx->gkeys) cudaFree(idx->gkeys);
   if (idx->gpos) cudaFree(idx->gpos);
   if (idx->dfirst) cudaFree(idx->dfirst);
+  if (idx->hrange) cudaFree(idx->hrange);
   idx->gkeys = nullptr;
   idx->gpos = nullptr;
   idx->dfirst = nullptr;
+  idx->hrange = nullptr;
   idx->gslots = 0;
   idx->gscale = 0;
   idx->gkind = 0;
@@ -463,6 +479,17 @@ extern "C" int lhash_build(lj_index* index, uint32_t spk, lj_stream_t stream) {
     else
       rc = build_gapped(index, ModelF32{index->root_f32[0], index->root_f32[1], index->L}, slot,
                         dkey, D, 4 * B, s);
+    if (!rc) {   // per-slot ranges, so that a probe reads its matches with one load
+      const uint64_t C = index->gslots;
+      cudaError_t ce = cudaMalloc(&index->hrange, std::max<uint64_t>(C, 1) * 8);
+      if (ce == cudaSuccess) {
+        const unsigned g = (unsigned)std::min<uint64_t>(8192, std::max<uint64_t>(1, (C + 255) / 256));
+        lhash_range_kernel<<<g, 256, 0, s>>>(index->gpos, index->dfirst, C, (uint32_t)D,
+                                              index->hrange);
+        ce = cudaGetLastError();
+      }
+      if (ce != cudaSuccess) rc = fail_cuda(ce, "lhash_build: slot ranges");
+    }
     if (!rc) {
       index->gkind = 1;
       index->ndistinct = D;

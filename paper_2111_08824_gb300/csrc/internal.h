@@ -29,6 +29,7 @@ struct lj_index {
   uint32_t gscale = 0;           // 1 + gaps (gapped RMI)
   int gkind = 0;                 // 0: gapped RMI over R's keys, 1: learned hash over distinct keys
   uint32_t* dfirst = nullptr;    // learned hash: first position of each distinct key, D + 1
+  uint64_t* hrange = nullptr;    // learned hash: per slot, first | count << 32 of its entry
   uint64_t ndistinct = 0;        // learned hash: D
   uint64_t hbuckets = 0;         // learned hash: B
   lj_grmi_stats gstats{};

@@ -779,6 +779,7 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.gslots = idx->gslots;
   P.gscale = idx->gscale;
   P.dfirst = idx->dfirst;
+  P.hrange = idx->hrange;
   P.ndistinct = (uint32_t)idx->ndistinct;
   P.hB = idx->hbuckets;
   P.hn1 = idx->n + 1;

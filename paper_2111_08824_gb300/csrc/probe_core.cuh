@@ -45,6 +45,7 @@ struct ProbeParams {
   // learned hash index (Section 3.C): payload = distinct-key rank d,
   // matches of d = [dfirst[d], dfirst[d+1])
   const uint32_t* dfirst;
+  const uint64_t* hrange; // per slot: first | count << 32 of the slot's entry (count 0: none)
   uint32_t ndistinct;     // D
   uint64_t hB;            // buckets
   uint64_t hn1;           // n + 1
@@ -559,17 +560,15 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
 #pragma unroll
   for (int p = 0; p < 2; ++p) hit[p] = valid[p] && pos[p] < P.gslots && val[p] == x[p];
   if (HASH) {
-    // the entry's distinct-key rank gives the whole range of matches (the
-    // copies after the last key carry rank D: no match)
+    // one 8-byte load gives the slot's whole range of matches (the copies
+    // after the last key carry count 0: no match)
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-      const uint32_t d = hit[p] ? __ldg(P.gpos + pos[p]) : P.ndistinct;
-      const bool h = d < P.ndistinct;
-      // a unique R has first[d] = d: no second load
-      const uint32_t a = h ? (P.ndistinct == P.n ? d : __ldg(P.dfirst + d)) : 0u;
-      const uint32_t b = (h && MODE == kDupCount) ? __ldg(P.dfirst + d + 1) : a + 1u;
-      cnt[p] = h ? b - a : 0u;
-      r_idx[p] = a;
+      const uint64_t rg = hit[p] ? __ldg(reinterpret_cast<const unsigned long long*>(P.hrange) + pos[p])
+                                 : 0ull;
+      const uint32_t c = (uint32_t)(rg >> 32);
+      cnt[p] = MODE == kDupCount ? c : (c ? 1u : 0u);
+      r_idx[p] = (uint32_t)rg;
     }
   } else if (MODE == kDupCount) {
     uint32_t ub[2] = {hit[0] ? pos[0] : P.gslots, hit[1] ? pos[1] : P.gslots};
