@@ -172,7 +172,8 @@ int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream);
  * probing; the hash is monotone, so the table stays sorted and a free slot
  * holds a copy of the next entry).  An entry's payload is the rank d of its
  * key among the distinct keys; first[d] is the position of its first copy in
- * R, first[D] = n, and its matches are R's positions [first[d], first[d+1]).
+ * R, first[D] = n, and its matches are R's positions [first[d], first[d+1]);
+ * each slot also stores that range (8 bytes), so a hit reads it with one load.
  * Lookups hash the probe and search forward from its bucket (exponential
  * steps, then a binary search); duplicates need no second search.  Joins on
  * the index then behave as after grmi_build (same results, same paths).
