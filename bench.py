@@ -171,6 +171,8 @@ def _overrides(args) -> dict:
         kw["m"] = args.m
     if args.leaves is not None:
         kw["leaves"] = args.leaves
+    if args.workload == "dup_seqh_50m":
+        kw["reading"] = args.dup_reading
     return kw
 
 
@@ -470,6 +472,8 @@ def main():
                          "lhash: learned hash index; auto: index_autotune on 2^22 probes")
     ap.add_argument("--gaps", type=int, default=4,
                     help="grmi: gaps per key; lhash: slots per distinct key")
+    ap.add_argument("--dup-reading", default="clip", choices=["clip", "truncate"],
+                    help="dup_seqh_50m: Zipf(1.2) multiplicity clipped at 64, or truncated to 1..64")
     ap.add_argument("--probe-buckets", type=int, default=0, choices=[0, 1, 2],
                     help="1: probes looked up in bucketed order; 2: learned sort-merge order "
                          "(option probe_buckets)")

@@ -182,6 +182,16 @@ def zipf_clipped_table(s: float, cap: int) -> np.ndarray:
     return cdf
 
 
+def zipf_truncated_table(s: float, cap: int) -> np.ndarray:
+    """CDF over k = 1..cap of a Zipf(s) truncated to support 1..cap (mass
+    renormalised over the support)."""
+    k = np.arange(1, cap + 1, dtype=np.float64)
+    p = k ** -s
+    cdf = np.cumsum(p / p.sum())
+    cdf[-1] = 1.0
+    return cdf
+
+
 # --------------------------------------------------------------------------
 # Workloads
 # --------------------------------------------------------------------------
@@ -260,11 +270,15 @@ def lognormal_100m(seed: int = 0, n: int = 100_000_000, m: int = 400_000_000,
 
 
 def dup_seqh(rows: int, seed: int, skip_p: float = 0.1, s: float = 1.2,
-             cap: int = 64) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+             cap: int = 64, reading: str = "clip") -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     """Sequential keys from 0 with each value skipped with probability
-    skip_p; each kept value repeated min(Zipf(s), cap) times; truncated to
-    `rows` rows. Returns (R sorted, distinct keys, multiplicity per key)."""
-    cdf = zipf_clipped_table(s, cap)
+    skip_p; each kept value repeated min(Zipf(s), cap) times ("clip": an
+    unbounded Zipf clipped at cap) or a Zipf truncated to 1..cap times
+    ("truncate"); truncated to `rows` rows. Returns (R sorted, distinct keys,
+    multiplicity per key)."""
+    if reading not in ("clip", "truncate"):
+        raise ValueError(reading)
+    cdf = zipf_clipped_table(s, cap) if reading == "clip" else zipf_truncated_table(s, cap)
     keep_p = 1.0 - skip_p
     mean_mult = float(np.sum(np.diff(np.concatenate([[0.0], cdf])) *
                              np.arange(1, cap + 1)))
@@ -288,14 +302,18 @@ def dup_seqh(rows: int, seed: int, skip_p: float = 0.1, s: float = 1.2,
 
 
 def dup_seqh_50m(seed: int = 0, rows: int = 50_000_000, m: int = 200_000_000,
-                 leaves: int = 1 << 18) -> Workload:
-    """R: duplicated sequential-with-holes keys; S: uniform over distinct keys."""
-    R, vals, mult = dup_seqh(rows, seed)
+                 leaves: int = 1 << 18, reading: str = "clip") -> Workload:
+    """R: duplicated sequential-with-holes keys; S: uniform over distinct keys.
+    `reading` picks how "Zipf(1.2) capped at 64" is read: "clip" (an unbounded
+    draw clipped at 64, mean multiplicity ~31) or "truncate" (support 1..64,
+    mean ~10)."""
+    R, vals, mult = dup_seqh(rows, seed, reading=reading)
     pick = bounded(rand_u64(seed, ST_S_HIT, 0, m), vals.size).astype(np.int64)
     S = vals[pick]
     expected = int(np.sum(mult[pick], dtype=np.int64))
     return Workload("dup_seqh_50m", R, S, leaves, "fp32",
-                    {"expected_pairs": expected, "distinct": int(vals.size)})
+                    {"expected_pairs": expected, "distinct": int(vals.size),
+                     "zipf_reading": reading})
 
 
 def clustered_keys(n: int, seed: int, clusters: int = 64,

@@ -29,3 +29,25 @@ def test_batched_workload_shapes_cpu():
         assert np.all(np.diff(Ru.astype(np.float64)) >= 0) and np.unique(Ru).size == Ru.size
     assert {j["dist"] for j in dg.batched_workload(k=30, seed=2, device="cpu", scale=1 / 1024)} \
         == set(dg.DISTRIBUTIONS)
+
+
+def test_duplicate_multiplicity_readings():
+    """"Zipf(1.2) capped at 64": clipped, P(64) ~ 0.39 and mean ~ 31; truncated
+    to 1..64, mean ~ 10 (closed forms of the two distributions)."""
+    import math
+    import datagen
+    s, cap = 1.2, 64
+    clip = datagen.zipf_clipped_table(s, cap)
+    trunc = datagen.zipf_truncated_table(s, cap)
+    k = np.arange(1, cap + 1)
+    mean = lambda cdf: float(np.sum(np.diff(np.concatenate([[0.0], cdf])) * k))
+    z = datagen.zeta(math.inf, s)
+    assert abs((1 - clip[-2]) - (z - np.sum(np.arange(1, cap) ** -s)) / z) < 1e-9
+    assert 0.37 < 1 - clip[-2] < 0.41 and 29 < mean(clip) < 33
+    assert abs(mean(trunc) - np.sum(k ** (1 - s)) / np.sum(k ** -s)) < 1e-9
+    assert 9.5 < mean(trunc) < 10.5 and trunc[-1] == 1.0
+    for reading, lo, hi in (("clip", 28, 34), ("truncate", 9, 11)):
+        R, vals, mult = datagen.dup_seqh(200_000, 3, reading=reading)
+        assert R.size == 200_000 and np.all(np.diff(R.astype(np.int64)) >= 0)
+        assert mult.min() >= 1 and mult.max() <= cap and lo < mult.mean() < hi
+        assert np.array_equal(np.repeat(vals, mult), R)
