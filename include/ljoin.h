@@ -8,7 +8,11 @@
  *                model picks a leaf model, the leaf's linear model predicts
  *                a position, per-leaf min/max error bounds delimit a binary
  *                search.
- *   Section 3    RMI-INLJ: index R with an RMI, probe it with every s.
+ *   Section 3    RMI-INLJ: index R with an RMI, probe it with every s;
+ *                3.A gapped RMI (grmi_build), 3.B buffered probing (the
+ *                bucketed probe order), 3.C learned hash index
+ *                (lhash_build).
+ *   Section 4    learned sort-merge join (the sort-merge probe order).
  *   Section 6.A  the index is built before the join; its build time is not
  *                part of the join (Section 3.A).
  *   Section 6.B  duplicate keys: a range scan between the error bounds
