@@ -62,9 +62,9 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
-            self.fh = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="lj_clocks_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "50"],
@@ -95,6 +95,10 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() in ("active", "1", "yes"):
                     reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
@@ -129,8 +133,25 @@ def weak_value(world: int, units_per_rank: int, ms_per_step: float) -> float:
     return world * units_per_rank / (ms_per_step / 1e3)
 
 
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
 def run_reference(args, rank, world):
-    """CPU oracle (sort-merge) on bounded samples of the same workload."""
+    """CPU oracle (sort-merge) on bounded samples of the same workload, on
+    every host core (chunks of S on parallel threads)."""
     import oracle
     if rank != 0:
         return
@@ -138,12 +159,13 @@ def run_reference(args, rank, world):
     wl = w["fn"](seed=args.seed, **_overrides(args))
     m_s = min(wl.S.size, args.ref_sample)
     oracle.build()
+    cores = oracle.host_threads()
     times = []
     for step in range(args.warmup + args.steps):
         off = (step * m_s) % max(1, wl.S.size - m_s + 1)
         S = wl.S[off:off + m_s]
         t0 = time.perf_counter()
-        _, _, total = oracle.join_ranges(wl.R, S)
+        oracle.join_ranges_mt(wl.R, S, threads=cores)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
@@ -155,8 +177,10 @@ def run_reference(args, rank, world):
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": _config(args, wl),
-        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{m_s} probes of S per step against the full R"},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": cores, "kind": "oracle",
+                         "cpu": _cpu_model(),
+                         "sample": f"{m_s} probes of S per step against the full R, "
+                                   f"{cores} threads"},
         "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -221,16 +245,25 @@ def _ncu_traffic(kernel: str, args) -> float | None:
     return d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch")
 
 
-def cpu_baseline(wl, sample: int) -> dict:
+def cpu_baseline(wl, sample: int, sample_1t: int) -> dict:
+    """The oracle (sort-merge) as it stands, on every host core and on one
+    thread, over bounded samples of S against the full R."""
     import oracle
     oracle.build()
+    cores = oracle.host_threads()
     m_s = min(sample, wl.S.size)
-    S = wl.S[:m_s]
     t0 = time.perf_counter()
-    oracle.join_ranges(wl.R, S)
+    oracle.join_ranges_mt(wl.R, wl.S[:m_s], threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": m_s / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {m_s} probes of S against the full R ({dt:.1f} s, single thread)"}
+    m1 = min(sample_1t, wl.S.size)
+    t0 = time.perf_counter()
+    oracle.join_ranges(wl.R, wl.S[:m1])
+    dt1 = time.perf_counter() - t0
+    return {"value": m_s / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
+            "cpu": _cpu_model(),
+            "sample": f"first {m_s} probes of S against the full R ({dt:.2f} s on {cores} threads)",
+            "one_thread": {"value": m1 / dt1, "unit": "keys/s",
+                           "sample": f"first {m1} probes of S ({dt1:.2f} s)"}}
 
 
 def run_batched(args, rank, world, dist):
@@ -461,12 +494,15 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="batched workload: size scale")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 25)
-    ap.add_argument("--ref-sample", type=int, default=1 << 23)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 27)
+    ap.add_argument("--cpu-sample-1t", type=int, default=1 << 23)
+    ap.add_argument("--ref-sample", type=int, default=1 << 25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override |R| (profiling runs)")
     ap.add_argument("--m", type=int, default=None, help="override |S| (profiling runs)")
     ap.add_argument("--leaves", type=int, default=None, help="override L (profiling runs)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"],
+                    help="override the workload's model precision")
     ap.add_argument("--index", default="rmi", choices=["rmi", "grmi", "lhash", "auto"],
                     help="rmi: bounded search in R; grmi: gapped RMI (exponential search); "
                          "lhash: learned hash index; auto: index_autotune on 2^22 probes")
@@ -505,6 +541,8 @@ def main():
     # weak scaling: every rank probes its own S (seeded by rank) against the
     # replicated R; no collective on the data path.
     wl = w["fn"](seed=args.seed + 1000 * rank, **_overrides(args))
+    if args.precision:
+        wl.precision = args.precision
     n, m, L = wl.R.size, wl.S.size, wl.leaves
 
     Rd = torch.from_numpy(wl.R.view(np.int64)).cuda()
@@ -661,7 +699,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample)
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample, args.cpu_sample_1t)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -269,7 +269,11 @@ int join_count(const lj_index* index, const uint64_t* S_dev, uint64_t m,
  *       overlap on the GPU (different streams without ordering, several host
  *       threads) race and give wrong results; order them on one stream.
  *   The array keeps the last call's contents; each call clears what must
- *   start at zero (ticket, tile flags, error word) on `stream`.
+ *   start at zero (ticket, tile flags) on `stream`.  Errors of the kernel
+ *   (a look-back wait that ran out) go to an error word in the array: a call
+ *   with total_host reports them (LJ_E_TIMEOUT) and clears the word; the
+ *   error of a call without total_host stays there until the next call on the
+ *   device that passes total_host.
  */
 int join_count_noalloc(const lj_index* index, const uint64_t* S_dev, uint64_t m,
                        uint32_t* counts_dev, uint64_t* offsets_dev, uint64_t* total_host,
@@ -445,29 +449,37 @@ typedef struct {
   double p50_us, p99_us, mean_us, max_us;
   double span_s;               /* first submit -> last completion */
   double keys_per_s;           /* probe keys completed / span */
+  uint64_t resident;           /* bytes of the registered relations (keys + leaf records),
+                                  part of mem_in_use */
 } lj_server_stats;
 
 /*
  * Serving: resident learned indexes answer probe requests with continuous
  * batching.  Each request is one join (Section 2.A probe of its keys against
  * a resident relation's index, Section 2.D), answered exactly as join_emit
- * would answer it alone.  A scheduler thread admits pending requests first
- * come, first served, when an in-flight slot is free and the memory they need
- * (12 bytes per probe: 8 for pairs, 4 for search words) fits the budget;
+ * would answer it alone.  The budget covers the registered relations (their
+ * keys and leaf records, charged when added) and the requests in flight.  A
+ * scheduler thread admits pending requests first come, first served, when an
+ * in-flight slot is free and the memory they need (12 bytes per probe: 8 for
+ * pairs, 4 for search words) fits what the budget has left;
  * every admitted group runs as one batched launch on its slot's stream, so
  * batches admitted while others run overlap on the device.
  *
  * join_server_create   start a server on the current device.
  * join_server_add_relation  register a built index (unique R, one precision
  *                      for all relations; borrowed); returns its id.
+ *                      LJ_E_BUDGET if its keys and leaf records do not fit
+ *                      the budget left.
  * join_submit          queue a request: m probe keys at S (device or
  *                      page-locked host memory, valid until the request
  *                      completes).  Returns at once.  LJ_E_BUDGET if the
- *                      request alone exceeds the budget.
+ *                      request alone exceeds what the relations leave of the
+ *                      budget.
  * join_wait            wait (timeout_us < 0: forever) for a request;
  *                      LJ_E_TIMEOUT if it is not done in time.
  * join_fetch           copy a completed request's pairs to dst_dev
- *                      (stream-ordered on `stream`).
+ *                      (stream-ordered on `stream`; a later join_release
+ *                      frees the pairs only after that copy).
  * join_release         drop a completed request and free its pairs.
  * join_server_stats    counters and latency percentiles (reset: clear them).
  * join_server_destroy  finish queued work, stop the scheduler, free all.
@@ -508,6 +520,17 @@ void join_server_destroy(lj_server* server);
  *                      are searched probe by probe).
  *                      0 (default): probes in S order.  Gapped indexes
  *                      ignore it.
+ *   "lookback_polls"   bound of one decoupled look-back wait of the probe
+ *                      kernels: polls of a predecessor tile's state before the
+ *                      tile gives up, records LJ_E_TIMEOUT in the error word
+ *                      and goes on (16 .. 2^20; default 2^20).
+ *   "fault_skip_tiles" fault injection for tests (0 .. 1024; default 0): the
+ *                      single-pass kernel (single_pass_max, join_count_noalloc)
+ *                      skips this many leading tiles, which then never publish
+ *                      their state, so the look-back waits of the next tiles
+ *                      run out and the call reports LJ_E_TIMEOUT (no device
+ *                      trap; the context stays usable).  Results of such a
+ *                      call are unspecified.
  *   "profile"          1: record CUDA events around every kernel the library
  *                      launches (on the launch's stream); lj_profile_report
  *                      returns the per-kernel totals.  0 (default): off.

@@ -12,7 +12,9 @@ Python, used only on tiny inputs to pin the C sort-merge.
 Functions and the passages they follow (Sabek and Kraska, "The Case for
 Learned In-Memory Joins"):
   join_ranges / join_pairs   Section 2.A (indexed nested loop join) and
-                             Section 6.B (duplicates return all matches)
+                             Section 6.B (duplicates return all matches);
+                             join_ranges_mt runs join_ranges on chunks of S
+                             on every host core
   rmi_fit / rmi_lookup       Section 2.D (two-level RMI with per-leaf
                              min/max error bounds and a bounded search)
   grmi_build / grmi_join     Section 3.A (gapped RMI: model-based insertion
@@ -127,6 +129,46 @@ def join_ranges(R, S) -> tuple[np.ndarray, np.ndarray, int]:
         raise OracleError("R is not sorted non-decreasing")
     if total < 0:
         raise MemoryError("oracle ran out of memory")
+    return lo, hi, int(total)
+
+
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:          # not Linux
+        return os.cpu_count() or 1
+
+
+def join_ranges_mt(R, S, threads: int | None = None, chunk: int = 1 << 20
+                   ) -> tuple[np.ndarray, np.ndarray, int]:
+    """join_ranges over contiguous chunks of S on `threads` host threads (all
+    cores by default).  Each chunk is one unchanged call of the C sort-merge
+    (ctypes releases the GIL during the call), writing its slice of lo / hi;
+    per-probe ranges do not depend on the chunking."""
+    from concurrent.futures import ThreadPoolExecutor
+    R, S = _u64(R), _u64(S)
+    threads = threads or host_threads()
+    lo = np.zeros(S.size, dtype=np.uint64)
+    hi = np.zeros(S.size, dtype=np.uint64)
+    lib = _load()
+    if S.size and not lib.lj_oracle_is_sorted(_ptr(R), R.size):
+        raise OracleError("R is not sorted non-decreasing")
+    bounds = [(a, min(S.size, a + chunk)) for a in range(0, S.size, chunk)]
+
+    def one(ab):
+        a, b = ab
+        t = lib.lj_oracle_join_ranges(_ptr(R), R.size, _ptr(S[a:b]), b - a,
+                                      _ptr(lo[a:b]), _ptr(hi[a:b]))
+        if t < 0:
+            raise MemoryError("oracle ran out of memory") if t == -2 else OracleError("unsorted R")
+        return t
+
+    if threads <= 1 or len(bounds) <= 1:
+        total = sum(one(ab) for ab in bounds)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            total = sum(ex.map(one, bounds))
     return lo, hi, int(total)
 
 

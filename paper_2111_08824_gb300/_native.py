@@ -63,7 +63,8 @@ class lj_server_stats(ctypes.Structure):
                 ("mem_in_use", ctypes.c_uint64), ("mem_peak", ctypes.c_uint64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
                 ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
-                ("span_s", ctypes.c_double), ("keys_per_s", ctypes.c_double)]
+                ("span_s", ctypes.c_double), ("keys_per_s", ctypes.c_double),
+                ("resident", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()

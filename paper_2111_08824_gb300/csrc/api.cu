@@ -127,6 +127,15 @@ KernelTimer::~KernelTimer() {
   g_prof.push_back({name_, a_, b_});
 }
 
+// Bound of one look-back wait (polls of a predecessor tile) and the test
+// hook that makes such a wait run out (see lj_set_option).
+namespace {
+std::atomic<uint32_t> g_lookback_polls{kLookbackPolls};
+std::atomic<uint32_t> g_fault_skip_tiles{0};
+}  // namespace
+uint32_t lookback_polls() { return g_lookback_polls.load(); }
+uint32_t fault_skip_tiles() { return g_fault_skip_tiles.load(); }
+
 }  // namespace lj
 
 extern "C" {
@@ -154,6 +163,17 @@ int lj_set_option(const char* name, int64_t value) {
     set_host_chunk((uint64_t)value);
     return LJ_OK;
   }
+  if (!strcmp(name, "lookback_polls")) {
+    if (value < 16 || value > (int64_t)kLookbackPolls)
+      return fail(LJ_E_INVAL, "lookback_polls must be in [16, 2^20]");
+    g_lookback_polls = (uint32_t)value;
+    return LJ_OK;
+  }
+  if (!strcmp(name, "fault_skip_tiles")) {
+    if (value < 0 || value > 1024) return fail(LJ_E_INVAL, "fault_skip_tiles must be in [0, 1024]");
+    g_fault_skip_tiles = (uint32_t)value;
+    return LJ_OK;
+  }
   return fail(LJ_E_INVAL, "lj_set_option: unknown option '%s'", name);
 }
 
@@ -163,6 +183,8 @@ int64_t lj_get_option(const char* name) {
   if (name && !strcmp(name, "profile")) return profiling() ? 1 : 0;
   if (name && !strcmp(name, "host_chunk")) return (int64_t)get_host_chunk();
   if (name && !strcmp(name, "probe_buckets")) return get_probe_buckets();
+  if (name && !strcmp(name, "lookback_polls")) return lookback_polls();
+  if (name && !strcmp(name, "fault_skip_tiles")) return fault_skip_tiles();
   fail(LJ_E_INVAL, "lj_get_option: unknown option '%s'", name ? name : "(null)");
   return -1;
 }

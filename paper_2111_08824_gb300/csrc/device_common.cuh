@@ -12,23 +12,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#ifndef LJ_L2HINT
-#define LJ_L2HINT 0   // L2 eviction priorities: keep R and leaf records, stream S and results (measured slower)
-#endif
-
 namespace lj {
-
-// L2 cache policies (createpolicy has no side effects: the compiler may hoist it).
-__device__ __forceinline__ uint64_t l2_keep() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_stream() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
 
 constexpr float kPredClampF = 1099511627776.0f;   // 2^40
 constexpr double kPredClampD = 1099511627776.0;
@@ -81,15 +65,9 @@ struct ModelF32 {
   // one 32-byte load (the record is one aligned sector)
   __device__ __forceinline__ static Leaf load_leaf(const Leaf* leaves, uint32_t l) {
     unsigned long long w0, w1, w2, w3;
-#if LJ_L2HINT
-    asm("ld.global.nc.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], %5;"
-        : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
-        : "l"(leaves + l), "l"(l2_keep()));
-#else
     asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
         : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
         : "l"(leaves + l));
-#endif
     Leaf r;
     r.base_key = w0;
     r.lo = (uint32_t)w1;
@@ -200,51 +178,21 @@ struct HashSlot {
 };
 
 __device__ __forceinline__ uint64_t ldg_key(const uint64_t* R, uint32_t i) {
-#if LJ_L2HINT
-  unsigned long long v;
-  asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(R + i), "l"(l2_keep()));
-  return v;
-#else
   return __ldg(reinterpret_cast<const unsigned long long*>(R) + i);
-#endif
 }
 
-// Streaming accesses (read or written once): evicted from L2 first.
+// Streaming accesses (S and per-probe results, read or written once).
 __device__ __forceinline__ ulonglong2 ldg_stream_u64x2(const uint64_t* p) {
-#if LJ_L2HINT
-  unsigned long long a, b;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
-      : "=l"(a), "=l"(b) : "l"(p), "l"(l2_stream()));
-  return make_ulonglong2(a, b);
-#else
   return __ldg(reinterpret_cast<const ulonglong2*>(p));
-#endif
 }
 __device__ __forceinline__ void st_stream_u32x2(uint32_t* p, uint32_t a, uint32_t b) {
-#if LJ_L2HINT
-  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;"
-               ::"l"(p), "r"(a), "r"(b), "l"(l2_stream()) : "memory");
-#else
   *reinterpret_cast<uint2*>(p) = make_uint2(a, b);
-#endif
 }
 __device__ __forceinline__ uint4 ldg_stream_u32x4(const uint32_t* p) {
-#if LJ_L2HINT
-  unsigned a, b, c, d;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-      : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "l"(p), "l"(l2_stream()));
-  return make_uint4(a, b, c, d);
-#else
   return __ldg(reinterpret_cast<const uint4*>(p));
-#endif
 }
 __device__ __forceinline__ void st_stream_u64(uint64_t* p, uint64_t v) {
-#if LJ_L2HINT
-  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(l2_stream())
-               : "memory");
-#else
   *p = v;
-#endif
 }
 
 // Four consecutive keys R[g .. g+3] with one 32-byte load (R + g 32-byte aligned).
@@ -299,19 +247,21 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
 // its predecessors' published states until it meets an inclusive prefix.
 // Tiles take their ids from an atomic ticket, so every predecessor of a
 // running tile has already started and the walk finishes; the wait is still
-// bounded (kLookbackPolls polls) and, if it ever runs out, the tile records
-// kErrLookbackTimeout and continues with a zero prefix.
+// bounded (st.polls polls of a predecessor, by default kLookbackPolls; the
+// option "lookback_polls" lowers it) and, if it ever runs out, the tile
+// records kErrLookbackTimeout and continues with a zero prefix.
 
 enum : uint32_t { kTileEmpty = 0, kTileAggregate = 1, kTilePrefix = 2 };
+
+constexpr uint32_t kLookbackPolls = 1u << 20;   // default bound of one look-back wait
 
 struct TileState {
   uint32_t* flag;     // [tiles], zeroed before the launch
   uint64_t* agg;      // [tiles]
   uint64_t* incl;     // [tiles]
   uint32_t* ticket;   // 1 counter, zeroed before the launch
+  uint32_t polls = kLookbackPolls;   // polls of one predecessor before giving up
 };
-
-constexpr uint32_t kLookbackPolls = 1u << 20;
 
 // Called by all 32 lanes of one warp.  Returns the exclusive prefix of tile t.
 __device__ __forceinline__ uint64_t lookback_warp(const TileState& st, uint32_t t,
@@ -338,7 +288,7 @@ __device__ __forceinline__ uint64_t lookback_warp(const TileState& st, uint32_t 
     if (pt >= 0) {
       f = ld_acquire_u32(st.flag + pt);
       while (f == kTileEmpty) {
-        if (++polls > kLookbackPolls) {
+        if (++polls > st.polls) {
           timed_out = true;
           break;
         }

@@ -115,6 +115,12 @@ uint64_t get_host_chunk();
 void set_probe_buckets(int v);
 int get_probe_buckets();
 
+// Bound of one look-back wait (option "lookback_polls") and the test hook
+// "fault_skip_tiles": single-pass launches skip that many leading tiles, whose
+// states are then never published, so the waits of the next tiles run out.
+uint32_t lookback_polls();
+uint32_t fault_skip_tiles();
+
 // Probe batches of at most this many keys take the single-pass kernel.
 void set_single_pass_max(uint64_t v);
 uint64_t get_single_pass_max();

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kBlock, LJ_MINB) probe_single_pass_kernel(Prob
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_wpre[K * kWarps];
   __shared__ uint64_t s_prefix;
-  if (threadIdx.x == 0) s_tile = atomicAdd(P.st.ticket, 1u);
+  if (threadIdx.x == 0) s_tile = atomicAdd(P.st.ticket, 1u) + P.tile_skip;
   __syncthreads();
   const uint32_t tile = s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
       window<Model>(lf, key, wl, wh);
       uint32_t b[1] = {wl}, l[1] = {wh - wl};
       uint64_t cv[1];
-      search_last<1, true>(P.R, P.n, P.r32, xk, b, l, cv);
+      search_last<1, true>(P.R, xk, b, l, cv);
       lb = b[0];
     }
     off = P.offsets[j];
@@ -308,7 +308,7 @@ __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32
     if constexpr (GAP != 0)
       lookup_gapped<Model, MODE, VEC, GAP == 2>(P, j0, r_idx, cnt, valid);
     else
-      lookup_probes<Model, MODE, 1, VEC, LJ_ENDGAME, LJ_GUIDED, LJ_CANON>(P, j0, 0, r_idx, cnt, valid);
+      lookup_probes<Model, MODE, 1, VEC>(P, j0, 0, r_idx, cnt, valid);
     uint32_t w0, w1;
     if (MODE == kDupCount) {
       w0 = cnt[0];
@@ -560,10 +560,10 @@ __global__ void __launch_bounds__(kSortMergeBlock)
     uint32_t base[1] = {wl}, len[1] = {wh - wl};
     uint64_t cv[1];
     if (threadIdx.x == 0) {
-      search_last<1, true>(P.R, P.n, P.r32, xk, base, len, cv);   // lower bound of the smallest key
+      search_last<1, true>(P.R, xk, base, len, cv);   // lower bound of the smallest key
       s_lo = base[0];
     } else {
-      search_last<1, false>(P.R, P.n, P.r32, xk, base, len, cv);  // upper bound of the largest key
+      search_last<1, false>(P.R, xk, base, len, cv);  // upper bound of the largest key
       s_hi = base[0];
     }
   }
@@ -757,13 +757,16 @@ int ws_acquire(Workspace& w, uint32_t tiles, uint64_t words, cudaStream_t s) {
   w.st.flag = (uint32_t*)(b + 256);
   w.st.agg = (uint64_t*)(b + 256 + flags);
   w.st.incl = w.st.agg + w.tiles;
+  w.st.polls = lookback_polls();
   w.words = words ? (uint32_t*)(b + 256 + flags + states) : nullptr;
   return 0;
 }
 
+// Parameters of a probe launch; err = the word its kernels OR errors into
+// (the per-device error word unless the caller passes another).
 template <class Model>
 ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
-                               uint32_t s_base) {
+                               uint32_t s_base, uint32_t* err) {
   ProbeParams<Model> P{};
   P.R = idx->R;
   P.n = (uint32_t)idx->n;
@@ -773,7 +776,7 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.S = S;
   P.m = m;
   P.s_base = s_base;
-  P.err = device_error_word(idx->device);
+  P.err = err;
   P.gkeys = idx->gkeys;
   P.gpos = idx->gpos;
   P.gslots = idx->gslots;
@@ -797,7 +800,7 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
   constexpr uint64_t tile = (uint64_t)kBlock * 2 * kRounds;
   Workspace w;
   if (int rc = ws_acquire(w, (uint32_t)((m + tile - 1) / tile), 0, s)) return rc;
-  ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
+  ProbeParams<Model> P = make_params(idx, model, S, m, s_base, device_error_word(idx->device));
   if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   P.pairs = pairs;
   P.capacity = cap;
@@ -808,12 +811,14 @@ int launch_single_pass(const lj_index* idx, Model model, int mode, const uint64_
   P.total_ws = w.total;
   P.st = w.st;
   P.num_tiles = w.tiles;
+  P.tile_skip = std::min(fault_skip_tiles(), w.tiles - 1);
+  const unsigned grid = w.tiles - P.tile_skip;
   const bool vec = aligned(S, 16) && (!offsets || aligned(offsets, 16)) &&
                    (!counts || aligned(counts, 8)) && (!first || aligned(first, 8));
   KernelTimer kt("probe_single_pass_kernel", s);
-#define LJ_LAUNCH(MODE)                                                                     \
-  (vec ? probe_single_pass_kernel<Model, MODE, kRounds, true><<<w.tiles, kBlock, 0, s>>>(P) \
-       : probe_single_pass_kernel<Model, MODE, kRounds, false><<<w.tiles, kBlock, 0, s>>>(P))
+#define LJ_LAUNCH(MODE)                                                                  \
+  (vec ? probe_single_pass_kernel<Model, MODE, kRounds, true><<<grid, kBlock, 0, s>>>(P) \
+       : probe_single_pass_kernel<Model, MODE, kRounds, false><<<grid, kBlock, 0, s>>>(P))
   if (mode == kUniqueEmit)
     LJ_LAUNCH(kUniqueEmit);
   else if (mode == kUniqueCount)
@@ -858,6 +863,7 @@ int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, 
   st.flag = (uint32_t*)(ws + 256 + b_ctr);
   st.agg = (uint64_t*)(ws + 256 + b_ctr + b_flags);
   st.incl = st.agg + sb;
+  st.polls = lookback_polls();
   uint64_t* cursor = (uint64_t*)(ws + 256 + b_ctr + b_flags + b_states);
   uint64_t* bx = (uint64_t*)(ws + 256 + b_ctr + b_flags + b_states + b_cur);
   uint32_t* bj = (uint32_t*)(ws + 256 + b_ctr + b_flags + b_states + b_cur + b_x);
@@ -942,10 +948,11 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   st.flag = (uint32_t*)(ws + 256 + b_cnt);
   st.agg = (uint64_t*)(ws + 256 + b_cnt + b_flags);
   st.incl = st.agg + scan_blocks;
+  st.polls = lookback_polls();
   uint64_t* tile_prefix = (uint64_t*)(ws + 256 + b_cnt + b_flags + b_states);
   uint32_t* words = words_in_counts ? counts : (uint32_t*)(ws + 256 + b_cnt + b_flags + b_states + b_pre);
 
-  ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
+  ProbeParams<Model> P = make_params(idx, model, S, m, s_base, device_error_word(idx->device));
   if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   P.first = first;
   const bool vec = aligned(S, 16) && (!first || aligned(first, 8));
@@ -1042,7 +1049,7 @@ template <class Model>
 int launch_emit(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
                 const uint64_t* offsets, lj_pair* pairs, uint64_t cap, uint32_t s_base,
                 cudaStream_t s) {
-  ProbeParams<Model> P = make_params(idx, model, S, m, s_base);
+  ProbeParams<Model> P = make_params(idx, model, S, m, s_base, device_error_word(idx->device));
   if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   P.pairs = pairs;
   P.capacity = cap;
@@ -1242,8 +1249,10 @@ constexpr uint32_t kNoAllocTiles = (uint32_t)((kNoAllocMaxProbes + kNoAllocTile 
 constexpr size_t kNoAllocFlagBytes = ((size_t)kNoAllocTiles * 4 + 255) / 256 * 256;
 constexpr size_t kNoAllocBytes = 256 + kNoAllocFlagBytes + (size_t)kNoAllocTiles * 16;
 
-// header: [0] ticket (u32), [64] total (u64), [128] error word (u32);
-// then the tile flags, then the aggregates and the inclusive prefixes.
+// header: [0] ticket (u32), [64] total (u64), [128] error word (u32,
+// sticky: an asynchronous call's error stays until a synchronising call
+// reports and clears it); then the tile flags, then the aggregates and the
+// inclusive prefixes.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
@@ -1271,37 +1280,43 @@ int noalloc_count(const lj_index* idx, Model model, const uint64_t* S, uint64_t 
   unsigned char* b = nullptr;
   if (int rc = noalloc_scratch(idx->device, &b)) return rc;
   const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, (m + kNoAllocTile - 1) / kNoAllocTile);
-  LJ_CUDA(cudaMemsetAsync(b, 0, 256 + ((size_t)tiles * 4 + 255) / 256 * 256, s));
-  ProbeParams<Model> P{};
-  P.R = idx->R;
-  P.leaves = (const typename Model::Leaf*)idx->leaves;
-  P.model = model;
-  P.S = S;
-  P.m = m;
+  // clear the ticket and the flags of this call's tiles (not the error word)
+  LJ_CUDA(cudaMemsetAsync(b, 0, 128, s));
+  LJ_CUDA(cudaMemsetAsync(b + 256, 0, ((size_t)tiles * 4 + 255) / 256 * 256, s));
+  uint32_t* err = (uint32_t*)(b + 128);
+  ProbeParams<Model> P = make_params(idx, model, S, m, 0, err);
   P.counts = counts;
   P.offsets = offsets;
   P.total_ws = (uint64_t*)(b + 64);
-  P.err = (uint32_t*)(b + 128);
   P.st.ticket = (uint32_t*)b;
   P.st.flag = (uint32_t*)(b + 256);
   P.st.agg = (uint64_t*)(b + 256 + kNoAllocFlagBytes);
   P.st.incl = P.st.agg + kNoAllocTiles;
+  P.st.polls = lookback_polls();
   P.num_tiles = tiles;
+  P.tile_skip = std::min(fault_skip_tiles(), tiles - 1);
+  const unsigned grid = tiles - P.tile_skip;
   const bool vec = aligned(S, 16) && (!offsets || aligned(offsets, 16)) && (!counts || aligned(counts, 8));
   if (idx->unique)
-    vec ? probe_single_pass_kernel<Model, kUniqueCount, kRounds, true><<<tiles, kBlock, 0, s>>>(P)
-        : probe_single_pass_kernel<Model, kUniqueCount, kRounds, false><<<tiles, kBlock, 0, s>>>(P);
+    vec ? probe_single_pass_kernel<Model, kUniqueCount, kRounds, true><<<grid, kBlock, 0, s>>>(P)
+        : probe_single_pass_kernel<Model, kUniqueCount, kRounds, false><<<grid, kBlock, 0, s>>>(P);
   else
-    vec ? probe_single_pass_kernel<Model, kDupCount, kRounds, true><<<tiles, kBlock, 0, s>>>(P)
-        : probe_single_pass_kernel<Model, kDupCount, kRounds, false><<<tiles, kBlock, 0, s>>>(P);
+    vec ? probe_single_pass_kernel<Model, kDupCount, kRounds, true><<<grid, kBlock, 0, s>>>(P)
+        : probe_single_pass_kernel<Model, kDupCount, kRounds, false><<<grid, kBlock, 0, s>>>(P);
   LJ_CUDA(cudaGetLastError());
   if (total_host) {
-    uint32_t err = 0;
+    uint32_t e = 0;
     LJ_CUDA(cudaMemcpyAsync(total_host, P.total_ws, 8, cudaMemcpyDeviceToHost, s));
-    LJ_CUDA(cudaMemcpyAsync(&err, P.err, 4, cudaMemcpyDeviceToHost, s));
+    LJ_CUDA(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s));
     LJ_CUDA(cudaStreamSynchronize(s));
-    if (err & kErrLookbackTimeout)
-      return fail(LJ_E_TIMEOUT, "join_count_noalloc: a device-side look-back wait ran out");
+    if (e) {
+      LJ_CUDA(cudaMemsetAsync(err, 0, 4, s));
+      LJ_CUDA(cudaStreamSynchronize(s));
+      if (e & kErrLookbackTimeout)
+        return fail(LJ_E_TIMEOUT, "join_count_noalloc: a device-side look-back wait ran out "
+                                  "(in this call or an earlier one without total_host)");
+      return fail(LJ_E_CUDA, "join_count_noalloc: device error bits 0x%x", e);
+    }
   }
   return 0;
 }

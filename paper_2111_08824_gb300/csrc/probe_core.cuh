@@ -37,6 +37,7 @@ struct ProbeParams {
   TileState st;
   uint32_t* err;
   uint32_t num_tiles;
+  uint32_t tile_skip;     // single-pass kernel: tile ids start here (fault-injection hook; 0)
   // gapped arrays of a GRMI (Section 3.A); gkeys == nullptr: plain RMI lookup
   const uint64_t* gkeys;
   const uint32_t* gpos;   // gslots + 1 payloads (positions in R)
@@ -58,9 +59,6 @@ struct ProbeParams {
 #ifndef LJ_MINB
 #define LJ_MINB 1          // min resident blocks per SM requested from ptxas
 #endif
-#ifndef LJ_FAN
-#define LJ_FAN 2           // search fan-out: FAN-1 independent pivots per round
-#endif
 #ifndef LJ_SCHUNK
 #define LJ_SCHUNK 1        // search kernel: tiles of 2*LJ_SBLOCK probes per block (1 measured best)
 #endif
@@ -71,20 +69,11 @@ struct ProbeParams {
 #define LJ_SMINB 16        // search kernel: 16 blocks of 128 threads per SM (32 registers,
                            // full occupancy): measured 9% faster than the unconstrained build
 #endif
-#ifndef LJ_CANON
-#define LJ_CANON false     // search kernel: canonical (aligned-grid) bisection (measured 1.6x slower)
-#endif
-#ifndef LJ_GUIDED
-#define LJ_GUIDED false    // search kernel: model-guided search (measured 2.6x slower: pivots no longer shared)
-#endif
 #ifndef LJ_GROUP4
 #define LJ_GROUP4 true     // duplicates: halving over aligned 4-key groups + one 32-byte load
                            // (measured 11% faster on the duplicate workload, whose search
                            // is DRAM-bound; 7% slower on unique lognormal keys, where the
                            // bisection stays in use)
-#endif
-#ifndef LJ_ENDGAME
-#define LJ_ENDGAME false   // search kernel: resolve the last <= 4 keys in one round (measured slower)
 #endif
 constexpr int kRounds = LJ_ROUNDS;
 constexpr int kSearchChunk = LJ_SCHUNK;
@@ -98,12 +87,9 @@ constexpr uint64_t kCompactTile = 256ull * kScanItems;   // probes per compactio
 // window [base, base+len): finds c = the last position whose key is < x
 // (STRICT) or <= x (!STRICT), and returns res = c + 1 (so the lower bound,
 // resp. the upper bound, of x) and cv = R[c] when res > window start.
-// Rounds with FAN > 2 cut the window into FAN parts with FAN-1 independent
-// pivot loads (fewer dependent rounds, more loads); the later rounds halve.
-// ENDGAME: halving stops at 4 keys; the last <= 4 keys are then read in one
-// round (a single 32-byte load when they share an aligned sector of R).
-template <int NP, bool STRICT, bool ENDGAME = false, int FAN = LJ_FAN>
-__device__ __forceinline__ void search_last(const uint64_t* __restrict__ R, uint32_t n, bool r32,
+// Branch-free halving, the NP searches' loads issued together each round.
+template <int NP, bool STRICT>
+__device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
                                             const uint64_t (&x)[NP], uint32_t (&base)[NP],
                                             uint32_t (&len)[NP], uint64_t (&cv)[NP]) {
   bool moved[NP];
@@ -114,57 +100,19 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R, uint
     start[p] = base[p];
     cv[p] = 0;
   }
-  if (FAN > 2) {
-    // k-ary rounds while the window has at least 2*FAN keys
-    while (true) {
-      bool any = false;
-      uint64_t v[NP][FAN - 1];
-#pragma unroll
-      for (int p = 0; p < NP; ++p)
-        if (len[p] >= 2 * FAN) {
-          any = true;
-          const uint32_t step = len[p] / FAN;
-#pragma unroll
-          for (int t = 1; t < FAN; ++t) v[p][t - 1] = ldg_key(R, base[p] + t * step);
-        }
-      if (!any) break;
-#pragma unroll
-      for (int p = 0; p < NP; ++p)
-        if (len[p] >= 2 * FAN) {
-          const uint32_t step = len[p] / FAN;
-          int c = 0;
-          uint64_t last = 0;
-#pragma unroll
-          for (int t = 1; t < FAN; ++t) {
-            const bool go = STRICT ? (v[p][t - 1] < x[p]) : (v[p][t - 1] <= x[p]);
-            if (go) {
-              c = t;
-              last = v[p][t - 1];
-            }
-          }
-          if (c > 0) {
-            cv[p] = last;
-            moved[p] = true;
-          }
-          base[p] += c * step;
-          len[p] = c == FAN - 1 ? len[p] - (FAN - 1) * step : step;
-        }
-    }
-  }
-  constexpr uint32_t kStop = ENDGAME ? 4u : 1u;
   while (true) {
     bool any = false;
     uint64_t v[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p)
-      if (len[p] > kStop) {
+      if (len[p] > 1) {
         any = true;
         v[p] = ldg_key(R, base[p] + (len[p] >> 1));
       }
     if (!any) break;
 #pragma unroll
     for (int p = 0; p < NP; ++p)
-      if (len[p] > kStop) {
+      if (len[p] > 1) {
         const uint32_t half = len[p] >> 1;
         const bool go = STRICT ? (v[p] < x[p]) : (v[p] <= x[p]);
         if (go) {
@@ -175,43 +123,6 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R, uint
         len[p] -= half;
       }
   }
-  if constexpr (ENDGAME) {
-    // len <= 4: read the remaining keys in one round and count how many of
-    // them pass the test (a prefix, as R is sorted)
-    uint64_t k[NP][4];
-    uint32_t shift[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      shift[p] = 0;
-      if (len[p] > 0) {
-        const uint32_t g = base[p] & ~3u;
-        if (r32 && base[p] + len[p] - 1 <= g + 3 && g + 3 < n) {
-          ldg_key4(R, g, k[p]);
-          shift[p] = base[p] - g;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) k[p][i] = i < (int)len[p] ? ldg_key(R, base[p] + i) : 0;
-        }
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      uint32_t c = 0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint32_t q = shift[p] + i;   // only the window's keys count
-        const uint64_t kv = q == 0 ? k[p][0] : q == 1 ? k[p][1] : q == 2 ? k[p][2] : k[p][3];
-        const bool in = i < (int)len[p] && q < 4;
-        const bool go = STRICT ? (kv < x[p]) : (kv <= x[p]);
-        if (in && go) {
-          c = i + 1;
-          cv[p] = kv;
-        }
-      }
-      base[p] += c;   // c == 0 with a non-empty window only when nothing moved
-      len[p] = start[p];
-    }
-  } else {
   uint64_t w[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p)
@@ -230,7 +141,6 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R, uint
       }
     }
     len[p] = start[p];   // keep the window start for the caller
-  }
   }
 }
 
@@ -297,139 +207,6 @@ __device__ __forceinline__ void search_last_g4(const uint64_t* __restrict__ R, u
     }
     base[p] = res;
     len[p] = start[p];
-  }
-}
-
-// Model-guided bounded search (same contract as search_last): the first
-// pivot is the model's predicted position, then interpolation between the
-// bracketing keys alternates with bisection (at least one halving every two
-// rounds).  On lognormal keys this needs ~18% fewer loads than bisection,
-// most of it on hits; the result is exact whatever the pivots.
-template <int NP, bool STRICT>
-__device__ __forceinline__ void search_guided(const uint64_t* __restrict__ R,
-                                              const uint64_t (&x)[NP], const uint32_t (&pred)[NP],
-                                              uint32_t (&base)[NP], uint32_t (&len)[NP],
-                                              uint64_t (&cv)[NP]) {
-  uint32_t a[NP], b[NP], start[NP];
-  uint64_t klo[NP], khi[NP];
-  bool has_lo[NP], has_hi[NP];
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    a[p] = start[p] = base[p];
-    b[p] = base[p] + len[p];
-    has_lo[p] = has_hi[p] = false;
-    klo[p] = khi[p] = 0;
-    cv[p] = 0;
-  }
-  for (int step = 0;; ++step) {
-    bool any = false;
-    uint32_t g[NP];
-    uint64_t v[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      if (a[p] < b[p]) {
-        any = true;
-        const uint32_t w = b[p] - a[p];
-        uint32_t q = a[p] + (w >> 1);                       // bisection
-        if (step == 0) {
-          q = pred[p];                                       // the model's guess
-        } else if ((step & 1) && has_lo[p] && has_hi[p]) { // interpolation
-          const float dx = __ull2float_rn(x[p] - klo[p]);
-          const float dk = __ull2float_rn(khi[p] - klo[p]);
-          const float f = __fdividef(dx, dk) * (float)w;
-          q = a[p] + (f > 0.0f ? (f < (float)w ? (uint32_t)f : w - 1) : 0u);
-        }
-        q = q < a[p] ? a[p] : (q >= b[p] ? b[p] - 1 : q);
-        g[p] = q;
-        v[p] = ldg_key(R, q);
-      }
-    }
-    if (!any) break;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      if (a[p] < b[p]) {
-        const bool go = STRICT ? (v[p] < x[p]) : (v[p] <= x[p]);
-        if (go) {
-          a[p] = g[p] + 1;
-          klo[p] = v[p];
-          has_lo[p] = true;
-          cv[p] = v[p];
-        } else {
-          b[p] = g[p];
-          khi[p] = v[p];
-          has_hi[p] = true;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    base[p] = a[p];
-    len[p] = start[p];   // keep the window start for the caller
-  }
-}
-
-// Canonical bounded search (same contract as search_last): bisects the
-// smallest power-of-two-aligned block of R that contains the window, with
-// pivots at fixed positions of that grid.  A pivot outside the window needs
-// no load (keys before the window pass the test, keys after it fail), so a
-// probe loads about log2(window) + 1 keys, and probes whose windows fall in
-// the same region of R visit the same pivots: a warp's lanes then share
-// sectors and other warps find them in L1.
-template <int NP, bool STRICT>
-__device__ __forceinline__ void search_canon(const uint64_t* __restrict__ R,
-                                             const uint64_t (&x)[NP], uint32_t (&base)[NP],
-                                             uint32_t (&len)[NP], uint64_t (&cv)[NP]) {
-  int64_t pos[NP];
-  uint64_t step[NP];
-  uint32_t wl[NP], wh[NP];
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    wl[p] = base[p];
-    wh[p] = base[p] + len[p];
-    cv[p] = 0;
-    if (len[p] == 0) {
-      step[p] = 0;
-      pos[p] = (int64_t)wl[p] - 1;
-    } else {
-      const uint32_t d = wl[p] ^ (wh[p] - 1);
-      const int j = d ? 32 - __clz(d) : 0;
-      step[p] = 1ull << j;
-      pos[p] = (int64_t)((uint64_t)wl[p] & ~(step[p] - 1)) - 1;
-    }
-  }
-  while (true) {
-    bool any = false;
-    int64_t q[NP];
-    bool inw[NP];
-    uint64_t v[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      inw[p] = false;
-      if (step[p]) {
-        any = true;
-        q[p] = pos[p] + (int64_t)step[p];
-        inw[p] = q[p] >= (int64_t)wl[p] && q[p] < (int64_t)wh[p];
-        if (inw[p]) v[p] = ldg_key(R, (uint32_t)q[p]);
-      }
-    }
-    if (!any) break;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      if (step[p]) {
-        const bool t = inw[p] ? (STRICT ? (v[p] < x[p]) : (v[p] <= x[p])) : (q[p] < (int64_t)wl[p]);
-        if (t) {
-          pos[p] = q[p];
-          if (inw[p]) cv[p] = v[p];
-        }
-        step[p] >>= 1;
-      }
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    base[p] = (uint32_t)(pos[p] + 1);
-    len[p] = wl[p];   // keep the window start for the caller
   }
 }
 
@@ -593,19 +370,14 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
   }
 }
 
-// Lookups of 2K probes per thread: round k covers probes
-// j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
-// leaf record -> window, then the interleaved bounded searches.  cnt is the
-// number of matches, r_idx the first matching position (when cnt > 0).
 // Lookups of NP keys already loaded (x, valid): root -> leaf record ->
 // window, then the interleaved bounded searches; cnt = number of matches,
 // r_idx = first matching position (when cnt > 0).
-template <class Model, int MODE, int NP, bool ENDGAME = false, bool GUIDED = false,
-          bool CANON = false>
+template <class Model, int MODE, int NP>
 __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const uint64_t (&x)[NP],
                                             const bool (&valid)[NP], uint32_t (&r_idx)[NP],
                                             uint32_t (&cnt)[NP]) {
-  uint32_t base[NP], len[NP], ppos[NP];
+  uint32_t base[NP], len[NP];
   {
     uint32_t leaf[NP];
 #pragma unroll
@@ -616,11 +388,10 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
       if (valid[p]) lf[p] = Model::load_leaf(P.leaves, leaf[p]);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      uint32_t wl = 0, wh = 0, pp = 0;
-      if (valid[p]) window<Model>(lf[p], x[p], wl, wh, &pp);
+      uint32_t wl = 0, wh = 0;
+      if (valid[p]) window<Model>(lf[p], x[p], wl, wh);
       base[p] = wl;
       len[p] = wh - wl;
-      ppos[p] = pp;
     }
   }
   if (MODE == kDupCount) {
@@ -628,50 +399,28 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
 #pragma unroll
     for (int p = 0; p < NP; ++p) wh[p] = base[p] + len[p];
     uint64_t cv[NP];
-    if (CANON)
-      search_canon<NP, true>(P.R, x, base, len, cv);                     // base = lower bound
-    else if (LJ_GROUP4 && P.r32)
-      search_last_g4<NP, true>(P.R, P.n, x, base, len, cv);               // base = lower bound
+    if (LJ_GROUP4 && P.r32)
+      search_last_g4<NP, true>(P.R, P.n, x, base, len, cv);   // base = lower bound
     else
-      search_last<NP, true, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = lower bound
+      search_last<NP, true>(P.R, x, base, len, cv);            // base = lower bound
     uint32_t lb[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       lb[p] = base[p];
       len[p] = wh[p] - base[p];
     }
-    if (CANON)
-      search_canon<NP, false>(P.R, x, base, len, cv);                      // base = upper bound
-    else if (LJ_GROUP4 && P.r32)
-      search_last_g4<NP, false>(P.R, P.n, x, base, len, cv);                // base = upper bound
+    if (LJ_GROUP4 && P.r32)
+      search_last_g4<NP, false>(P.R, P.n, x, base, len, cv);  // base = upper bound
     else
-      search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound
+      search_last<NP, false>(P.R, x, base, len, cv);           // base = upper bound
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       cnt[p] = valid[p] ? base[p] - lb[p] : 0;
       r_idx[p] = lb[p];
     }
-  } else if (CANON) {
-    uint64_t cv[NP];
-    search_canon<NP, false>(P.R, x, base, len, cv);  // base = upper bound, len = start
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
-      cnt[p] = match ? 1u : 0u;
-      r_idx[p] = base[p] - 1;
-    }
-  } else if (GUIDED) {
-    uint64_t cv[NP];
-    search_guided<NP, false>(P.R, x, ppos, base, len, cv);  // base = upper bound, len = start
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
-      cnt[p] = match ? 1u : 0u;
-      r_idx[p] = base[p] - 1;
-    }
   } else {
     uint64_t cv[NP];
-    search_last<NP, false, ENDGAME>(P.R, P.n, P.r32, x, base, len, cv);  // base = upper bound, len = start
+    search_last<NP, false>(P.R, x, base, len, cv);  // base = upper bound, len = start
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
@@ -681,8 +430,11 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
   }
 }
 
-template <class Model, int MODE, int K, bool VEC, bool ENDGAME = false, bool GUIDED = false,
-          bool CANON = false>
+// Lookups of 2K probes per thread: round k covers probes
+// j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
+// leaf record -> window, then the interleaved bounded searches.  cnt is the
+// number of matches, r_idx the first matching position (when cnt > 0).
+template <class Model, int MODE, int K, bool VEC>
 __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
                                               uint32_t stride, uint32_t (&r_idx)[2 * K],
                                               uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
@@ -704,7 +456,7 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
           valid[2 * k + 1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
     }
   }
-  lookup_keys<Model, MODE, NP, ENDGAME, GUIDED, CANON>(P, x, valid, r_idx, cnt);
+  lookup_keys<Model, MODE, NP>(P, x, valid, r_idx, cnt);
 }
 
 // Exclusive scan of the per-tile counts: blocks of 256 threads x 16 counts

@@ -28,6 +28,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace {
@@ -69,7 +70,9 @@ struct lj_server {
   std::unordered_map<uint64_t, Request*> reqs;
   std::vector<Slot> slots;
   cudaStream_t free_stream = nullptr;
+  cudaEvent_t fetch_done = nullptr;  // orders the release of a request's pairs after its fetches
   uint64_t next_id = 1;
+  uint64_t resident = 0;             // bytes of the registered relations (R and index)
   uint64_t mem_in_use = 0, mem_peak = 0;
   bool stop = false;
   std::atomic<bool> wake{false};   // set by the completion callbacks
@@ -172,6 +175,8 @@ void scheduler(lj_server* sv) {
           if (r->pairs) lj::scratch_free(r->pairs, sl.stream);
           r->pairs = nullptr;
         }
+        if (sl.scratch) lj::scratch_free(sl.scratch, sl.stream);
+        sl.scratch = nullptr;
         sl.reqs.clear();
         sl.busy = false;
         sv->cv_done.notify_all();
@@ -218,7 +223,8 @@ int join_server_create(const lj_server_cfg* cfg, lj_server** out) {
       return bail(fail(LJ_E_NOMEM, "join_server_create: slot resources"));
     if (int rc = dyn_batch_alloc(sl.buf, cfg->max_batch)) return bail(rc);
   }
-  if (cudaStreamCreateWithFlags(&sv->free_stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&sv->free_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sv->fetch_done, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(LJ_E_CUDA, "join_server_create: stream"));
   sv->sched = std::thread(scheduler, sv);
   *out = sv;
@@ -234,6 +240,15 @@ int join_server_add_relation(lj_server* sv, const lj_index* index, uint32_t* rel
   std::lock_guard<std::mutex> lk(sv->mu);
   if (!sv->rels.empty() && sv->rels[0]->precision != index->precision)
     return fail(LJ_E_INVAL, "served relations must share one precision");
+  // the resident relation (its keys and its leaf records) counts against the budget
+  const uint64_t rec = index->precision == LJ_FP64 ? sizeof(lj::LeafF64) : sizeof(lj::LeafF32);
+  const uint64_t bytes = index->n * 8 + (uint64_t)index->L * rec;
+  if (sv->mem_in_use + bytes > sv->cfg.hbm_budget_bytes)
+    return fail(LJ_E_BUDGET, "join_server_add_relation: %llu resident bytes exceed the HBM budget",
+                (unsigned long long)bytes);
+  sv->resident += bytes;
+  sv->mem_in_use += bytes;
+  sv->mem_peak = std::max(sv->mem_peak, sv->mem_in_use);
   *rel_id = (uint32_t)sv->rels.size();
   sv->rels.push_back(index);
   return LJ_OK;
@@ -265,11 +280,12 @@ int join_submit(lj_server* sv, uint32_t rel_id, const uint64_t* S, uint64_t m, l
       sv->t_first = r->t_submit;
       sv->any = true;
     }
-    if (r->need > sv->cfg.hbm_budget_bytes) {
+    if (r->need + sv->resident > sv->cfg.hbm_budget_bytes) {
       sv->rejected++;
       delete r;
-      return fail(LJ_E_BUDGET, "join_submit: %llu probes need more than the HBM budget",
-                  (unsigned long long)m);
+      return fail(LJ_E_BUDGET,
+                  "join_submit: %llu probes need more than the HBM budget left by the "
+                  "resident relations", (unsigned long long)m);
     }
     sv->reqs[r->id] = r;
     sv->pending.push_back(r);
@@ -311,7 +327,13 @@ int join_fetch(lj_server* sv, lj_ticket t, lj_pair* dst_dev, uint64_t capacity, 
   Request* r = it->second;
   if (r->status != 0) return fail(LJ_E_STATE, "join_fetch: request not completed");
   const uint64_t n = std::min(capacity, r->count);
-  if (n) LJ_CUDA(cudaMemcpyAsync(dst_dev, r->pairs, n * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  if (n) {
+    LJ_CUDA(cudaMemcpyAsync(dst_dev, r->pairs, n * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    // join_release frees the pairs on free_stream: make that stream wait for
+    // this copy, so the memory is not handed out again while it is read
+    LJ_CUDA(cudaEventRecord(sv->fetch_done, (cudaStream_t)stream));
+    LJ_CUDA(cudaStreamWaitEvent(sv->free_stream, sv->fetch_done, 0));
+  }
   if (r->count > capacity) return fail(LJ_E_CAPACITY, "join_fetch: %llu pairs, capacity %llu",
                                        (unsigned long long)r->count, (unsigned long long)capacity);
   return LJ_OK;
@@ -346,6 +368,7 @@ int join_server_stats(lj_server* sv, lj_server_stats* out, int reset) {
   out->batches = sv->batches;
   out->mean_batch = sv->batches ? (double)sv->batched_reqs / (double)sv->batches : 0.0;
   out->mem_in_use = sv->mem_in_use;
+  out->resident = sv->resident;
   out->mem_peak = sv->mem_peak;
   if (!sv->lat_us.empty()) {
     std::vector<double> v = sv->lat_us;
@@ -393,6 +416,7 @@ void join_server_destroy(lj_server* sv) {
     if (sl.stream) cudaStreamDestroy(sl.stream);
   }
   if (sv->free_stream) cudaStreamDestroy(sv->free_stream);
+  if (sv->fetch_done) cudaEventDestroy(sv->fetch_done);
   delete sv;
 }
 

@@ -9,6 +9,14 @@ prediction error, bit for bit as correctly rounded hardware computes them:
                TwoSum for the addition, explicit fix of the single
                double-rounding case: a float64 sum that lands exactly on a
                float32 midpoint while the exact sum does not)
+  u64_to_f64   uint64 -> float64, round to nearest even (integer arithmetic)
+  floor_fma64  floor(fma(a, x, b)) in float64 with one rounding: the exact
+               value a*x + b as an unevaluated sum (Dekker's exact product
+               by Veltkamp splitting, TwoSum), its floor decided from that
+               sum; the rare elements whose value lies within a few units in
+               the last place of an integer (where the one rounding of the
+               hardware fma can move the floor) are recomputed with exact
+               rationals
 
 The helpers are themselves pinned against exact rational arithmetic
 (`fractions.Fraction`) in tests/test_fpemu.py.
@@ -123,4 +131,109 @@ def leaf_pred_f32(keys: np.ndarray, base: np.ndarray, a: np.ndarray,
     df = u64_to_f32(d)
     df = np.where(ge, df, -df).astype(np.float32)
     v = np.floor(fma32(a, df, b).astype(np.float64))
+    return np.clip(v, -(2.0 ** 40), 2.0 ** 40).astype(np.int64)
+
+
+# --------------------------------------------------------------- float64 --
+
+def u64_to_f64(x: np.ndarray) -> np.ndarray:
+    """Correctly rounded uint64 -> float64 (integer arithmetic)."""
+    x = np.asarray(x, dtype=np.uint64)
+    out = np.empty(x.shape, dtype=np.float64)
+    small = x < _U(1 << 53)
+    out[small] = x[small].astype(np.float64)        # exact
+    big = ~small
+    if np.any(big):
+        v = x[big]
+        hi32 = (v >> _U(32)).astype(np.float64)      # exact (< 2^32)
+        k = np.floor(np.log2(hi32)).astype(np.int64) + 32
+        k = np.where((k < 63) & ((v >> (k + 1).astype(np.uint64)) > 0), k + 1, k)
+        k = np.where((v >> k.astype(np.uint64)) == 0, k - 1, k)
+        shift = (k - 52).astype(np.uint64)
+        q = v >> shift
+        rem = v - (q << shift)
+        half = _U(1) << (shift - _U(1))
+        up = (rem > half) | ((rem == half) & ((q & _U(1)) == _U(1)))
+        q = q + up.astype(np.uint64)
+        out[big] = np.ldexp(q.astype(np.float64), shift.astype(np.int64))
+    return out
+
+
+def _split(a: np.ndarray):
+    c = 134217729.0 * a                         # 2^27 + 1 (Veltkamp)
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def _two_prod(a: np.ndarray, b: np.ndarray):
+    """p + e == a * b exactly (Dekker), no fma needed; finite, no underflow."""
+    p = a * b
+    ah, al = _split(a)
+    bh, bl = _split(b)
+    e = ((ah * bh - p) + ah * bl + al * bh) + al * bl
+    return p, e
+
+
+def _ulp(v: np.ndarray) -> np.ndarray:
+    v = np.abs(v)
+    return np.nextafter(v, np.inf) - v
+
+
+def floor_fma64(a, x, b) -> np.ndarray:
+    """floor(fma(a, x, b)) for float64 arrays, as float64 (NaN stays NaN).
+
+    fma rounds the exact value a*x + b once to float64; its floor differs
+    from the floor of the exact value only where the exact value lies within
+    half a unit in the last place below an integer.  The exact value is
+    carried as s + w (+ a residual far below ulp(s)); elements whose floor
+    that sum cannot settle are recomputed with exact rationals."""
+    a = np.asarray(a, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    a, x, b = np.broadcast_arrays(a, x, b)
+    with np.errstate(over="ignore", invalid="ignore"):
+        p, e = _two_prod(a, x)
+        s1, t1 = _two_sum(p, b)                  # s1 + t1 == p + b
+        w1 = t1 + e                              # error <= 2^-53 |t1 + e|
+        s, w = _two_sum(s1, w1)                  # s + w == s1 + w1, |w| <= ulp(s)/2
+        k = np.floor(s)
+        fl = np.where((s == k) & (w < 0), k - 1, k)
+        # distance to the integer above, and how close the one rounding of
+        # the fma (half an ulp) or the residual could bring the value to it
+        gap_up = (fl + 1 - s) - w
+        gap_dn = (s - fl) + w
+        tol = 4 * _ulp(np.abs(s) + 1.0) + (np.abs(t1) + np.abs(e)) * 2.0 ** -50
+        unsure = (gap_up <= tol) | (gap_dn <= tol) | ~np.isfinite(p) | ~np.isfinite(e)
+    out = fl.astype(np.float64)
+    out[np.isnan(a) | np.isnan(x) | np.isnan(b)] = np.nan
+    idx = np.flatnonzero(unsure & ~(np.isnan(a) | np.isnan(x) | np.isnan(b)))
+    for i in idx:
+        ai, xi, bi = float(a.flat[i]), float(x.flat[i]), float(b.flat[i])
+        try:
+            v = float(Fraction(ai) * Fraction(xi) + Fraction(bi))
+        except OverflowError:
+            v = np.inf if (Fraction(ai) * Fraction(xi) + Fraction(bi)) > 0 else -np.inf
+        out.flat[i] = np.floor(v)
+    return out
+
+
+def leaf_of_f64(keys: np.ndarray, a0: float, b0: float, L: int) -> np.ndarray:
+    """Double-precision root: clamp(floor(fma(a0, double(x), b0)), 0, L-1)."""
+    fx = u64_to_f64(keys)
+    v = floor_fma64(np.float64(a0), fx, np.float64(b0))
+    v = np.where(np.isnan(v), -1.0, v)
+    return np.clip(v, 0, L - 1).astype(np.int64)
+
+
+def leaf_pred_f64(keys: np.ndarray, base: np.ndarray, a: np.ndarray,
+                  b: np.ndarray) -> np.ndarray:
+    """Double-precision leaf prediction floor(fma(a, D, b)), D = x - base
+    signed and rounded to float64, clamped to [-2^40, 2^40]."""
+    keys = np.asarray(keys, np.uint64)
+    base = np.asarray(base, np.uint64)
+    ge = keys >= base
+    d = np.where(ge, keys - base, base - keys)
+    df = u64_to_f64(d)
+    df = np.where(ge, df, -df)
+    v = floor_fma64(np.asarray(a, np.float64), df, np.asarray(b, np.float64))
     return np.clip(v, -(2.0 ** 40), 2.0 ** 40).astype(np.int64)

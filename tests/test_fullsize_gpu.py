@@ -1,18 +1,23 @@
 """Full-size parity: the three single-GPU workloads at their real sizes, in
-the launch configuration bench.py times (default execution paths).
+the launch configuration bench.py times (default execution paths), every
+probe compared with the oracle (the CPU sort-merge join, run on chunks of S
+on every host core).
 
-  uniform_1m        2^20 x 2^20, fp64 model, L = 4096: every pair compared
-                    with the oracle.
-  lognormal_100m    100M x 400M, L = 2^20, fp32 and fp64 models: properties
-                    that hold at any size (|J| = number of generated hits,
-                    the matched probes are exactly the generated hits, every
-                    pair has equal keys), both precisions give the same pairs,
-                    and 2^20 sampled probes compared with the oracle.
-  dup_seqh_50m      50M rows x 200M probes (~6.2e9 pairs), L = 2^18: counts
-                    equal the generated multiplicities, |J| equals their sum,
-                    every pair has equal keys and the pairs of each probe are
-                    its contiguous run of R; 2^18 sampled probes compared with
-                    the oracle's ranges.
+  uniform_1m        2^20 x 2^20, L = 4096: every pair compared with the
+                    oracle's pairs, fp64 (the workload's model) and fp32.
+  lognormal_100m    100M x 400M, L = 2^20, fp32 and fp64 models: the pairs of
+                    every probe equal the oracle's (each hit j gives exactly
+                    (lo_j, j), in s order), and join_count's counts and
+                    offsets equal the oracle's for all 400M probes.
+  dup_seqh_50m      50M rows x 200M probes (~6.2e9 pairs), L = 2^18: the
+                    located range (first match, count) and the offset of every
+                    probe equal the oracle's; every one of the ~6.2e9 emitted
+                    pairs, through join_expand and through the two-pass
+                    join_emit, is checked on the device against the oracle's
+                    ranges: the pair at output position q is (lo_s + q -
+                    off_s, s) for the one probe s with off_s <= q < off_s+1.
+  gapped RMI and learned hash at full size: their arrays equal the oracle's,
+                    and their joins give the oracle's ranges for every probe.
 """
 import numpy as np
 import pytest
@@ -22,6 +27,9 @@ import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+_CHUNK = 1 << 25            # probes per host-side comparison chunk
+_PCHUNK = 1 << 27           # pairs per device-side comparison chunk
 
 
 def _dev(a):
@@ -33,104 +41,152 @@ def _lj():
     return lj
 
 
-def test_uniform_1m_full_parity():
+class _Cached:
+    """A workload, its device copies and the oracle's ranges (computed once)."""
+
+    def __init__(self, w):
+        self.w = w
+        self.Rd, self.Sd = _dev(w.R), _dev(w.S)
+        self._ranges = None
+
+    def ranges(self):
+        if self._ranges is None:
+            lo, hi, total = oracle.join_ranges_mt(self.w.R, self.w.S)
+            self._ranges = (lo, hi, total)
+        return self._ranges
+
+
+@pytest.fixture(scope="module")
+def lognormal():
+    c = _Cached(datagen.lognormal_100m(seed=0))
+    yield c
+    del c.Rd, c.Sd
+    torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def dup():
+    c = _Cached(datagen.dup_seqh_50m(seed=0))
+    yield c
+    del c.Rd, c.Sd
+    torch.cuda.empty_cache()
+
+
+def _unique_pairs_equal_oracle(pairs, total, lo, hi):
+    """Direct path on a unique R: the pairs are (lo_j, j) for every hit j,
+    in s order (compared chunk by chunk of probes)."""
+    done = 0
+    for a in range(0, lo.size, _CHUNK):
+        b = min(lo.size, a + _CHUNK)
+        hit = hi[a:b] > lo[a:b]
+        js = np.flatnonzero(hit) + a
+        want = np.stack([lo[a:b][hit].astype(np.uint32), js.astype(np.uint32)], axis=1)
+        got = pairs[done:done + js.size].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), f"pairs of probes [{a}, {b})"
+        done += js.size
+    assert total == done
+
+
+def _pairs_equal_ranges_on_device(pairs, total, lo, off):
+    """Every pair at output position q is (lo_s + q - off_s, s) for the one
+    probe s with off_s <= q < off_{s+1} (lo, off: the oracle's, on the host)."""
+    lo_d = torch.from_numpy(lo.view(np.int64)).cuda()
+    off_d = torch.from_numpy(off).cuda()
+    for a in range(0, total, _PCHUNK):
+        b = min(total, a + _PCHUNK)
+        p = pairs[a:b].to(torch.int64) & 0xFFFFFFFF
+        r, s = p[:, 0], p[:, 1]
+        q = torch.arange(a, b, dtype=torch.int64, device="cuda")
+        o = off_d[s]
+        assert bool(((o <= q) & (q < off_d[s + 1])).all()), f"s labels of pairs [{a}, {b})"
+        assert torch.equal(r, lo_d[s] + (q - o)), f"r of pairs [{a}, {b})"
+        del p, r, s, q, o
+    del lo_d, off_d
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uniform_1m_full_parity(prec):
     lj = _lj()
     w = datagen.uniform_1m(seed=0)
     Rd, Sd = _dev(w.R), _dev(w.S)
-    idx = lj.rmi_build(Rd, w.leaves, w.precision)
+    idx = lj.rmi_build(Rd, w.leaves, prec)
     pairs = torch.empty((w.S.size, 2), dtype=torch.int32, device="cuda")
-    total = lj.join_emit(idx, Sd, pairs)
-    assert total == w.meta["expected_pairs"] == w.S.size
-    got = pairs[:total].cpu().numpy().view(np.uint32)
-    assert np.array_equal(got, oracle.join_pairs(w.R, w.S))
+    want = oracle.join_pairs(w.R, w.S)
+    for spm in (0, 1 << 40):       # the pipeline and the fused single-pass kernel
+        old = lj.lj_get_option("single_pass_max")
+        lj.lj_set_option("single_pass_max", spm)
+        try:
+            pairs.fill_(-1)
+            total = lj.join_emit(idx, Sd, pairs)
+        finally:
+            lj.lj_set_option("single_pass_max", old)
+        assert total == w.meta["expected_pairs"] == w.S.size
+        assert np.array_equal(pairs[:total].cpu().numpy().view(np.uint32), want)
 
 
-def _pairs_equal_keys(Rd, Sd, pairs, total, chunk=1 << 28):
-    """Every pair (r, s) has R[r] == S[s]; s non-decreasing across the list."""
-    prev_s = -1
-    for a in range(0, total, chunk):
-        p = pairs[a:min(total, a + chunk)].to(torch.int64) & 0xFFFFFFFF
-        r, s = p[:, 0], p[:, 1]
-        assert torch.equal(Rd[r], Sd[s])
-        assert bool((s[1:] >= s[:-1]).all()) and int(s[0]) >= prev_s
-        prev_s = int(s[-1])
-
-
-def test_lognormal_100m_full_properties_and_samples():
+def test_lognormal_100m_full_parity(lognormal):
     lj = _lj()
-    w = datagen.lognormal_100m(seed=0)
-    Rd, Sd = _dev(w.R), _dev(w.S)
+    w, Rd, Sd = lognormal.w, lognormal.Rd, lognormal.Sd
     m = w.S.size
-    hits = w.meta["hits"]
-    results = {}
-    for prec in ("fp32", "fp64"):
+    lo, hi, total_o = lognormal.ranges()
+    assert total_o == w.meta["hits"] and int((hi - lo).max()) == 1
+    # which probes hit is fixed by the generator: the oracle agrees
+    assert np.array_equal(hi > lo, w.meta["hit_mask"])
+    pairs = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+    for prec in ("fp32", "fp64"):   # results stay exact whatever the model precision
         idx = lj.rmi_build(Rd, w.leaves, prec)
-        pairs = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+        pairs.fill_(-1)
         total = lj.join_emit(idx, Sd, pairs)
-        assert total == hits
-        _pairs_equal_keys(Rd, Sd, pairs, total)
-        s_idx = pairs[:total, 1].to(torch.int64) & 0xFFFFFFFF
-        assert bool((s_idx[1:] > s_idx[:-1]).all())          # unique R: one pair per probe
-        mask = torch.zeros(m, dtype=torch.bool, device="cuda")
-        mask[s_idx] = True
-        assert torch.equal(mask.cpu(), torch.from_numpy(w.meta["hit_mask"]))
-        results[prec] = (pairs[:total].clone(), idx.stats()["mean_window"])
-        del pairs
-    # results stay exact whatever precision the model runs at
-    assert torch.equal(results["fp32"][0], results["fp64"][0])
-    # sampled probes against the oracle
-    rng = np.random.default_rng(5)
-    sample = np.sort(rng.choice(m, 1 << 20, replace=False))
-    lo, hi, _ = oracle.join_ranges(w.R, w.S[sample])
-    p = results["fp32"][0].cpu().numpy().view(np.uint32)
-    r_of_s = np.full(m, -1, dtype=np.int64)
-    r_of_s[p[:, 1]] = p[:, 0]
-    got = r_of_s[sample]
-    want = np.where(hi > lo, lo.astype(np.int64), -1)
-    assert np.array_equal(got, want)
+        _unique_pairs_equal_oracle(pairs, total, lo, hi)
+    # counts and offsets of the count pass (fp32 index), all probes
+    del pairs
+    counts = torch.empty(m, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    assert lj.join_count(idx, Sd, counts=counts, offsets=offsets) == total_o
+    for a in range(0, m, _CHUNK):
+        b = min(m, a + _CHUNK)
+        c_o = (hi[a:b] - lo[a:b]).astype(np.int64)
+        assert np.array_equal(counts[a:b].cpu().numpy().astype(np.int64), c_o)
+        off = offsets[a:b + 1].cpu().numpy()
+        assert np.array_equal(np.diff(off), c_o)
+    assert int(offsets[0]) == 0 and int(offsets[m]) == total_o
 
 
-def test_dup_seqh_50m_full_properties_and_samples():
+def test_dup_seqh_50m_full_parity(dup):
     lj = _lj()
-    w = datagen.dup_seqh_50m(seed=0)
-    Rd, Sd = _dev(w.R), _dev(w.S)
+    w, Rd, Sd = dup.w, dup.Rd, dup.Sd
     m = w.S.size
     idx = lj.rmi_build(Rd, w.leaves, w.precision)
     assert idx.stats()["unique"] == 0
+    lo, hi, total_o = dup.ranges()
+    assert total_o == w.meta["expected_pairs"]
+    cnt_o = (hi - lo).astype(np.int64)
+    off_o = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(cnt_o, out=off_o[1:])
+    first = torch.empty(m, dtype=torch.int32, device="cuda")
     counts = torch.empty(m, dtype=torch.int32, device="cuda")
     offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
-    total = lj.join_count(idx, Sd, counts=counts, offsets=offsets)
-    assert total == w.meta["expected_pairs"]
-    # counts equal the generated multiplicity of each probe's key
-    _, vals_pos = np.unique(w.R, return_index=True)
-    mult = np.diff(np.append(vals_pos, w.R.size))
-    key_rank = np.searchsorted(w.R[vals_pos], w.S)
-    assert np.array_equal(counts.cpu().numpy().astype(np.int64), mult[key_rank])
+    total = lj.join_locate(idx, Sd, first, counts=counts, offsets=offsets)
+    assert total == total_o
+    hit = cnt_o > 0
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), cnt_o)
+    assert np.array_equal(first.cpu().numpy().view(np.uint32)[hit], lo[hit].astype(np.uint32))
+    assert np.array_equal(offsets.cpu().numpy(), off_o)
     pairs = torch.empty((total, 2), dtype=torch.int32, device="cuda")
-    assert lj.join_emit(idx, Sd, pairs, offsets=offsets) == total
-    _pairs_equal_keys(Rd, Sd, pairs, total)
-    # sampled probes: their pairs are exactly the oracle's range of R
-    rng = np.random.default_rng(6)
-    sample = np.sort(rng.choice(m, 1 << 18, replace=False))
-    lo, hi, _ = oracle.join_ranges(w.R, w.S[sample])
-    off = offsets.cpu().numpy()
-    assert np.array_equal(off[sample + 1] - off[sample], (hi - lo).astype(np.int64))
-    for k in range(0, sample.size, 4096):
-        j = sample[k]
-        a, b = int(off[j]), int(off[j + 1])
-        blk = pairs[a:b].cpu().numpy().view(np.uint32)
-        assert np.array_equal(blk[:, 0], np.arange(lo[k], hi[k], dtype=np.uint32))
-        assert np.all(blk[:, 1] == j)
+    assert lj.join_expand(first, offsets, pairs) == total          # the bench's path
+    _pairs_equal_ranges_on_device(pairs, total, lo, off_o)
+    pairs.fill_(-1)
+    assert lj.join_emit(idx, Sd, pairs, offsets=offsets) == total  # two-pass emit
+    _pairs_equal_ranges_on_device(pairs, total, lo, off_o)
 
 
-def test_lognormal_100m_gapped_full():
+def test_lognormal_100m_gapped_full(lognormal):
     """Gapped RMI (Section 3.A, 4 gaps per key, the paper's default) at full
     size: the 500M-slot arrays equal the oracle's model-based insertion slot
-    for slot, and the join through the exponential search has the workload's
-    properties and matches the oracle on 2^20 sampled probes."""
+    for slot, and the join through the exponential search gives the oracle's
+    result for every probe."""
     lj = _lj()
-    w = datagen.lognormal_100m(seed=0)
-    Rd, Sd = _dev(w.R), _dev(w.S)
+    w, Rd, Sd = lognormal.w, lognormal.Rd, lognormal.Sd
     m = w.S.size
     idx = lj.rmi_build(Rd, w.leaves, "fp32")
     st = lj.grmi_build(idx, 4)
@@ -139,59 +195,41 @@ def test_lognormal_100m_gapped_full():
     assert st["slots"] == want.keys.size
     assert np.array_equal(keys, want.keys) and np.array_equal(pos, want.pos)
     del keys, pos
+    # the oracle's own gapped lookup agrees with its sort-merge on a sample
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(m, 1 << 18, replace=False))
+    glo, ghi, _ = oracle.grmi_join(w.R, want, w.S[sample])[:3]
+    lo, hi, _ = lognormal.ranges()
+    assert np.array_equal(glo, lo[sample]) and np.array_equal(ghi, hi[sample])
+    del want
     pairs = torch.empty((m, 2), dtype=torch.int32, device="cuda")
     total = lj.join_emit(idx, Sd, pairs)
-    assert total == w.meta["hits"]
-    _pairs_equal_keys(Rd, Sd, pairs, total)
-    s_idx = pairs[:total, 1].to(torch.int64) & 0xFFFFFFFF
-    mask = torch.zeros(m, dtype=torch.bool, device="cuda")
-    mask[s_idx] = True
-    assert torch.equal(mask.cpu(), torch.from_numpy(w.meta["hit_mask"]))
-    rng = np.random.default_rng(7)
-    sample = np.sort(rng.choice(m, 1 << 20, replace=False))
-    lo, hi, _ = oracle.grmi_join(w.R, want, w.S[sample])[:3]
-    lo2, hi2, _ = oracle.join_ranges(w.R, w.S[sample])
-    assert np.array_equal(lo, lo2) and np.array_equal(hi, hi2)
-    p = pairs[:total].cpu().numpy().view(np.uint32)
-    r_of_s = np.full(m, -1, dtype=np.int64)
-    r_of_s[p[:, 1]] = p[:, 0]
-    assert np.array_equal(r_of_s[sample], np.where(hi > lo, lo.astype(np.int64), -1))
+    _unique_pairs_equal_oracle(pairs, total, lo, hi)
 
 
-def test_dup_seqh_50m_gapped_counts_and_samples():
+def test_dup_seqh_50m_gapped_full(dup):
     lj = _lj()
-    w = datagen.dup_seqh_50m(seed=0)
-    Rd, Sd = _dev(w.R), _dev(w.S)
+    w, Rd, Sd = dup.w, dup.Rd, dup.Sd
     m = w.S.size
     idx = lj.rmi_build(Rd, w.leaves, w.precision)
     lj.grmi_build(idx, 4)
+    lo, hi, total_o = dup.ranges()
+    first = torch.empty(m, dtype=torch.int32, device="cuda")
     counts = torch.empty(m, dtype=torch.int32, device="cuda")
-    offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
-    total = lj.join_count(idx, Sd, counts=counts, offsets=offsets)
-    assert total == w.meta["expected_pairs"]
-    _, vals_pos = np.unique(w.R, return_index=True)
-    mult = np.diff(np.append(vals_pos, w.R.size))
-    key_rank = np.searchsorted(w.R[vals_pos], w.S)
-    assert np.array_equal(counts.cpu().numpy().astype(np.int64), mult[key_rank])
-    # emit a sampled slice of probes through the two-pass path and check them
-    rng = np.random.default_rng(8)
-    sample = np.sort(rng.choice(m, 1 << 16, replace=False))
-    Ss = _dev(w.S[sample])
-    off_s = torch.empty(sample.size + 1, dtype=torch.int64, device="cuda")
-    tot_s = lj.join_count(idx, Ss, offsets=off_s)
-    pairs = torch.empty((tot_s, 2), dtype=torch.int32, device="cuda")
-    assert lj.join_emit(idx, Ss, pairs, offsets=off_s) == tot_s
-    got = pairs.cpu().numpy().view(np.uint32)
-    assert np.array_equal(got, oracle.join_pairs(w.R, w.S[sample]))
+    total = lj.join_locate(idx, Sd, first, counts=counts)
+    assert total == total_o
+    cnt_o = (hi - lo).astype(np.int64)
+    hit = cnt_o > 0
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), cnt_o)
+    assert np.array_equal(first.cpu().numpy().view(np.uint32)[hit], lo[hit].astype(np.uint32))
 
 
-def test_dup_seqh_50m_learned_hash():
+def test_dup_seqh_50m_learned_hash_full(dup):
     """Learned hash index (Section 3.C, 4 slots per distinct key) on the
-    duplicate workload: the table equals the oracle's, counts equal the
-    generated multiplicities, sampled probes' pairs equal the oracle's."""
+    duplicate workload: the table equals the oracle's; the located range of
+    every probe and every emitted pair equal the oracle's."""
     lj = _lj()
-    w = datagen.dup_seqh_50m(seed=0)
-    Rd, Sd = _dev(w.R), _dev(w.S)
+    w, Rd, Sd = dup.w, dup.Rd, dup.Sd
     m = w.S.size
     idx = lj.rmi_build(Rd, w.leaves, w.precision)
     lj.lhash_build(idx, 4)
@@ -199,19 +237,20 @@ def test_dup_seqh_50m_learned_hash():
     want = oracle.lhash_build(w.R, oracle.rmi_fit(w.R, w.leaves, fp64=False), 4)
     assert np.array_equal(keys, want.keys) and np.array_equal(pos, want.pos)
     assert np.array_equal(lj.lhash_export_first(idx), want.first)
+    del keys, pos, want
+    lo, hi, total_o = dup.ranges()
+    cnt_o = (hi - lo).astype(np.int64)
+    off_o = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(cnt_o, out=off_o[1:])
+    first = torch.empty(m, dtype=torch.int32, device="cuda")
     counts = torch.empty(m, dtype=torch.int32, device="cuda")
-    total = lj.join_count(idx, Sd, counts=counts)
-    assert total == w.meta["expected_pairs"]
-    _, vals_pos = np.unique(w.R, return_index=True)
-    mult = np.diff(np.append(vals_pos, w.R.size))
-    assert np.array_equal(counts.cpu().numpy().astype(np.int64),
-                          mult[np.searchsorted(w.R[vals_pos], w.S)])
-    rng = np.random.default_rng(11)
-    sample = np.sort(rng.choice(m, 1 << 16, replace=False))
-    Ss = _dev(w.S[sample])
-    first = torch.empty(sample.size, dtype=torch.int32, device="cuda")
-    off = torch.empty(sample.size + 1, dtype=torch.int64, device="cuda")
-    tot_s = lj.join_locate(idx, Ss, first, offsets=off)
-    pairs = torch.empty((tot_s, 2), dtype=torch.int32, device="cuda")
-    assert lj.join_expand(first, off, pairs) == tot_s
-    assert np.array_equal(pairs.cpu().numpy().view(np.uint32), oracle.join_pairs(w.R, w.S[sample]))
+    offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    total = lj.join_locate(idx, Sd, first, counts=counts, offsets=offsets)
+    assert total == total_o
+    hit = cnt_o > 0
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), cnt_o)
+    assert np.array_equal(first.cpu().numpy().view(np.uint32)[hit], lo[hit].astype(np.uint32))
+    assert np.array_equal(offsets.cpu().numpy(), off_o)
+    pairs = torch.empty((total, 2), dtype=torch.int32, device="cuda")
+    assert lj.join_expand(first, offsets, pairs) == total
+    _pairs_equal_ranges_on_device(pairs, total, lo, off_o)

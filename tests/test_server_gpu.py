@@ -81,7 +81,10 @@ def test_results_alone_equal_results_in_the_mix():
             srv.release(tickets[q])
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["batches"] >= 1
-        assert st["p99_us"] >= st["p50_us"] > 0 and st["mem_in_use"] == 0
+        assert st["p99_us"] >= st["p50_us"] > 0
+        # only the registered relations stay charged once every request is released
+        assert st["mem_in_use"] == st["resident"] == sum(
+            R.numel() * 8 + ix.leaves * 32 for R, ix in zip(rels, idx))
     finally:
         srv.close()
 
@@ -89,10 +92,21 @@ def test_results_alone_equal_results_in_the_mix():
 def test_budget_admission_rejection_and_timeout():
     lj = _lj()
     rels, idx = _relations(lj, k=1, seed=10)
-    budget = 12 * 300_000 + 4096          # room for one 300k-probe request at a time
+    resident = rels[0].numel() * 8 + idx[0].leaves * 32   # keys + fp32 leaf records
+    # a relation larger than the budget is refused
+    small = lj.Server(hbm_budget_bytes=resident - 1, streams=1, max_batch=8)
+    try:
+        with pytest.raises(lj.LJoinError) as e:
+            small.add_relation(idx[0])
+        assert e.value.code == -7                           # LJ_E_BUDGET
+    finally:
+        small.close()
+    # room for the relation and one 300k-probe request at a time
+    budget = resident + 12 * 300_000 + 4096
     srv = lj.Server(hbm_budget_bytes=budget, streams=2, max_batch=8)
     try:
         rid = srv.add_relation(idx[0])
+        assert srv.stats()["resident"] == resident
         with pytest.raises(lj.LJoinError) as e:
             srv.submit(rid, _request(rels[0], 400_000, 1))
         assert e.value.code == -7                           # LJ_E_BUDGET
