@@ -266,6 +266,75 @@ def cpu_baseline(wl, sample: int, sample_1t: int) -> dict:
                            "sample": f"first {m1} probes of S ({dt1:.2f} s)"}}
 
 
+def uniform_1m_record(reps: int = 200) -> dict:
+    """The 1M x 1M uniform workload (L = 4096) as a latency case: the inputs
+    fit in L2, so L2 is flushed before every rep and each rep is timed alone
+    (CUDA events around the call on the launch stream; median of `reps`).
+    Both model precisions, the count-scan-compact pipeline and the fused
+    single-pass kernel; roofline on the algorithmic bytes of the pass."""
+    import torch
+
+    import paper_2111_08824_gb300 as lj
+    w = datagen.uniform_1m(seed=0)
+    n, m, L = w.R.size, w.S.size, w.leaves
+    Rd = torch.from_numpy(w.R.view(np.int64)).cuda()
+    Sd = torch.from_numpy(w.S.view(np.int64)).cuda()
+    pairs = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+    written = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    peak, _ = _peaks()
+
+    def timed(fn, k):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sorted(a.elapsed_time(b) for a, b in evs)
+
+    out = {"workload": "uniform_1m", "n": n, "m": m, "leaves": L,
+           "timing": f"L2 flushed ({L2_FLUSH_BYTES >> 20} MB written) before each rep, "
+                     f"median of {reps} reps, CUDA events around the call"}
+    empty = torch.zeros(1, device="cuda")
+    out["event_floor_us"] = 1e3 * statistics.median(timed(lambda: empty.add_(1), reps))
+    old = lj.lj_get_option("single_pass_max")
+    for prec in ("fp64", "fp32"):
+        idx = lj.rmi_build(Rd, L, prec)
+        rec = 64 if prec == "fp64" else 32
+        for name, spm in (("pipeline", 0), ("single_pass", 1 << 40)):
+            lj.lj_set_option("single_pass_max", spm)
+
+            def step():
+                lj.join_emit(idx, Sd, pairs, written=written, want_total=False)
+            for _ in range(5):
+                step()
+            total = int(lj.join_emit(idx, Sd, pairs))
+            ts = timed(step, reps)
+            lj.lj_profile_report()
+            lj.lj_set_option("profile", 1)
+            timed(step, 20)
+            lj.lj_set_option("profile", 0)
+            kern = lj.lj_profile_report()
+            med = statistics.median(ts)
+            alg = 8 * m + 8 * n + 8 * total + rec * L
+            out[f"{prec}_{name}"] = {
+                "us_median": 1e3 * med, "us_min": 1e3 * ts[0],
+                "probe_keys_per_s": m / (med / 1e3), "pairs": total,
+                "roofline": {"bound": "hbm", "alg_bytes": alg,
+                             "achieved": alg / (med / 1e3) / 1e9, "peak": peak,
+                             "frac": alg / (med / 1e3) / 1e9 / peak, "unit": "GB/s"},
+                "kernels_us": {k: 1e3 * v["total_ms"] / v["launches"] for k, v in kern.items()},
+                "mean_window": idx.stats()["mean_window"]}
+    lj.lj_set_option("single_pass_max", old)
+    del Rd, Sd, pairs, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_batched(args, rank, world, dist):
     """4096 uneven joins: per-join launches of the plain probe vs one batched
     plan run vs the same run replayed from a CUDA graph (same GPU, same data)."""
@@ -338,8 +407,9 @@ def run_batched(args, rank, world, dist):
         "tile_shape_chosen": {"block": shape[0], "tiles_per_item": shape[1]},
         "gpu_launches": 3 * args.steps,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    del plan, pairs, idx, joins
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_served(args, rank, world, dist):
@@ -476,8 +546,9 @@ def run_served(args, rank, world, dist):
                        "plain_per_request": sat_plain},
         "setup_s": setup_s,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    del pool, idx, rels
+    torch.cuda.empty_cache()
+    return line
 
 
 def main():
@@ -498,6 +569,8 @@ def main():
     ap.add_argument("--cpu-sample-1t", type=int, default=1 << 23)
     ap.add_argument("--ref-sample", type=int, default=1 << 25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="skip the uniform_1m, batched and served records of the default line")
     ap.add_argument("--n", type=int, default=None, help="override |R| (profiling runs)")
     ap.add_argument("--m", type=int, default=None, help="override |S| (profiling runs)")
     ap.add_argument("--leaves", type=int, default=None, help="override L (profiling runs)")
@@ -527,13 +600,11 @@ def main():
 
     import paper_2111_08824_gb300 as lj
     torch.cuda.set_device(local)
-    if args.workload == "served_64":
-        run_served(args, rank, world, dist)
-        if dist:
-            dist.destroy_process_group()
-        return
-    if args.workload == "batched_4096":
-        run_batched(args, rank, world, dist)
+    if args.workload in ("served_64", "batched_4096"):
+        fn = run_served if args.workload == "served_64" else run_batched
+        line = fn(args, rank, world, dist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         if dist:
             dist.destroy_process_group()
         return
@@ -552,8 +623,11 @@ def main():
     unique = bool(st["unique"])
     # precision variants: windows re-measured under each model precision
     windows = {}
+    other = None                                 # the index in the other precision
     for prec in ("fp32", "fp64"):
-        s2 = st if prec == wl.precision else lj.rmi_build(Rd, L, prec).stats()
+        if prec != wl.precision:
+            other = lj.rmi_build(Rd, L, prec)
+        s2 = st if prec == wl.precision else other.stats()
         windows[prec] = {"mean_window": s2["mean_window"], "max_window": s2["max_window"],
                          "build_ms": s2["build_ms"]}
     lj.lj_set_option("probe_buckets", args.probe_buckets)
@@ -698,8 +772,43 @@ def main():
         "gpu_launches": sum(k["launches"] for k in kernels.values()),
         "clocks": clk,
     }
+    # the same probe pass with the other model precision (same inputs, same
+    # pipeline): FP32-model vs FP64-model probe
+    if unique and args.index == "rmi" and other is not None:
+        def step_other():
+            lj.join_emit(other, Sd, pairs, written=written, want_total=False)
+        for _ in range(args.warmup):
+            step_other()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if _small(wl):
+            flush.fill_(1)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_other()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_o = e0.elapsed_time(e1) / args.steps
+        assert int(lj.join_emit(other, Sd, pairs)) == total
+        prec_o = "fp64" if wl.precision == "fp32" else "fp32"
+        line[prec_o + "_model_probe"] = {
+            "ms_per_step": ms_o, "value": world * m / (ms_o / 1e3), "unit": "keys/s",
+            "roofline_pass": {"alg_bytes": pass_bytes,
+                              "frac": pass_bytes / (ms_o / 1e3) / 1e9 / peak},
+            "mean_window": windows[prec_o]["mean_window"],
+            "max_window": windows[prec_o]["max_window"]}
+    del other
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample, args.cpu_sample_1t)
+    # the other workloads' records (one GPU): the 1M x 1M latency case, the
+    # batched and the served workloads, each measured against its baseline
+    if world == 1 and args.workload == "lognormal_100m" and not args.no_subrecords:
+        del idx, pairs, Rd, Sd
+        torch.cuda.empty_cache()
+        sub = argparse.Namespace(**vars(args))
+        sub.joins, sub.scale, sub.seed = 4096, 1.0, args.seed
+        line["configs"] = {"uniform_1m": uniform_1m_record(),
+                           "batched_4096": run_batched(sub, rank, world, dist),
+                           "served_64": run_served(sub, rank, world, dist)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

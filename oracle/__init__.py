@@ -154,6 +154,7 @@ def join_ranges_mt(R, S, threads: int | None = None, chunk: int = 1 << 20
     lib = _load()
     if S.size and not lib.lj_oracle_is_sorted(_ptr(R), R.size):
         raise OracleError("R is not sorted non-decreasing")
+    chunk = max(1 << 14, min(chunk, -(-S.size // (4 * threads))))   # >= 4 chunks per thread
     bounds = [(a, min(S.size, a + chunk)) for a in range(0, S.size, chunk)]
 
     def one(ab):

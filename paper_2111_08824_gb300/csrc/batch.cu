@@ -87,11 +87,11 @@ template <class Model>
 __device__ __forceinline__ Model model_of(const JoinDesc& d);
 template <>
 __device__ __forceinline__ ModelF32 model_of<ModelF32>(const JoinDesc& d) {
-  return ModelF32{(float)d.a0, (float)d.b0, d.L};
+  return ModelF32::make((float)d.a0, (float)d.b0, d.L);
 }
 template <>
 __device__ __forceinline__ ModelF64 model_of<ModelF64>(const JoinDesc& d) {
-  return ModelF64{d.a0, d.b0, d.L};
+  return ModelF64::make(d.a0, d.b0, d.L);
 }
 
 // Work item = CHUNK consecutive tiles of 2*BLOCK probes of one join: one

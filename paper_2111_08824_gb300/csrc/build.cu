@@ -151,8 +151,8 @@ template <class Model>
 __global__ void leaf_bounds_kernel(const uint64_t* R, uint64_t n, Model model, uint32_t* lo) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const int64_t li = model.leaf(R[i]);
-    const int64_t lp = i > 0 ? (int64_t)model.leaf(R[i - 1]) : -1;
+    const int64_t li = model.leaf_exact(R[i]);
+    const int64_t lp = i > 0 ? (int64_t)model.leaf_exact(R[i - 1]) : -1;
     for (int64_t l = lp + 1; l <= li; ++l) lo[l] = (uint32_t)i;
     if (i + 1 == n)
       for (int64_t l = li + 1; l <= (int64_t)model.L; ++l) lo[l] = (uint32_t)n;
@@ -329,13 +329,13 @@ struct Deployed;
 template <>
 struct Deployed<ModelF32> {
   __device__ __forceinline__ static int64_t pred(uint64_t x, uint64_t base, double2 f) {
-    return ModelF32::pred(x, base, (float)f.x, (float)f.y);
+    return ModelF32::pred_exact(x, base, f.x, f.y);
   }
 };
 template <>
 struct Deployed<ModelF64> {
   __device__ __forceinline__ static int64_t pred(uint64_t x, uint64_t base, double2 f) {
-    return ModelF64::pred(x, base, f.x, f.y);
+    return ModelF64::pred_exact(x, base, f.x, f.y);
   }
 };
 
@@ -384,8 +384,7 @@ __global__ void leaf_records_kernel(const uint64_t* R, uint64_t n, const uint32_
     rec.hi = b;
     rec.base_key = a < n ? R[a] : 0;
     const double2 f = fit[l];
-    rec.a = f.x;   // narrowed to float for the single-precision record
-    rec.b = f.y;
+    Model::set_params(rec, f.x, f.y);   // deployed parameters (float or double)
     if (b > a) {
       rec.e_lo = elo[l];
       rec.e_hi = ehi[l];
@@ -583,12 +582,12 @@ extern "C" int rmi_build(const uint64_t* R_dev, uint64_t n, uint32_t leaves, int
       break;
     }
     if (precision == LJ_FP64) {
-      ModelF64 m{idx->root_f64[0], idx->root_f64[1], leaves};
+      const ModelF64 m = ModelF64::make(idx->root_f64[0], idx->root_f64[1], leaves);
       rc = build_leaves(idx, m, s, idx->leaves);
       idx->stats.root_a = m.a0;
       idx->stats.root_b = m.b0;
     } else {
-      ModelF32 m{idx->root_f32[0], idx->root_f32[1], leaves};
+      const ModelF32 m = ModelF32::make(idx->root_f32[0], idx->root_f32[1], leaves);
       rc = build_leaves(idx, m, s, idx->leaves);
       idx->stats.root_a = m.a0;
       idx->stats.root_b = m.b0;

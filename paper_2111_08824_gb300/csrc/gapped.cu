@@ -426,10 +426,10 @@ extern "C" int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream) {
   const GappedSlot slot{1 + gaps};
   const uint64_t min_slots = (uint64_t)(1 + gaps) * index->n;
   if (index->precision == LJ_FP64)
-    rc = build_gapped(index, ModelF64{index->root_f64[0], index->root_f64[1], index->L}, slot,
+    rc = build_gapped(index, ModelF64::make(index->root_f64[0], index->root_f64[1], index->L), slot,
                       index->R, index->n, min_slots, s);
   else
-    rc = build_gapped(index, ModelF32{index->root_f32[0], index->root_f32[1], index->L}, slot,
+    rc = build_gapped(index, ModelF32::make(index->root_f32[0], index->root_f32[1], index->L), slot,
                       index->R, index->n, min_slots, s);
   if (!rc) {
     index->gscale = 1 + gaps;
@@ -474,10 +474,10 @@ extern "C" int lhash_build(lj_index* index, uint32_t spk, lj_stream_t stream) {
     const uint64_t B = std::max<uint64_t>(1, ((uint64_t)spk * D + 3) / 4);
     const HashSlot slot{B, index->n + 1};
     if (index->precision == LJ_FP64)
-      rc = build_gapped(index, ModelF64{index->root_f64[0], index->root_f64[1], index->L}, slot,
+      rc = build_gapped(index, ModelF64::make(index->root_f64[0], index->root_f64[1], index->L), slot,
                         dkey, D, 4 * B, s);
     else
-      rc = build_gapped(index, ModelF32{index->root_f32[0], index->root_f32[1], index->L}, slot,
+      rc = build_gapped(index, ModelF32::make(index->root_f32[0], index->root_f32[1], index->L), slot,
                         dkey, D, 4 * B, s);
     if (!rc) {   // per-slot ranges, so that a probe reads its matches with one load
       const uint64_t C = index->gslots;

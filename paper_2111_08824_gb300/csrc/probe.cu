@@ -650,7 +650,18 @@ struct ScanParams {
   uint64_t* offsets;
   uint32_t* counts;       // kScanOffsets from matches: optional 0/1 counts
   const uint64_t* tile_prefix;
+  // direct prefixes (small batches, no tile_scan_kernel): each tile sums the
+  // counts of the tiles before it; the last tile publishes the total
+  const unsigned long long* tile_counts;   // non-null: direct mode
+  uint32_t tiles;
+  uint64_t* total_ws;
+  uint64_t* total_out;    // optional
+  uint64_t* offsets_end;  // optional: offsets[m]
+  uint32_t* err;
 };
+
+// Batches of at most this many compaction tiles take the direct prefixes.
+constexpr uint32_t kDirectPrefixTiles = 1024;
 
 template <int MODE, bool FROM_COUNTS, bool VEC>
 __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
@@ -661,7 +672,28 @@ __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t tile_base = (uint64_t)tile * kCompactTile;
   const uint64_t base = tile_base + (uint64_t)threadIdx.x * kScanItems;
-  const uint64_t prefix = P.tile_prefix[tile];
+  uint64_t prefix;
+  if (P.tile_counts) {
+    __shared__ unsigned long long s_red[kWarps];
+    unsigned long long part = 0;
+    for (uint32_t u = threadIdx.x; u < tile; u += kBlock) part += __ldg(P.tile_counts + u);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    prefix = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) prefix += s_red[w];
+    if (tile + 1 == P.tiles && threadIdx.x == 0) {
+      const uint64_t total = prefix + __ldg(P.tile_counts + tile);
+      *P.total_ws = total;
+      if (P.total_out) *P.total_out = total;
+      if (P.offsets_end) *P.offsets_end = total;
+      if (MODE == kScanPairs && total > P.capacity) atomicOr(P.err, kErrCapacity);
+    }
+  } else {
+    prefix = P.tile_prefix[tile];
+  }
   uint32_t v[kScanItems];
   if (VEC && base + kScanItems <= P.m) {
 #pragma unroll
@@ -989,7 +1021,11 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
 #undef LJ_SEARCH
   }
   LJ_CUDA(cudaGetLastError());
-  {
+  const bool need_compact = mode == kUniqueEmit || offsets || (!dup && counts);
+  // small batches: the compaction tiles sum their predecessors' counts
+  // themselves (one launch less); larger ones scan the tile counts first
+  const bool direct = need_compact && tiles <= kDirectPrefixTiles;
+  if (!direct) {
     KernelTimer kt("tile_scan_kernel", s);
     tile_scan_kernel<<<scan_blocks, kBlock, 0, s>>>(tile_counts, tiles, tile_prefix, st,
                                                    scan_blocks, total_ws, total_dev,
@@ -999,6 +1035,14 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   LJ_CUDA(cudaGetLastError());
 
   ScanParams Q{};
+  if (direct) {
+    Q.tile_counts = tile_counts;
+    Q.tiles = tiles;
+    Q.total_ws = total_ws;
+    Q.total_out = total_dev;
+    Q.offsets_end = offsets ? offsets + m : nullptr;
+    Q.err = P.err;
+  }
   Q.in = words;
   Q.m = m;
   Q.s_base = s_base;
@@ -1008,7 +1052,6 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   Q.counts = dup ? nullptr : counts;
   Q.tile_prefix = tile_prefix;
   const bool qvec = aligned(words, 16) && (!Q.counts || aligned(Q.counts, 16));
-  const bool need_compact = mode == kUniqueEmit || offsets || Q.counts;
   if (need_compact) {
     KernelTimer kt("compact_kernel", s);
     if (mode == kUniqueEmit)
@@ -1069,10 +1112,10 @@ int launch_emit(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
 }
 
 ModelF32 f32_model(const lj_index* idx) {
-  return ModelF32{idx->root_f32[0], idx->root_f32[1], idx->L};
+  return ModelF32::make(idx->root_f32[0], idx->root_f32[1], idx->L);
 }
 ModelF64 f64_model(const lj_index* idx) {
-  return ModelF64{idx->root_f64[0], idx->root_f64[1], idx->L};
+  return ModelF64::make(idx->root_f64[0], idx->root_f64[1], idx->L);
 }
 
 int check_common(const lj_index* idx, const uint64_t* S, uint64_t m, const char* who) {
