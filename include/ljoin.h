@@ -109,6 +109,25 @@ typedef struct {
 int rmi_build(const uint64_t* R_dev, uint64_t n, uint32_t leaves, int precision,
               lj_stream_t stream, lj_index** out);
 
+/*
+ * rmi_build_batch -- fit k RMIs at once (Section 2.D, as rmi_build), one
+ * segmented pass over all relations: every build kernel covers the whole
+ * batch (root sums per relation, leaf bounds, chunked leaf fits and error
+ * bounds over all leaves of all relations), a dozen launches in all instead
+ * of a dozen per relation.  Each relation's arithmetic is the one rmi_build
+ * uses, so out[j] is bit for bit the index rmi_build(R_dev[j], n[j],
+ * leaves[j], precision) gives.
+ *   R_dev[k], n[k], leaves[k]   as rmi_build, per relation (borrowed)
+ *   precision                   one precision for the batch
+ *   out[k]                      receives the indexes; free each with
+ *                               rmi_free (their leaf records share one
+ *                               allocation, released with the last index)
+ * stats.build_ms of each index is the time of the whole batch.  Synchronises.
+ * Errors: those of rmi_build (for any relation); no index is returned then.
+ */
+int rmi_build_batch(const uint64_t* const* R_dev, const uint64_t* n, const uint32_t* leaves,
+                    uint32_t k, int precision, lj_stream_t stream, lj_index** out);
+
 /* Release an index (its device memory; R itself is not touched). NULL is ok. */
 void rmi_free(lj_index* index);
 

@@ -15,7 +15,7 @@ from ._native import (LJ_FP32, LJ_FP64, BatchPlan, Index, LJoinError, Server, gr
                       rmi_autotune, rmi_autotune_clear,
                       library_path, lj_get_option, lj_last_error, lj_profile_report,
                       lj_set_option,
-                      lj_version, load, rmi_build, rmi_export,
+                      lj_version, load, rmi_build, rmi_build_batch, rmi_export,
                       rmi_free, rmi_stats)
 
 __all__ = ["LJ_FP32", "LJ_FP64", "BatchPlan", "Index", "LJoinError", "Server", "grmi_build",
@@ -24,5 +24,5 @@ __all__ = ["LJ_FP32", "LJ_FP64", "BatchPlan", "Index", "LJoinError", "Server", "
            "join_batch_plan", "join_count", "join_count_noalloc", "join_emit", "join_host",
            "rmi_autotune", "rmi_autotune_clear",
            "library_path", "lj_get_option", "lj_last_error", "lj_profile_report",
-           "lj_set_option", "lj_version", "load", "rmi_build", "rmi_export",
+           "lj_set_option", "lj_version", "load", "rmi_build", "rmi_build_batch", "rmi_export",
            "rmi_free", "rmi_stats"]

@@ -74,6 +74,7 @@ _lib = None
 _P, _U64, _U32, _I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
 SIGNATURES = {
     "rmi_build": ([_P, _U64, _U32, _I, _P, _P], _I),
+    "rmi_build_batch": ([_P, _P, _P, _U32, _I, _P, _P], _I),
     "rmi_free": ([_P], None),
     "rmi_stats": ([_P, _P], _I),
     "rmi_export": ([_P, _P, _P, _P, _P], _I),
@@ -195,6 +196,23 @@ def rmi_build(R, leaves: int, precision: str | int = "fp32", stream=None) -> Ind
     _check(load().rmi_build(_ptr(R), R.numel(), leaves, prec, _stream_ptr(stream),
                             ctypes.byref(out)))
     return Index(out.value, R, leaves, prec)
+
+
+def rmi_build_batch(Rs, leaves, precision: str | int = "fp32", stream=None) -> list:
+    """Fit one RMI per sorted device tensor of Rs in one segmented pass;
+    leaves[j] leaf models for Rs[j]."""
+    k = len(Rs)
+    if len(leaves) != k:
+        raise ValueError("one leaf count per relation")
+    for R in Rs:
+        _require_cuda_u64(R, "R")
+    prec = {"fp32": LJ_FP32, "fp64": LJ_FP64}.get(precision, precision)
+    ptrs = _ptr_array(list(Rs)) if k else (ctypes.c_void_p * 1)()
+    ns = (ctypes.c_uint64 * max(k, 1))(*[R.numel() for R in Rs])
+    ls = (ctypes.c_uint32 * max(k, 1))(*[int(x) for x in leaves])
+    out = (ctypes.c_void_p * max(k, 1))()
+    _check(load().rmi_build_batch(ptrs, ns, ls, k, prec, _stream_ptr(stream), out))
+    return [Index(out[j], Rs[j], int(leaves[j]), prec) for j in range(k)]
 
 
 def rmi_free(index: Index):

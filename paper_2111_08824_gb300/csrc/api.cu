@@ -241,8 +241,8 @@ const char* lj_version(void) { return "ljoin-gb300 0.1 (sm_103a)"; }
 void rmi_free(lj_index* index) {
   if (!index) return;
   lj::grmi_release(index);
-  if (index->leaves) cudaFree(index->leaves);
-  delete index;
+  if (index->leaves && !index->leaves_block) cudaFree(index->leaves);
+  delete index;   // the last index of a batch releases the batch's leaf records
 }
 
 int rmi_stats(const lj_index* index, lj_index_stats* out) {

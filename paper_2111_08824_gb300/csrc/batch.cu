@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(BLOCK) batch_search_kernel(const JoinDesc* __r
 #pragma unroll 1
     for (int t = 0; t < CHUNK; ++t) {
       const uint64_t j0 = first + (uint64_t)t * 2 * BLOCK + 2 * threadIdx.x;
-      if (j0 >= d.m) break;
+      if (__all_sync(0xffffffffu, j0 >= d.m)) break;   // warp-uniform: lookups run as a warp
       uint32_t r_idx[2], cnt[2];
       bool valid[2];
       if (vec)

@@ -14,8 +14,6 @@
 
 namespace lj {
 
-constexpr float kPredClampF = 1099511627776.0f;   // 2^40
-constexpr double kPredClampD = 1099511627776.0;
 
 // Error word bits (sticky, per device).
 constexpr uint32_t kErrLookbackTimeout = 1u;
@@ -23,94 +21,34 @@ constexpr uint32_t kErrCapacity = 2u;
 
 // --------------------------------------------------------------- records --
 
-// ------------------------------------------- conversions without FP64 --
+// ------------------------------------------------------ floor + convert --
 //
-// On GB300 the FP64 pipe runs at a small fraction of the FP32 rate, and
-// conversions between 64-bit integers and floating point run on it too.
-// The probe kernels therefore convert with integer instructions; the results
-// are the correctly rounded values the conversion instructions would give.
-
-// x * 2^e as a float, for a 24-bit significand m in [2^23, 2^24] (2^24: the
-// carry of a rounding, folded into the exponent) and -149 < e + 23 < 128.
-__device__ __forceinline__ float f32_from_sig(uint32_t m, int e) {
-  return __uint_as_float(((uint32_t)(e + 149) << 23) + m);
+// floor of a model output converted to an integer in one instruction
+// (cvt.rmi: round toward minus infinity; NaN gives 0, out-of-range values
+// saturate).  The clamps that follow are integer operations, so a model
+// evaluation issues no separate floor or min/max in floating point (on GB300
+// the FP64 pipe is narrow: the double-precision model then needs three FP64
+// instructions per evaluation: the key conversion, the fma and this one).
+__device__ __forceinline__ int64_t floor_to_i64(double v) {
+  long long r;
+  asm("cvt.rmi.s64.f64 %0, %1;" : "=l"(r) : "d"(v));
+  return r;
+}
+__device__ __forceinline__ int64_t floor_to_i64(float v) {
+  long long r;
+  asm("cvt.rmi.s64.f32 %0, %1;" : "=l"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ int32_t floor_to_i32(float v) {
+  int r;
+  asm("cvt.rmi.s32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
 }
 
-// uint64 -> float, round to nearest even (as __ull2float_rn).
-__device__ __forceinline__ float u64_to_f32_rn(uint64_t x) {
-  if (x == 0) return 0.0f;
-  const int lz = __clzll(x);
-  const uint64_t y = x << lz;                       // leading one at bit 63
-  uint32_t m = (uint32_t)(y >> 40);                 // 24-bit significand
-  const uint64_t rest = y & ((1ull << 40) - 1);     // the 40 bits below it
-  const uint64_t half = 1ull << 39;
-  m += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
-  return f32_from_sig(m, 40 - lz);
-}
+constexpr int64_t kPredClamp = 1ll << 40;   // predictions are clamped to [-2^40, 2^40]
 
-// uint64 -> float, rounded toward zero; `val` receives the integer value of
-// the result (x - val < 2^-23 x).
-__device__ __forceinline__ float u64_to_f32_rz(uint64_t x, uint64_t& val) {
-  if (x == 0) {
-    val = 0;
-    return 0.0f;
-  }
-  const int lz = __clzll(x);
-  const uint32_t m = (uint32_t)((x << lz) >> 40);
-  const int e = 40 - lz;
-  val = e >= 0 ? (uint64_t)m << e : (uint64_t)(m >> -e);
-  return f32_from_sig(m, e);
-}
-
-// uint64 as an unevaluated sum hi + lo of two floats, |x - hi - lo| < 2^-46 x.
-__device__ __forceinline__ void u64_to_ff(uint64_t x, float& hi, float& lo) {
-  uint64_t v, w;
-  hi = u64_to_f32_rz(x, v);
-  lo = u64_to_f32_rz(x - v, w);
-}
-
-// An integral float with |v| <= 2^40 (or +-0) as int64 (as a float -> int64
-// conversion would give).
-__device__ __forceinline__ int64_t f32_integral_to_i64(float v) {
-  const uint32_t b = __float_as_uint(v);
-  const uint32_t ef = (b >> 23) & 0xFFu;
-  if (ef == 0) return 0;
-  const int e = (int)ef - 150;                      // v = m * 2^e
-  const uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
-  const uint64_t mag = e >= 0 ? m << e : m >> -e;
-  return (b >> 31) ? -(int64_t)mag : (int64_t)mag;
-}
-
-// floor(fma(a, D, b)) of the double-precision model, exactly, from float
-// parts: a ~ ah + al, D ~ Dh + Dl, b ~ bh + bl (each pair within 2^-45 of
-// the double it stands for).  The product and the sum are carried as an
-// unevaluated float sum (exact product error by fmaf, TwoSum), whose error is
-// below 2^-21 while |ah*Dh|, |bh| < 2^20.  Returns false (no answer) outside
-// that range and when the value lies within 2^-20 of an integer: there the
-// floor of the double-precision fma must be computed in double.  Explicit
-// _rn intrinsics keep the compiler from contracting the error terms.
-__device__ __forceinline__ bool ff_floor_fma(float ah, float al, float Dh, float Dl, float bh,
-                                             float bl, int64_t& out) {
-  constexpr float kLimit = 1048576.0f;               // 2^20
-  constexpr float kMargin = 9.5367431640625e-07f;    // 2^-20
-  const float p = __fmul_rn(ah, Dh);
-  if (!(fabsf(p) < kLimit && fabsf(bh) < kLimit)) return false;
-  const float pe = __fmaf_rn(ah, Dh, -p);            // ah*Dh - p, exact
-  const float cross = __fmaf_rn(ah, Dl, __fmul_rn(al, Dh));
-  const float s = __fadd_rn(p, bh);                  // TwoSum: s + se == p + bh
-  const float bb = __fsub_rn(s, p);
-  const float se = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
-  const float t = __fadd_rn(__fadd_rn(__fadd_rn(pe, cross), bl), se);
-  const float k1 = floorf(s);
-  const float u = __fsub_rn(s, k1);                  // TwoSum: u + ue == s - k1
-  const float bv = __fsub_rn(u, s);
-  const float ue = __fadd_rn(__fsub_rn(s, __fsub_rn(u, bv)), __fsub_rn(-k1, bv));
-  const float f = __fadd_rn(u, __fadd_rn(ue, t));    // value - k1
-  const float k2 = floorf(f);
-  const float frac = __fsub_rn(f, k2);
-  if (!(frac >= kMargin && frac <= 1.0f - kMargin)) return false;
-  out = f32_integral_to_i64(k1) + f32_integral_to_i64(k2);
-  return true;
+__device__ __forceinline__ int64_t clamp_pred(int64_t v) {
+  return v < -kPredClamp ? -kPredClamp : (v > kPredClamp ? kPredClamp : v);
 }
 
 // ---------------------------------------------------------------- records --
@@ -124,67 +62,50 @@ struct __align__(32) LeafF32 {
 };
 static_assert(sizeof(LeafF32) == 32, "LeafF32 must be one sector");
 
-// Leaf record, double-precision model: 64 bytes = two sectors.  The first
-// holds what a lookup needs besides the bounds: the key base, the positions
-// and the parameters as float pairs (ah + al ~ a, bh + bl ~ b) for the
-// single-precision evaluation of the double-precision model; the second the
-// error bounds and the parameters in double (for values near an integer).
+// Leaf record, double-precision model: 64 bytes = two aligned sectors, read
+// with two 32-byte loads.
 struct __align__(32) LeafF64 {
   uint64_t base_key;
   uint32_t lo, hi;
-  float ah, al, bh, bl;
-  int32_t e_lo, e_hi;
   double a, b;
-  uint64_t pad;
+  int32_t e_lo, e_hi;
+  uint64_t pad[3];
 };
 static_assert(sizeof(LeafF64) == 64, "LeafF64 layout");
 
 // ----------------------------------------------------------------- models --
 //
-// leaf()/pred() are the lookups' evaluation (no FP64 instruction in the
-// common case); leaf_exact()/pred_exact() evaluate the same formulas with the
-// conversion and fma instructions of the model's precision and are used by
-// the index build.  The two give identical integers for every input.
+// Root:  leaf(x) = clamp(floor(fma(a0, X, b0)), 0, L-1), X = x rounded to the
+//        model precision.
+// Leaf:  pred(x) = clamp(floor(fma(a, D, b)), -2^40, 2^40), D = x - base_key
+//        as a signed value rounded to the model precision.
+// The index build and the lookups evaluate these same functions.
 
 struct ModelF32 {
   using Leaf = LeafF32;
   float a0, b0;
   uint32_t L;
-  float lm1f;          // L - 1 (exact: L <= 2^24)
 
   static __host__ __device__ ModelF32 make(float a0, float b0, uint32_t L) {
-    return ModelF32{a0, b0, L, (float)(L - 1u)};
+    return ModelF32{a0, b0, L};
   }
-
   __device__ __forceinline__ uint32_t leaf(uint64_t x) const {
-    const float v = floorf(__fmaf_rn(a0, u64_to_f32_rn(x), b0));
-    if (!(v >= 0.0f)) return 0u;
-    if (v >= lm1f) return L - 1u;
-    return (uint32_t)f32_integral_to_i64(v);
-  }
-  __device__ __forceinline__ uint32_t leaf_exact(uint64_t x) const {
-    float v = floorf(__fmaf_rn(a0, __ull2float_rn(x), b0));
-    if (!(v >= 0.0f)) return 0u;
-    const uint32_t lm1 = L - 1u;
-    return v >= (float)lm1 ? lm1 : (uint32_t)v;
+    const int32_t v = floor_to_i32(__fmaf_rn(a0, __ull2float_rn(x), b0));
+    return v <= 0 ? 0u : ((uint32_t)v >= L - 1u ? L - 1u : (uint32_t)v);
   }
   __device__ __forceinline__ static int64_t pred(uint64_t x, uint64_t base, float a,
                                                  float b) {
-    const float d = x >= base ? u64_to_f32_rn(x - base) : -u64_to_f32_rn(base - x);
-    float v = floorf(__fmaf_rn(a, d, b));
-    v = fminf(fmaxf(v, -kPredClampF), kPredClampF);
-    return f32_integral_to_i64(v);
-  }
-  __device__ __forceinline__ static int64_t pred_exact(uint64_t x, uint64_t base, double a,
-                                                       double b) {
     const float d = x >= base ? __ull2float_rn(x - base) : -__ull2float_rn(base - x);
-    float v = floorf(__fmaf_rn((float)a, d, (float)b));
-    v = fminf(fmaxf(v, -kPredClampF), kPredClampF);
-    return (int64_t)v;
+    return clamp_pred(floor_to_i64(__fmaf_rn(a, d, b)));
   }
   __device__ __forceinline__ static void set_params(Leaf& r, double a, double b) {
     r.a = (float)a;
     r.b = (float)b;
+  }
+  // deployed parameters of a double-precision fit
+  __device__ __forceinline__ static int64_t pred_fit(uint64_t x, uint64_t base, double a,
+                                                     double b) {
+    return pred(x, base, (float)a, (float)b);
   }
   // one 32-byte load (the record is one aligned sector)
   __device__ __forceinline__ static Leaf load_leaf(const Leaf* leaves, uint32_t l) {
@@ -211,41 +132,26 @@ struct ModelF64 {
   using Leaf = LeafF64;
   double a0, b0;
   uint32_t L;
-  float a0h, a0l, b0h, b0l;   // a0 ~ a0h + a0l, b0 ~ b0h + b0l
 
   static __host__ __device__ ModelF64 make(double a0, double b0, uint32_t L) {
-    const float ah = (float)a0, bh = (float)b0;
-    return ModelF64{a0, b0, L, ah, (float)(a0 - (double)ah), bh, (float)(b0 - (double)bh)};
+    return ModelF64{a0, b0, L};
   }
-
   __device__ __forceinline__ uint32_t leaf(uint64_t x) const {
-    float xh, xl;
-    u64_to_ff(x, xh, xl);
-    int64_t f;
-    if (ff_floor_fma(a0h, a0l, xh, xl, b0h, b0l, f))
-      return f < 0 ? 0u : (f >= (int64_t)L - 1 ? L - 1u : (uint32_t)f);
-    return leaf_exact(x);
+    const int64_t v = floor_to_i64(__fma_rn(a0, __ull2double_rn(x), b0));
+    return v <= 0 ? 0u : (v >= (int64_t)L - 1 ? L - 1u : (uint32_t)v);
   }
-  __device__ __forceinline__ uint32_t leaf_exact(uint64_t x) const {
-    double v = floor(__fma_rn(a0, __ull2double_rn(x), b0));
-    if (!(v >= 0.0)) return 0u;
-    const uint32_t lm1 = L - 1u;
-    return v >= (double)lm1 ? lm1 : (uint32_t)v;
-  }
-  __device__ __forceinline__ static int64_t pred_exact(uint64_t x, uint64_t base, double a,
-                                                       double b) {
-    double d = x >= base ? __ull2double_rn(x - base) : -__ull2double_rn(base - x);
-    double v = floor(__fma_rn(a, d, b));
-    v = fmin(fmax(v, -kPredClampD), kPredClampD);
-    return (int64_t)v;
+  __device__ __forceinline__ static int64_t pred(uint64_t x, uint64_t base, double a,
+                                                 double b) {
+    const double d = x >= base ? __ull2double_rn(x - base) : -__ull2double_rn(base - x);
+    return clamp_pred(floor_to_i64(__fma_rn(a, d, b)));
   }
   __device__ __forceinline__ static void set_params(Leaf& r, double a, double b) {
     r.a = a;
     r.b = b;
-    r.ah = (float)a;
-    r.al = (float)(a - (double)r.ah);
-    r.bh = (float)b;
-    r.bl = (float)(b - (double)r.bh);
+  }
+  __device__ __forceinline__ static int64_t pred_fit(uint64_t x, uint64_t base, double a,
+                                                     double b) {
+    return pred(x, base, a, b);
   }
   // two 32-byte loads (the record is two aligned sectors)
   __device__ __forceinline__ static Leaf load_leaf(const Leaf* leaves, uint32_t l) {
@@ -260,29 +166,17 @@ struct ModelF64 {
     r.base_key = w0;
     r.lo = (uint32_t)w1;
     r.hi = (uint32_t)(w1 >> 32);
-    r.ah = __uint_as_float((uint32_t)w2);
-    r.al = __uint_as_float((uint32_t)(w2 >> 32));
-    r.bh = __uint_as_float((uint32_t)w3);
-    r.bl = __uint_as_float((uint32_t)(w3 >> 32));
+    r.a = __longlong_as_double((long long)w2);
+    r.b = __longlong_as_double((long long)w3);
     r.e_lo = (int32_t)(uint32_t)w4;
     r.e_hi = (int32_t)(uint32_t)(w4 >> 32);
-    r.a = __longlong_as_double((long long)w5);
-    r.b = __longlong_as_double((long long)w6);
-    r.pad = w7;
+    r.pad[0] = w5;
+    r.pad[1] = w6;
+    r.pad[2] = w7;
     return r;
   }
   __device__ __forceinline__ static int64_t pred(const Leaf& lf, uint64_t x) {
-    const bool neg = x < lf.base_key;
-    const uint64_t d = neg ? lf.base_key - x : x - lf.base_key;
-    float Dh, Dl;
-    u64_to_ff(d, Dh, Dl);
-    if (neg) {
-      Dh = -Dh;
-      Dl = -Dl;
-    }
-    int64_t f;
-    if (ff_floor_fma(lf.ah, lf.al, Dh, Dl, lf.bh, lf.bl, f)) return f;   // |f| < 2^21
-    return pred_exact(x, lf.base_key, lf.a, lf.b);
+    return pred(x, lf.base_key, lf.a, lf.b);
   }
 };
 

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <memory>
 #include <string>
 
 #include "../../include/ljoin.h"
@@ -16,6 +17,7 @@ struct lj_index {
   int precision = LJ_FP32;
   int device = 0;
   void* leaves = nullptr;        // L records (LeafF32 or LeafF64), device
+  std::shared_ptr<void> leaves_block;   // owner of `leaves` (shared by a batch's indexes)
   double root_fit[2] = {0, 0};   // least-squares root (double)
   float root_f32[2] = {0, 0};    // deployed single-precision root
   double root_f64[2] = {0, 0};   // deployed double-precision root

@@ -295,14 +295,15 @@ template <class Model, int MODE, int CHUNK, bool VEC, int GAP>
 __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32_t* __restrict__ out,
                                              unsigned long long* __restrict__ tile_counts) {
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * CHUNK;
-  static_assert(kCompactTile % kChunkProbes == 0, "a chunk must lie in one compaction tile");
+  static_assert((256ull * kSmallScanItems) % kChunkProbes == 0,
+                "a chunk must lie in one compaction tile");
   __shared__ unsigned long long s_count[kSearchBlock / 32];
   const uint64_t first = blockIdx.x * kChunkProbes;
   unsigned long long c = 0;
 #pragma unroll 1
   for (int t = 0; t < CHUNK; ++t) {
     const uint64_t j0 = first + (uint64_t)t * 2 * kSearchBlock + 2 * threadIdx.x;
-    if (j0 >= P.m) break;
+    if (__all_sync(0xffffffffu, j0 >= P.m)) break;   // warp-uniform: lookups run as a warp
     uint32_t r_idx[2], cnt[2];
     bool valid[2];
     if constexpr (GAP != 0)
@@ -341,7 +342,7 @@ __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32
     unsigned long long tot = 0;
 #pragma unroll
     for (int w = 0; w < kSearchBlock / 32; ++w) tot += s_count[w];
-    if (tot) atomicAdd(tile_counts + first / kCompactTile, tot);
+    if (tot) atomicAdd(tile_counts + (first >> P.tile_shift), tot);
   }
 }
 
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
         const uint64_t size = bend[b] - (b ? bend[b - 1] : 0);
         valid[p] = size > kSortMergeMax;
       }
-    if (!valid[0] && !valid[1]) return;
+    if (__all_sync(0xffffffffu, !valid[0] && !valid[1])) return;   // warp-uniform
   }
   uint32_t r_idx[2], cnt[2];
   lookup_keys<Model, MODE, 2>(P, x, valid, r_idx, cnt);
@@ -606,16 +607,16 @@ __global__ void __launch_bounds__(kSortMergeBlock)
   }
 }
 
-// Matches per compaction tile (kCompactTile words), one block per tile.
+// Matches per compaction tile (`tile` words), one block per tile.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock)
     tile_count_kernel(const uint32_t* __restrict__ words, uint64_t m,
-                      unsigned long long* __restrict__ tile_counts) {
+                      unsigned long long* __restrict__ tile_counts, uint32_t tile) {
   __shared__ unsigned long long s_w[kWarps];
-  const uint64_t base = (uint64_t)blockIdx.x * kCompactTile;
+  const uint64_t base = (uint64_t)blockIdx.x * tile;
   unsigned long long c = 0;
 #pragma unroll 4
-  for (uint32_t i = threadIdx.x; i < kCompactTile; i += kBlock) {
+  for (uint32_t i = threadIdx.x; i < tile; i += kBlock) {
     const uint64_t q = base + i;
     if (q < m) {
       const uint32_t w = words[q];
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 // Compaction kernel of the pipeline: tiles of 256 threads x 16 words
-// (kCompactTile probes).  Each tile already knows its first output position
+// (kCompactTile probes; 256 x 4 for small batches).  Each tile already knows its first output position
 // (tile_scan_kernel), so tiles never wait for one another: load the words,
 // scan them in the block, stage the output in shared memory and write it
 // with coalesced stores:
@@ -663,15 +664,16 @@ struct ScanParams {
 // Batches of at most this many compaction tiles take the direct prefixes.
 constexpr uint32_t kDirectPrefixTiles = 1024;
 
-template <int MODE, bool FROM_COUNTS, bool VEC>
+template <int MODE, bool FROM_COUNTS, bool VEC, int ITEMS>
 __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
+  constexpr uint64_t kTile = (uint64_t)kBlock * ITEMS;
   __shared__ uint64_t s_warp[kWarps];
-  __shared__ uint64_t s_stage[kCompactTile];   // 32 KB
+  __shared__ uint64_t s_stage[kTile];   // 32 KB for tiles of 4096
   __shared__ uint64_t s_count;
   const uint32_t tile = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t tile_base = (uint64_t)tile * kCompactTile;
-  const uint64_t base = tile_base + (uint64_t)threadIdx.x * kScanItems;
+  const uint64_t tile_base = (uint64_t)tile * kTile;
+  const uint64_t base = tile_base + (uint64_t)threadIdx.x * ITEMS;
   uint64_t prefix;
   if (P.tile_counts) {
     __shared__ unsigned long long s_red[kWarps];
@@ -694,10 +696,10 @@ __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
   } else {
     prefix = P.tile_prefix[tile];
   }
-  uint32_t v[kScanItems];
-  if (VEC && base + kScanItems <= P.m) {
+  uint32_t v[ITEMS];
+  if (VEC && base + ITEMS <= P.m) {
 #pragma unroll
-    for (int q = 0; q < kScanItems / 4; ++q) {
+    for (int q = 0; q < ITEMS / 4; ++q) {
       const uint4 u = ldg_stream_u32x4(P.in + base + 4 * q);
       v[4 * q] = u.x;
       v[4 * q + 1] = u.y;
@@ -706,12 +708,12 @@ __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i)
+    for (int i = 0; i < ITEMS; ++i)
       v[i] = base + i < P.m ? __ldg(P.in + base + i) : (FROM_COUNTS ? 0u : kNoMatch);
   }
   uint64_t sum = 0;
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) sum += FROM_COUNTS ? v[i] : (v[i] != kNoMatch ? 1u : 0u);
+  for (int i = 0; i < ITEMS; ++i) sum += FROM_COUNTS ? v[i] : (v[i] != kNoMatch ? 1u : 0u);
   const uint64_t inc = warp_inclusive_sum(sum, lane);
   if (lane == 31) s_warp[warp] = inc;
   __syncthreads();
@@ -724,7 +726,7 @@ __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
   uint64_t local = s_warp[warp] + inc - sum;   // tile offset of this thread's first item
   if (MODE == kScanPairs) {
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i)
+    for (int i = 0; i < ITEMS; ++i)
       if (v[i] != kNoMatch) {
         s_stage[local] = (uint64_t)v[i] | ((uint64_t)(uint32_t)(base + i + P.s_base) << 32);
         ++local;
@@ -738,29 +740,29 @@ __global__ void __launch_bounds__(kBlock) compact_kernel(ScanParams P) {
       if (o < P.capacity) st_stream_u64(out + o, s_stage[q]);
     }
   } else {
-    const uint32_t first = threadIdx.x * kScanItems;
+    const uint32_t first = threadIdx.x * ITEMS;
     if (P.offsets) {
 #pragma unroll
-      for (int i = 0; i < kScanItems; ++i) {
+      for (int i = 0; i < ITEMS; ++i) {
         s_stage[first + i] = prefix + local;
         local += FROM_COUNTS ? v[i] : (v[i] != kNoMatch ? 1u : 0u);
       }
     }
     if (!FROM_COUNTS && P.counts && base < P.m) {
-      if (VEC && base + kScanItems <= P.m) {
+      if (VEC && base + ITEMS <= P.m) {
 #pragma unroll
-        for (int q = 0; q < kScanItems / 4; ++q)
+        for (int q = 0; q < ITEMS / 4; ++q)
           reinterpret_cast<uint4*>(P.counts + base)[q] =
               make_uint4(v[4 * q] != kNoMatch, v[4 * q + 1] != kNoMatch, v[4 * q + 2] != kNoMatch,
                          v[4 * q + 3] != kNoMatch);
       } else {
-        for (int i = 0; i < kScanItems; ++i)
+        for (int i = 0; i < ITEMS; ++i)
           if (base + i < P.m) P.counts[base + i] = v[i] != kNoMatch;
       }
     }
     if (P.offsets) {
       __syncthreads();
-      const uint64_t len = P.m - tile_base < kCompactTile ? P.m - tile_base : kCompactTile;
+      const uint64_t len = P.m - tile_base < kTile ? P.m - tile_base : kTile;
       for (uint64_t q = threadIdx.x; q < len; q += kBlock) P.offsets[tile_base + q] = s_stage[q];
     }
   }
@@ -942,9 +944,9 @@ int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, 
   {
     KernelTimer kt("tile_count_kernel", s);
     if (dup)
-      tile_count_kernel<kDupCount><<<tiles, kBlock, 0, s>>>(words, m, tile_counts);
+      tile_count_kernel<kDupCount><<<tiles, kBlock, 0, s>>>(words, m, tile_counts, 1u << P.tile_shift);
     else
-      tile_count_kernel<kUniqueCount><<<tiles, kBlock, 0, s>>>(words, m, tile_counts);
+      tile_count_kernel<kUniqueCount><<<tiles, kBlock, 0, s>>>(words, m, tile_counts, 1u << P.tile_shift);
   }
   LJ_CUDA(cudaGetLastError());
   LJ_CUDA(scratch_free(ws, s));
@@ -961,7 +963,11 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   const bool dup = mode == kDupCount;
   // duplicates: the search writes counts, into the caller's buffer if given
   const bool words_in_counts = dup && counts && aligned(counts, 16);
-  const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, (m + kCompactTile - 1) / kCompactTile);
+  // small batches: tiles of 1024 probes (more blocks for the compaction)
+  const bool small = m <= kSmallBatch;
+  const uint32_t tile_shift = small ? 10 : 12;
+  static_assert(kCompactTile == 4096 && 256 * kSmallScanItems == 1024, "tile sizes");
+  const uint32_t tiles = (uint32_t)std::max<uint64_t>(1, (m + (1ull << tile_shift) - 1) >> tile_shift);
   const size_t b_cnt = ((size_t)tiles * 8 + 255) / 256 * 256;
   const size_t b_pre = ((size_t)(tiles + 1) * 8 + 255) / 256 * 256;
   const size_t b_words = words_in_counts ? 0 : ((m + 3) & ~3ull) * 4;
@@ -987,6 +993,7 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   ProbeParams<Model> P = make_params(idx, model, S, m, s_base, device_error_word(idx->device));
   if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
   P.first = first;
+  P.tile_shift = tile_shift;
   const bool vec = aligned(S, 16) && (!first || aligned(first, 8));
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * kSearchChunk;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (m + kChunkProbes - 1) / kChunkProbes);
@@ -1054,15 +1061,23 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
   const bool qvec = aligned(words, 16) && (!Q.counts || aligned(Q.counts, 16));
   if (need_compact) {
     KernelTimer kt("compact_kernel", s);
-    if (mode == kUniqueEmit)
-      qvec ? compact_kernel<kScanPairs, false, true><<<tiles, kBlock, 0, s>>>(Q)
-           : compact_kernel<kScanPairs, false, false><<<tiles, kBlock, 0, s>>>(Q);
-    else if (dup)
-      qvec ? compact_kernel<kScanOffsets, true, true><<<tiles, kBlock, 0, s>>>(Q)
-           : compact_kernel<kScanOffsets, true, false><<<tiles, kBlock, 0, s>>>(Q);
+#define LJ_COMPACT(ITEMS)                                                                  \
+  do {                                                                                     \
+    if (mode == kUniqueEmit)                                                               \
+      qvec ? compact_kernel<kScanPairs, false, true, ITEMS><<<tiles, kBlock, 0, s>>>(Q)    \
+           : compact_kernel<kScanPairs, false, false, ITEMS><<<tiles, kBlock, 0, s>>>(Q);  \
+    else if (dup)                                                                          \
+      qvec ? compact_kernel<kScanOffsets, true, true, ITEMS><<<tiles, kBlock, 0, s>>>(Q)   \
+           : compact_kernel<kScanOffsets, true, false, ITEMS><<<tiles, kBlock, 0, s>>>(Q); \
+    else                                                                                   \
+      qvec ? compact_kernel<kScanOffsets, false, true, ITEMS><<<tiles, kBlock, 0, s>>>(Q)  \
+           : compact_kernel<kScanOffsets, false, false, ITEMS><<<tiles, kBlock, 0, s>>>(Q); \
+  } while (0)
+    if (small)
+      LJ_COMPACT(kSmallScanItems);
     else
-      qvec ? compact_kernel<kScanOffsets, false, true><<<tiles, kBlock, 0, s>>>(Q)
-           : compact_kernel<kScanOffsets, false, false><<<tiles, kBlock, 0, s>>>(Q);
+      LJ_COMPACT(kScanItems);
+#undef LJ_COMPACT
   }
   LJ_CUDA(cudaGetLastError());
   if (dup && counts && !words_in_counts)

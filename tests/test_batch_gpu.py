@@ -130,3 +130,53 @@ def test_autotuner_choice_does_not_change_results():
             pairs = torch.empty((max(S.numel(), 1), 2), dtype=torch.int32, device="cuda")
             t = lj.join_emit(idx, S, pairs)
             assert np.array_equal(pairs[:t].cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batched_index_build_is_bit_identical(prec):
+    """rmi_build_batch (one segmented pass over all relations) gives, for
+    every relation, exactly the index rmi_build gives for it alone: root,
+    leaf ranges, deployed parameters and error bounds; and each index also
+    passes the oracle's checks (tests/_validate.py)."""
+    from tests import _validate
+    lj = _lj()
+    joins = dg.batched_workload(k=24, seed=12, device="cuda", scale=1 / 32)
+    Rs = [j["R"] for j in joins]
+    Rs[3] = Rs[3][:0]                                   # an empty relation
+    Rs[5] = Rs[5][:1]                                   # a single key
+    Rs[7] = torch.sort(torch.cat([Rs[7], Rs[7][::3]]))[0]   # duplicates
+    leaves = [max(1, R.numel() // 48) for R in Rs]
+    leaves[0] = 1
+    leaves[1] = 1 << 14                                 # far more leaves than keys
+    batch = lj.rmi_build_batch(Rs, leaves, prec)
+    for R, L, b in zip(Rs, leaves, batch):
+        one = lj.rmi_build(R, L, prec)
+        ea, eb = lj.rmi_export(one), lj.rmi_export(b)
+        for key in ea:
+            assert np.array_equal(ea[key], eb[key]), key
+        sa, sb = one.stats(), b.stats()
+        for key in ("unique", "nonempty_leaves", "max_leaf_size", "max_window", "mean_window"):
+            assert sa[key] == sb[key], key
+        if R.numel():
+            Rh = _u64(R)
+            _validate.compare_index(Rh, eb, oracle.rmi_fit(Rh, L, prec == "fp64"), prec == "fp64")
+    # the batch's indexes join exactly like indexes built alone
+    S = joins[2]["S"]
+    p1 = torch.empty((S.numel(), 2), dtype=torch.int32, device="cuda")
+    t1 = lj.join_emit(batch[2], S, p1)
+    assert np.array_equal(p1[:t1].cpu().numpy().view(np.uint32),
+                          oracle.join_pairs(_u64(Rs[2]), _u64(S)))
+    # freeing indexes of a batch in any order keeps the others usable
+    del batch[0:2]
+    assert lj.join_emit(batch[0], S, p1) == t1
+
+
+def test_batched_index_build_rejects_an_unsorted_relation():
+    lj = _lj()
+    joins = dg.batched_workload(k=3, seed=13, device="cuda", scale=1 / 64)
+    Rs = [j["R"] for j in joins]
+    bad = Rs[1].clone()
+    bad[0], bad[-1] = Rs[1][-1], Rs[1][0]
+    with pytest.raises(lj.LJoinError) as e:
+        lj.rmi_build_batch([Rs[0], bad, Rs[2]], [16, 16, 16], "fp32")
+    assert e.value.code == -4          # LJ_E_UNSORTED
