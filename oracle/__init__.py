@@ -23,6 +23,11 @@ Learned In-Memory Joins"):
   lhash_build / lhash_join   Section 3.C (learned hash index: the CDF model as
                              an order-preserving hash into a table of 4-slot
                              buckets with linear probing)
+  rs_build / rs_predict      Section 2.D (RadixSpline: greedy error-bounded
+                             spline over the CDF, radix table over key
+                             prefixes, interpolation between spline points)
+  rs_lhash_build / _join     Section 3.C with a RadixSpline as the hash
+                             (the paper's RSHASH-INLJ)
 """
 from __future__ import annotations
 
@@ -92,6 +97,17 @@ def _load():
                                                         P, P, U64, P, P, U64, P, U64, P, U64, P,
                                                         P, P]
             lib.lj_oracle_lhash_join_ranges.restype = ctypes.c_int64
+            lib.lj_oracle_rs_build.argtypes = [P, U64, ctypes.c_uint32, U64, ctypes.c_uint32,
+                                               P, P, U64, P, P]
+            lib.lj_oracle_rs_build.restype = ctypes.c_int64
+            lib.lj_oracle_rs_predict_many.argtypes = [P, P, U64, U64, P, U64, P]
+            lib.lj_oracle_rs_predict_many.restype = None
+            lib.lj_oracle_rs_lhash_build.argtypes = [P, U64, P, P, U64, ctypes.c_uint32, P, P,
+                                                     U64, P, P, P]
+            lib.lj_oracle_rs_lhash_build.restype = ctypes.c_int64
+            lib.lj_oracle_rs_lhash_join_ranges.argtypes = [P, U64, P, P, U64, U64, P, P, U64,
+                                                           P, U64, P, U64, P, P]
+            lib.lj_oracle_rs_lhash_join_ranges.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -335,3 +351,90 @@ def lhash_join(R, h: LHash, S) -> tuple[np.ndarray, np.ndarray, int, np.ndarray]
         h.B, _ptr(h.keys), _ptr(h.pos), h.keys.size, _ptr(h.first), h.D, _ptr(S), S.size,
         _ptr(lo), _ptr(hi), _ptr(loads))
     return lo, hi, int(total), loads
+
+
+@dataclass
+class RadixSpline:
+    """RadixSpline of a sorted R (oracle side): S spline points (sx, sy),
+    radix table (2^rbits + 1 entries) over (key - sx[0]) >> shift."""
+    eps: int
+    chunk: int
+    rbits: int
+    sx: np.ndarray        # (S,) uint64
+    sy: np.ndarray        # (S,) uint32
+    table: np.ndarray     # (2^rbits + 1,) uint32
+    shift: int
+    n: int
+
+
+def rs_build(R, eps: int = 32, chunk: int = 1024, rbits: int = 18) -> RadixSpline:
+    R = _u64(R)
+    lib = _load()
+    shift = ctypes.c_uint32()
+    S = lib.lj_oracle_rs_build(_ptr(R), R.size, eps, chunk, rbits, None, None, 0, None,
+                               ctypes.byref(shift))
+    if S == -1:
+        raise OracleError("R is not sorted non-decreasing")
+    if S < 0:
+        raise MemoryError("oracle ran out of memory")
+    sx = np.zeros(S, dtype=np.uint64)
+    sy = np.zeros(S, dtype=np.uint32)
+    table = np.zeros((1 << rbits) + 1, dtype=np.uint32)
+    rc = lib.lj_oracle_rs_build(_ptr(R), R.size, eps, chunk, rbits, _ptr(sx), _ptr(sy), S,
+                                _ptr(table), ctypes.byref(shift))
+    if rc != S:
+        raise OracleError(f"RadixSpline build failed ({rc})")
+    return RadixSpline(eps, chunk, rbits, sx, sy, table, int(shift.value), int(R.size))
+
+
+def rs_predict(rs: RadixSpline, X) -> np.ndarray:
+    """Predicted position of every key of X (uint64)."""
+    X = _u64(X)
+    out = np.zeros(X.size, dtype=np.uint64)
+    _load().lj_oracle_rs_predict_many(_ptr(rs.sx), _ptr(rs.sy), rs.sx.size, rs.n, _ptr(X),
+                                      X.size, _ptr(out))
+    return out
+
+
+@dataclass
+class RSHash:
+    """Learned hash index with a RadixSpline as the hash (oracle side)."""
+    rs: RadixSpline
+    spk: int
+    keys: np.ndarray      # (C,) uint64
+    pos: np.ndarray       # (C+1,) uint32
+    first: np.ndarray     # (D+1,) uint32
+    D: int
+    B: int
+
+
+def rs_lhash_build(R, rs: RadixSpline, spk: int) -> RSHash:
+    R = _u64(R)
+    lib = _load()
+    args = (_ptr(R), R.size, _ptr(rs.sx), _ptr(rs.sy), rs.sx.size, spk)
+    D, B = ctypes.c_uint64(), ctypes.c_uint64()
+    C = lib.lj_oracle_rs_lhash_build(*args, None, None, 0, None, ctypes.byref(D),
+                                     ctypes.byref(B))
+    if C == -1:
+        raise OracleError("R is not sorted non-decreasing")
+    if C < 0:
+        raise MemoryError("oracle ran out of memory")
+    keys = np.zeros(C, dtype=np.uint64)
+    pos = np.zeros(C + 1, dtype=np.uint32)
+    first = np.zeros(D.value + 1, dtype=np.uint32)
+    rc = lib.lj_oracle_rs_lhash_build(*args, _ptr(keys), _ptr(pos), C, _ptr(first), None, None)
+    if rc != C:
+        raise OracleError(f"hash build failed ({rc})")
+    return RSHash(rs, spk, keys, pos, first, D.value, B.value)
+
+
+def rs_lhash_join(R, h: RSHash, S) -> tuple[np.ndarray, np.ndarray, int]:
+    """Per-probe match ranges through the RadixSpline hash index and |J|."""
+    R, S = _u64(R), _u64(S)
+    lo = np.zeros(S.size, dtype=np.uint64)
+    hi = np.zeros(S.size, dtype=np.uint64)
+    rs = h.rs
+    total = _load().lj_oracle_rs_lhash_join_ranges(
+        _ptr(R), R.size, _ptr(rs.sx), _ptr(rs.sy), rs.sx.size, h.B, _ptr(h.keys), _ptr(h.pos),
+        h.keys.size, _ptr(h.first), h.D, _ptr(S), S.size, _ptr(lo), _ptr(hi))
+    return lo, hi, int(total)

@@ -587,3 +587,264 @@ int64_t lj_oracle_lhash_join_ranges(const uint64_t* R, uint64_t n, uint32_t L, i
   }
   return total;
 }
+
+/* ---------------------------------------------------------- RadixSpline -- */
+/*
+ * RadixSpline (Section 2.D; Kipf et al., "RadixSpline: a single-pass learned
+ * index", aiDM 2020), the model of the learned hash INLJ variant (Section
+ * 3.C uses a RadixSpline as the hash function).  Built bottom-up in one pass
+ * over the sorted keys:
+ *   CDF points  the distinct keys k_d with the position of their first copy
+ *               in R, (k_d, first_d), d = 0..D-1;
+ *   spline      points chosen greedily (the error corridor of Neumann and
+ *               Michel, "Smooth interpolating histograms with error
+ *               guarantees", 2008): from the last spline point b, every
+ *               later CDF point q narrows a corridor of slopes to the window
+ *               [q.y - eps, q.y + eps]; the first point whose own slope from b
+ *               leaves the corridor makes the point before it a spline point,
+ *               which restarts the corridor.  Every CDF point then lies
+ *               within eps positions of the straight line between the spline
+ *               points around it.  The pass restarts at every `chunk`-th
+ *               CDF point (a spline point; chunk = 0: one pass over all);
+ *   radix table over the r most significant bits of (key - k_0) of the
+ *               spline points: table[b] = number of spline points whose
+ *               prefix is below b, b = 0..2^r, shift = max(0, bitlen(k_max -
+ *               k_0) - r);
+ *   prediction  for k_0 <= x <= k_max: the spline points (x_i, y_i) <= x <
+ *               (x_{i+1}, y_{i+1}) around x (prefix of x -> table -> binary
+ *               search), pred = y_i + floor((x - x_i)(y_{i+1} - y_i) /
+ *               (x_{i+1} - x_i)); below k_0: 0; above k_max: n.
+ * The slope comparisons and the interpolation are exact integer arithmetic.
+ */
+
+/* a/b < c/d for b, d > 0 */
+static int slope_lt(__int128 a, __int128 b, __int128 c, __int128 d) { return a * d < c * b; }
+
+/* Spline points of the distinct keys dk[0..D) with positions dy[0..D):
+ * writes up to cap points to sx/sy (if non-NULL) and returns their count. */
+static uint64_t rs_spline(const uint64_t* dk, const uint64_t* dy, uint64_t D, uint32_t eps,
+                          uint64_t chunk, uint64_t* sx, uint32_t* sy, uint64_t cap) {
+  uint64_t S = 0;
+#define RS_EMIT(d)                                         \
+  do {                                                     \
+    if (sx && S < cap) {                                   \
+      sx[S] = dk[d];                                       \
+      sy[S] = (uint32_t)dy[d];                             \
+    }                                                      \
+    ++S;                                                   \
+  } while (0)
+  if (chunk == 0) chunk = D ? D : 1;
+  for (uint64_t c0 = 0; c0 < D; c0 += chunk) {
+    const uint64_t c1 = c0 + chunk < D ? c0 + chunk : D;
+    uint64_t base = c0;                 /* last spline point */
+    RS_EMIT(base);
+    __int128 up_dy = 0, up_dx = 1, lo_dy = 0, lo_dx = 1;   /* corridor: slopes lo <= s <= up */
+    int open = 0;                       /* corridor started (a point after base seen) */
+    for (uint64_t d = c0 + 1; d < c1; ++d) {
+      const __int128 dx = (__int128)(dk[d] - dk[base]);
+      const __int128 y = (__int128)dy[d] - (__int128)dy[base];
+      if (!open) {
+        up_dy = y + eps;
+        up_dx = dx;
+        lo_dy = y - eps;
+        lo_dx = dx;
+        open = 1;
+        continue;
+      }
+      if (slope_lt(up_dy, up_dx, y, dx) || slope_lt(y, dx, lo_dy, lo_dx)) {
+        /* d leaves the corridor: the point before it becomes a spline point */
+        base = d - 1;
+        RS_EMIT(base);
+        const __int128 dx2 = (__int128)(dk[d] - dk[base]);
+        const __int128 y2 = (__int128)dy[d] - (__int128)dy[base];
+        up_dy = y2 + eps;
+        up_dx = dx2;
+        lo_dy = y2 - eps;
+        lo_dx = dx2;
+        continue;
+      }
+      if (slope_lt(y + eps, dx, up_dy, up_dx)) {
+        up_dy = y + eps;
+        up_dx = dx;
+      }
+      if (slope_lt(lo_dy, lo_dx, y - eps, dx)) {
+        lo_dy = y - eps;
+        lo_dx = dx;
+      }
+    }
+    if (c1 - 1 != base) RS_EMIT(c1 - 1);
+  }
+#undef RS_EMIT
+  return S;
+}
+
+/* bit length of v (0 for 0) */
+static uint32_t bitlen64(uint64_t v) {
+  uint32_t b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+/*
+ * Build the RadixSpline of sorted R.  Returns S (the number of spline
+ * points); sx/sy (S entries) and table (2^rbits + 1 entries) are written when
+ * non-NULL and S <= cap; *shift_out receives the prefix shift.  -1: R not
+ * sorted, -2: out of memory, -3: cap < S.
+ */
+int64_t lj_oracle_rs_build(const uint64_t* R, uint64_t n, uint32_t eps, uint64_t chunk,
+                           uint32_t rbits, uint64_t* sx, uint32_t* sy, uint64_t cap,
+                           uint32_t* table, uint32_t* shift_out) {
+  if (!lj_oracle_is_sorted(R, n)) return -1;
+  uint64_t D = 0;
+  for (uint64_t i = 0; i < n; ++i)
+    if (i == 0 || R[i] != R[i - 1]) ++D;
+  uint64_t* dk = (uint64_t*)malloc(sizeof(uint64_t) * (D ? D : 1));
+  uint64_t* dy = (uint64_t*)malloc(sizeof(uint64_t) * (D ? D : 1));
+  if (!dk || !dy) {
+    free(dk);
+    free(dy);
+    return -2;
+  }
+  uint64_t d = 0;
+  for (uint64_t i = 0; i < n; ++i)
+    if (i == 0 || R[i] != R[i - 1]) {
+      dk[d] = R[i];
+      dy[d] = i;
+      ++d;
+    }
+  const uint64_t S = rs_spline(dk, dy, D, eps, chunk, NULL, NULL, 0);
+  if (sx) {
+    if (cap < S) {
+      free(dk);
+      free(dy);
+      return -3;
+    }
+    rs_spline(dk, dy, D, eps, chunk, sx, sy, cap);
+  }
+  const uint32_t bl = D ? bitlen64(dk[D - 1] - dk[0]) : 0;
+  const uint32_t shift = bl > rbits ? bl - rbits : 0;
+  if (shift_out) *shift_out = shift;
+  if (table && sx) {
+    const uint64_t T = 1ull << rbits;
+    for (uint64_t b = 0; b <= T; ++b) {
+      uint64_t c = 0;   /* spline points with prefix below b */
+      while (c < S && ((sx[c] - dk[0]) >> shift) < b) ++c;
+      table[b] = (uint32_t)c;
+    }
+  }
+  free(dk);
+  free(dy);
+  return (int64_t)S;
+}
+
+/* Position predicted for x (see above); binary search over all spline points. */
+uint64_t lj_oracle_rs_predict(const uint64_t* sx, const uint32_t* sy, uint64_t S, uint64_t n,
+                              uint64_t x) {
+  if (S == 0 || x < sx[0]) return 0;
+  if (x > sx[S - 1]) return n;
+  uint64_t a = 0, b = S;   /* last i with sx[i] <= x */
+  while (b - a > 1) {
+    const uint64_t mid = a + (b - a) / 2;
+    if (sx[mid] <= x)
+      a = mid;
+    else
+      b = mid;
+  }
+  if (sx[a] == x || a + 1 == S) return sy[a];
+  const unsigned __int128 num = (unsigned __int128)(x - sx[a]) * (uint64_t)(sy[a + 1] - sy[a]);
+  return sy[a] + (uint64_t)(num / (sx[a + 1] - sx[a]));
+}
+
+/* Learned hash index with a RadixSpline as the hash (RSHASH-INLJ):
+ * h(x) = pred(x) * B / (n + 1); otherwise as lj_oracle_lhash_build. */
+int64_t lj_oracle_rs_lhash_build(const uint64_t* R, uint64_t n, const uint64_t* sx,
+                                 const uint32_t* sy, uint64_t S, uint32_t spk, uint64_t* keys,
+                                 uint32_t* pos, uint64_t cap, uint32_t* first, uint64_t* D_out,
+                                 uint64_t* B_out) {
+  if (!lj_oracle_is_sorted(R, n)) return -1;
+  uint64_t D = 0;
+  for (uint64_t i = 0; i < n; ++i)
+    if (i == 0 || R[i] != R[i - 1]) ++D;
+  uint64_t B = (spk * D + 3) / 4;
+  if (B == 0) B = 1;
+  uint64_t* slot = (uint64_t*)malloc(sizeof(uint64_t) * (D ? D : 1));
+  uint64_t* dkey = (uint64_t*)malloc(sizeof(uint64_t) * (D ? D : 1));
+  if (!slot || !dkey) {
+    free(slot);
+    free(dkey);
+    return -2;
+  }
+  uint64_t d = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (i > 0 && R[i] == R[i - 1]) continue;
+    dkey[d] = R[i];
+    if (first) first[d] = (uint32_t)i;
+    uint64_t s = 4 * (lj_oracle_rs_predict(sx, sy, S, n, R[i]) * B / (n + 1));
+    if (d > 0 && s <= slot[d - 1]) s = slot[d - 1] + 1;   /* linear probing */
+    slot[d] = s;
+    ++d;
+  }
+  if (first) first[D] = (uint32_t)n;
+  uint64_t C = 4 * B;
+  if (D > 0 && slot[D - 1] + 1 > C) C = slot[D - 1] + 1;
+  if (keys) {
+    if (cap < C) {
+      free(slot);
+      free(dkey);
+      return -3;
+    }
+    uint64_t next_key = UINT64_MAX;
+    uint32_t next_pos = (uint32_t)D;
+    uint64_t k = D;
+    for (uint64_t s = C; s-- > 0;) {
+      if (k > 0 && slot[k - 1] == s) {
+        --k;
+        next_key = dkey[k];
+        next_pos = (uint32_t)k;
+      }
+      keys[s] = next_key;
+      pos[s] = next_pos;
+    }
+    pos[C] = (uint32_t)D;
+  }
+  if (D_out) *D_out = D;
+  if (B_out) *B_out = B;
+  free(slot);
+  free(dkey);
+  return (int64_t)C;
+}
+
+/* Join through the RadixSpline hash index: [lo[j], hi[j]) per probe. */
+int64_t lj_oracle_rs_lhash_join_ranges(const uint64_t* R, uint64_t n, const uint64_t* sx,
+                                       const uint32_t* sy, uint64_t S, uint64_t B,
+                                       const uint64_t* keys, const uint32_t* pos, uint64_t C,
+                                       const uint32_t* first, uint64_t D, const uint64_t* Sq,
+                                       uint64_t m, uint64_t* lo, uint64_t* hi) {
+  int64_t total = 0;
+  for (uint64_t j = 0; j < m; ++j) {
+    uint64_t s = 4 * (lj_oracle_rs_predict(sx, sy, S, n, Sq[j]) * B / (n + 1));
+    while (s < C && keys[s] < Sq[j]) ++s;
+    if (s < C && keys[s] == Sq[j] && pos[s] < D) {
+      lo[j] = first[pos[s]];
+      hi[j] = first[pos[s] + 1];
+    } else {
+      uint64_t a = 0, b = n;
+      while (a < b) {
+        uint64_t mid = a + (b - a) / 2;
+        if (R[mid] < Sq[j]) a = mid + 1; else b = mid;
+      }
+      lo[j] = hi[j] = a;
+    }
+    total += (int64_t)(hi[j] - lo[j]);
+  }
+  return total;
+}
+
+/* pred[j] = lj_oracle_rs_predict(..., X[j]) for j < m. */
+void lj_oracle_rs_predict_many(const uint64_t* sx, const uint32_t* sy, uint64_t S, uint64_t n,
+                               const uint64_t* X, uint64_t m, uint64_t* pred) {
+  for (uint64_t j = 0; j < m; ++j) pred[j] = lj_oracle_rs_predict(sx, sy, S, n, X[j]);
+}

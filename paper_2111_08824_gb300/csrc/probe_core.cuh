@@ -147,103 +147,6 @@ __device__ __forceinline__ void search_last(const uint64_t* __restrict__ R,
   }
 }
 
-// Unique-key lookups finish with a window of at most kScanKeys keys, read
-// by the whole warp together (scan_windows) instead of halving to one key.
-constexpr uint32_t kScanKeys = 16;   // keys of one 128-byte line of R
-
-// Halving steps (the same pivots as search_last, non-strict) while a window
-// has more than kScanKeys keys.  Afterwards the last position whose key is
-// <= x lies in [base, base + len) or, if no key of the window is <= x, right
-// before the original window.
-template <int NP>
-__device__ __forceinline__ void narrow_window(const uint64_t* __restrict__ R,
-                                              const uint64_t (&x)[NP], uint32_t (&base)[NP],
-                                              uint32_t (&len)[NP]) {
-  while (true) {
-    bool any = false;
-    uint64_t v[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p)
-      if (len[p] > kScanKeys) {
-        any = true;
-        v[p] = ldg_key(R, base[p] + (len[p] >> 1));
-      }
-    if (!any) break;
-#pragma unroll
-    for (int p = 0; p < NP; ++p)
-      if (len[p] > kScanKeys) {
-        const uint32_t half = len[p] >> 1;
-        if (v[p] <= x[p]) base[p] += half;
-        len[p] -= half;
-      }
-  }
-}
-
-// The windows [b, b + len) (len <= kScanKeys; 0 = nothing to read) of the
-// 32 lanes' probes x, read cooperatively: called by all 32 lanes of a warp
-// together.  A window spans at most two 128-byte lines of R.  Groups of 4
-// lanes take 8 probes at a time; lane q of a group reads the q-th 32-byte
-// sector (4 keys) of the probe's line, so one load instruction of the warp
-// covers 8 whole lines, one per probe: one L1 wavefront per line instead of
-// one per key read by a halving step.  For its own probe each lane gets
-// le = the number of keys <= x in its window and eq = some key of the window
-// equals x.  R must be 32-byte aligned when r32 (else 8-byte loads).
-template <int NP>
-__device__ __forceinline__ void scan_windows(const uint64_t* __restrict__ R, uint32_t n, bool r32,
-                                             const uint64_t (&x)[NP], const uint32_t (&b)[NP],
-                                             const uint32_t (&len)[NP], uint32_t (&le)[NP],
-                                             bool (&eq)[NP]) {
-  constexpr unsigned kAll = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, q = lane & 3;
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    le[p] = 0;
-    eq[p] = false;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int o = 8 * s + g;                       // the probe this group reads now
-      const uint32_t bo = __shfl_sync(kAll, b[p], o);
-      const uint32_t lo_len = __shfl_sync(kAll, len[p], o);
-      const uint64_t xo = __shfl_sync(kAll, (unsigned long long)x[p], o);
-      uint32_t c = 0;
-      bool e = false;
-      if (lo_len) {
-        const uint32_t end = bo + lo_len;
-        const uint32_t l0 = bo / kScanKeys, l1 = (end - 1) / kScanKeys;
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const uint32_t p0 = (l0 + t) * kScanKeys + 4 * q;   // first key of the lane's sector
-          if (l0 + t <= l1 && p0 < end && p0 + 4 > bo) {
-            uint64_t k4[4];
-            if (r32 && p0 + 4 <= n) {
-              ldg_key4(R, p0, k4);
-            } else {
-#pragma unroll
-              for (int i = 0; i < 4; ++i) k4[i] = p0 + i < n ? ldg_key(R, p0 + i) : ~0ull;
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const bool in = p0 + i >= bo && p0 + i < end;
-              c += (in && k4[i] <= xo) ? 1u : 0u;
-              e |= in && k4[i] == xo;
-            }
-          }
-        }
-      }
-      c += __shfl_xor_sync(kAll, c, 1);
-      c += __shfl_xor_sync(kAll, c, 2);
-      const unsigned found = __ballot_sync(kAll, e);
-      // lane L's probe was read in round L / 8 by group L % 8
-      const uint32_t mine = __shfl_sync(kAll, c, 4 * (lane & 7));
-      if ((lane >> 3) == s) {
-        le[p] = mine;
-        eq[p] = ((found >> (4 * (lane & 7))) & 0xFu) != 0;
-      }
-    }
-  }
-}
-
 // Bounded search on 4-key groups (same contract as search_last; R 32-byte
 // aligned): the window is widened to whole aligned groups of 4 keys, the
 // halving runs over the groups' first keys, and the last group is read with
@@ -472,8 +375,7 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
 
 // Lookups of NP keys already loaded (x, valid): root -> leaf record ->
 // window, then the interleaved bounded searches; cnt = number of matches,
-// r_idx = first matching position (when cnt > 0).  Called by all 32 lanes of
-// a warp together (the unique-key path reads the final windows as a warp).
+// r_idx = first matching position (when cnt > 0).
 template <class Model, int MODE, int NP>
 __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const uint64_t (&x)[NP],
                                             const bool (&valid)[NP], uint32_t (&r_idx)[NP],
@@ -520,16 +422,13 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
       r_idx[p] = lb[p];
     }
   } else {
-    // unique R: halve to a line-sized window, then read it with the warp
-    // (every lane of the warp takes part; invalid probes have empty windows)
-    narrow_window<NP>(P.R, x, base, len);
-    uint32_t le[NP];
-    bool eq[NP];
-    scan_windows<NP>(P.R, P.n, P.r32, x, base, len, le, eq);
+    uint64_t cv[NP];
+    search_last<NP, false>(P.R, x, base, len, cv);  // base = upper bound, len = start
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      cnt[p] = valid[p] && eq[p] ? 1u : 0u;
-      r_idx[p] = base[p] + le[p] - 1;   // the last key <= x: x itself on a match
+      const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
+      cnt[p] = match ? 1u : 0u;
+      r_idx[p] = base[p] - 1;
     }
   }
 }
