@@ -216,6 +216,8 @@ def _config(args, wl):
             "leaves": int(wl.leaves), "precision": wl.precision, "seed": args.seed,
             "index": {"rmi": "rmi", "grmi": f"grmi, {args.gaps} gaps per key",
                       "lhash": f"learned hash, {args.gaps} slots per distinct key",
+                      "rshash": f"RadixSpline hash (eps {args.rs_eps}, {args.rs_bits} radix "
+                                f"bits), {args.gaps} slots per distinct key",
                       "auto": "chosen by index_autotune"}[args.index],
             "probe_order": ["as given", "bucketed", "learned sort-merge"][args.probe_buckets],
             "l2": l2 + " (S = %.3f GB, R = %.3f GB)" % (wl.S.nbytes / 1e9, wl.R.nbytes / 1e9)}
@@ -584,9 +586,12 @@ def main():
     ap.add_argument("--leaves", type=int, default=None, help="override L (profiling runs)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"],
                     help="override the workload's model precision")
-    ap.add_argument("--index", default="rmi", choices=["rmi", "grmi", "lhash", "auto"],
+    ap.add_argument("--index", default="rmi", choices=["rmi", "grmi", "lhash", "rshash", "auto"],
                     help="rmi: bounded search in R; grmi: gapped RMI (exponential search); "
-                         "lhash: learned hash index; auto: index_autotune on 2^22 probes")
+                         "lhash: learned hash index; rshash: learned hash with a RadixSpline "
+                         "as the hash; auto: index_autotune on 2^22 probes")
+    ap.add_argument("--rs-eps", type=int, default=16, help="rshash: spline error bound")
+    ap.add_argument("--rs-bits", type=int, default=18, help="rshash: radix table bits")
     ap.add_argument("--gaps", type=int, default=4,
                     help="grmi: gaps per key; lhash: slots per distinct key")
     ap.add_argument("--dup-reading", default="clip", choices=["clip", "truncate"],
@@ -644,8 +649,10 @@ def main():
         choice, ns = lj.index_autotune(idx, Sd[: min(m, 1 << 22)])
         autotune = {"choice": choice, "ns_per_probe": ns, "sample": min(m, 1 << 22)}
     grmi = (lj.grmi_build(idx, args.gaps) if args.index == "grmi"
-            else lj.lhash_build(idx, args.gaps) if args.index == "lhash" else None)
-    if autotune and autotune["choice"] in ("grmi", "lhash"):
+            else lj.lhash_build(idx, args.gaps) if args.index == "lhash"
+            else lj.lhash_build_rs(idx, args.gaps, args.rs_eps, args.rs_bits)
+            if args.index == "rshash" else None)
+    if autotune and autotune["choice"] in ("grmi", "lhash", "rshash"):
         grmi = lj.grmi_stats(idx)
     stream = torch.cuda.current_stream()
 
@@ -739,6 +746,7 @@ def main():
         "probe_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
         "gapped_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,  # the same join, gapped index
         "hash_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
+        "rs_hash_search_kernel": 8 * m + 8 * n + 4 * m + (0 if unique else 4 * m),
         "scan_kernel": 4 * m + (8 * total if unique else 8 * (m + 1)),
         "probe_single_pass_kernel": 8 * m + 8 * n + 32 * L + 8 * total,
         "emit_kernel": 8 * m + 8 * n + 32 * L + 8 * (m + 1) + 8 * total,

@@ -205,8 +205,41 @@ int grmi_build(lj_index* index, uint32_t gaps, lj_stream_t stream);
  */
 int lhash_build(lj_index* index, uint32_t spk, lj_stream_t stream);
 
-/* first[D + 1] of a learned hash index (lhash_build) into host memory;
- * LJ_E_STATE without one.  Synchronises. */
+/*
+ * lhash_build_rs -- the learned hash index of lhash_build with a RadixSpline
+ * (Section 2.D) as the hash function instead of the RMI: the paper's
+ * RSHASH-INLJ (Section 3.C; Section 6.A picks a RadixSpline for it).
+ *   spk         slots per distinct key, 1 .. 16 (as lhash_build)
+ *   eps         error bound of the spline, in positions (0 .. 2^20)
+ *   radix_bits  bits of the radix table, 1 .. 24 (2^radix_bits + 1 entries)
+ * The RadixSpline is fitted to the CDF of R's distinct keys (each at the
+ * position of its first copy): spline points are chosen greedily in one pass
+ * so that every CDF point lies within eps positions of the line between the
+ * spline points around it (the pass restarts every 1024 distinct keys: one
+ * GPU thread per run; each run starts and ends with a spline point); the
+ * radix table indexes the spline points by the top radix_bits bits of
+ * (key - smallest key).  Prediction of x: 0 below the smallest key, n above
+ * the largest, else y_i + floor((x - x_i)(y_{i+1} - y_i) / (x_{i+1} - x_i))
+ * for the spline points around x (exact integer arithmetic); the hash is
+ * h(x) = pred(x) * B / (n + 1), and the table and its lookups are those of
+ * lhash_build.  The RMI of `index` is not used by its joins.  Synchronises.
+ * Errors: LJ_E_INVAL, LJ_E_NOMEM, LJ_E_CUDA.
+ */
+int lhash_build_rs(lj_index* index, uint32_t spk, uint32_t eps, uint32_t radix_bits,
+                   lj_stream_t stream);
+
+/*
+ * rs_export -- the RadixSpline of an lhash_build_rs index into host memory:
+ * sx_host[count] keys and sy_host[count] positions of the spline points,
+ * table_host[2^radix_bits + 1] (spline points with prefix below b), the
+ * prefix shift and the count.  Any pointer may be NULL.  LJ_E_STATE without
+ * a RadixSpline.  Synchronises.
+ */
+int rs_export(const lj_index* index, uint64_t* sx_host, uint32_t* sy_host, uint32_t* table_host,
+              uint32_t* shift_host, uint64_t* count_host);
+
+/* first[D + 1] of a learned hash index (lhash_build, lhash_build_rs) into
+ * host memory; LJ_E_STATE without one.  Synchronises. */
 int lhash_export_first(const lj_index* index, uint32_t* first_host);
 
 /* Release the gapped arrays (grmi_build or lhash_build); joins go back to
@@ -219,7 +252,9 @@ enum {
   LJ_LOOKUP_RMI_BUCKETED = 1,   /* bounded search in R, bucketed probe order */
   LJ_LOOKUP_GRMI = 2,           /* gapped RMI, 4 gaps per key (grmi_build) */
   LJ_LOOKUP_LHASH = 3,          /* learned hash index, 4 slots per key (lhash_build) */
-  LJ_LOOKUP_SORTMERGE = 4       /* bounded search in R, learned sort-merge order (Section 4) */
+  LJ_LOOKUP_SORTMERGE = 4,      /* bounded search in R, learned sort-merge order (Section 4) */
+  LJ_LOOKUP_RSHASH = 5          /* learned hash with a RadixSpline as the hash, 4 slots per key,
+                                   eps 16, 18 radix bits (lhash_build_rs) */
 };
 
 /*
@@ -232,7 +267,7 @@ enum {
  * "probe_buckets" option for this index).  The RMI itself is unchanged, so
  * results are the same whatever the choice (Sections 2.D, 3.A, 3.B, 3.C).
  *   choice       receives LJ_LOOKUP_*
- *   ns_per_key   optional: receives the five timings (ns per probe)
+ *   ns_per_key   optional: receives the six timings (ns per probe, by LJ_LOOKUP_*)
  * Synchronises.  Errors: those of grmi_build, lhash_build and join_count.
  */
 int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uint64_t m_sample,

@@ -80,6 +80,8 @@ SIGNATURES = {
     "rmi_export": ([_P, _P, _P, _P, _P], _I),
     "grmi_build": ([_P, _U32, _P], _I),
     "lhash_build": ([_P, _U32, _P], _I),
+    "lhash_build_rs": ([_P, _U32, _U32, _U32, _P], _I),
+    "rs_export": ([_P, _P, _P, _P, _P, _P], _I),
     "lhash_export_first": ([_P, _P], _I),
     "index_autotune": ([_P, _P, _U64, _P, _P, _P], _I),
     "grmi_drop": ([_P], _I),
@@ -260,11 +262,40 @@ def lhash_export_first(index: Index) -> np.ndarray:
     return first
 
 
-LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge")
+def lhash_build_rs(index: Index, spk: int = 4, eps: int = 16, radix_bits: int = 18,
+                   stream=None) -> dict:
+    """Attach a learned hash index whose hash is a RadixSpline (Section 2.D)
+    over R's distinct keys (the paper's RSHASH-INLJ, Section 3.C); joins on
+    the index then hash each probe through the spline.  Returns the table's
+    statistics."""
+    _check(load().lhash_build_rs(index.handle, spk, eps, radix_bits, _stream_ptr(stream)))
+    return grmi_stats(index)
+
+
+def rs_export(index: Index) -> dict:
+    """The RadixSpline of an lhash_build_rs index: spline keys and positions,
+    radix table and prefix shift."""
+    count, shift = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(load().rs_export(index.handle, None, None, None, ctypes.byref(shift),
+                            ctypes.byref(count)))
+    sx = np.zeros(count.value, dtype=np.uint64)
+    sy = np.zeros(count.value, dtype=np.uint32)
+    _check(load().rs_export(index.handle, _ptr(sx), _ptr(sy), None, None, None))
+    return {"sx": sx, "sy": sy, "shift": shift.value, "count": count.value}
+
+
+def rs_export_table(index: Index, radix_bits: int) -> np.ndarray:
+    """The radix table (2^radix_bits + 1 entries) of an lhash_build_rs index."""
+    table = np.zeros((1 << radix_bits) + 1, dtype=np.uint32)
+    _check(load().rs_export(index.handle, None, None, _ptr(table), None, None))
+    return table
+
+
+LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge", "rshash")
 
 
 def index_autotune(index: Index, S_sample, stream=None) -> tuple[str, dict]:
-    """Time the five lookup structures on a probe sample and keep the fastest;
+    """Time the six lookup structures on a probe sample and keep the fastest;
     returns its name and every candidate's ns per probe."""
     _require_cuda_u64(S_sample, "S_sample")
     choice = ctypes.c_int()

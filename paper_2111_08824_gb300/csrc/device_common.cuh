@@ -15,6 +15,11 @@
 namespace lj {
 
 
+// Kinds of gapped lookup structure (lj_index::gkind): gapped RMI (Section
+// 3.A), learned hash with the RMI as the hash, learned hash with a
+// RadixSpline as the hash (Section 3.C).
+enum { kGappedRmi = 0, kRmiHash = 1, kRsHash = 2 };
+
 // Error word bits (sticky, per device).
 constexpr uint32_t kErrLookbackTimeout = 1u;
 constexpr uint32_t kErrCapacity = 2u;
@@ -235,6 +240,69 @@ struct HashSlot {
   __device__ __forceinline__ uint64_t at(const typename Model::Leaf& lf, uint64_t x) const {
     return 4 * (clamped_pos<Model>(lf, x) * B / n1);
   }
+};
+
+// RadixSpline (Section 2.D) as used by the learned hash index (Section 3.C):
+// spline points (sx[i], sy[i]) over the CDF of R's distinct keys, a radix
+// table over the top bits of (key - sx[0]) of the spline points, and the
+// interpolated position of a key.  rcp[i] = 1 / (sx[i+1] - sx[i]) in double
+// only seeds the exact integer division.
+struct RsDev {
+  const uint64_t* sx;
+  const uint32_t* sy;
+  const double* rcp;
+  const uint32_t* table;   // 2^rbits + 1 entries: spline points with prefix below b
+  uint64_t kmin, kmax;     // sx[0], sx[S-1]
+  uint64_t n;              // |R|: the prediction above the largest key
+  uint32_t S;              // spline points
+  uint32_t shift;          // prefix = (x - kmin) >> shift
+};
+
+// floor(num / den) for num = a * b (a < 2^64, b < 2^32) and a < den: a
+// double-precision estimate corrected by exact 128-bit products.
+__device__ __forceinline__ uint64_t muldiv_floor(uint64_t a, uint32_t b, uint64_t den, double rcp) {
+  const unsigned __int128 num = (unsigned __int128)a * b;
+  const double est = ((double)(uint64_t)(num >> 64) * 18446744073709551616.0 +
+                      (double)(uint64_t)num) * rcp;
+  uint64_t q = est > 0.0 ? (uint64_t)est : 0;
+  if ((unsigned __int128)q * den > num) --q;                       // estimate one too high
+  else if ((unsigned __int128)(q + 1) * den <= num) ++q;           // or one too low
+  return q;
+}
+
+// Interpolated position of x: 0 below the smallest key, n above the largest,
+// else y_i + floor((x - x_i)(y_{i+1} - y_i) / (x_{i+1} - x_i)) between the
+// spline points around x (found through the radix table).
+__device__ __forceinline__ uint64_t rs_predict(const RsDev& rs, uint64_t x) {
+  if (rs.S == 0 || x < rs.kmin) return 0;
+  if (x > rs.kmax) return rs.n;
+  const uint32_t b = (uint32_t)((x - rs.kmin) >> rs.shift);
+  uint32_t lo = __ldg(rs.table + b), len = __ldg(rs.table + b + 1) - lo;
+  // count the spline points <= x among those with x's prefix
+  while (len > 0) {
+    const uint32_t half = len >> 1;
+    if (__ldg(reinterpret_cast<const unsigned long long*>(rs.sx) + lo + half) <= x) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
+  }
+  const uint32_t i = lo - 1;   // the last spline point <= x (exists: sx[0] = kmin <= x)
+  const uint64_t x0 = __ldg(reinterpret_cast<const unsigned long long*>(rs.sx) + i);
+  const uint32_t y0 = __ldg(rs.sy + i);
+  if (x == x0 || i + 1 == rs.S) return y0;
+  const uint64_t x1 = __ldg(reinterpret_cast<const unsigned long long*>(rs.sx) + i + 1);
+  const uint32_t y1 = __ldg(rs.sy + i + 1);
+  return y0 + muldiv_floor(x - x0, y1 - y0, x1 - x0, __ldg(rs.rcp + i));
+}
+
+// Learned hash with the RadixSpline as the hash: first slot 4 h(x),
+// h(x) = pred(x) * B / (n + 1).
+struct RsHashSlot {
+  RsDev rs;
+  uint64_t B, n1;
+  __device__ __forceinline__ uint64_t at(uint64_t x) const { return 4 * (rs_predict(rs, x) * B / n1); }
 };
 
 __device__ __forceinline__ uint64_t ldg_key(const uint64_t* R, uint32_t i) {

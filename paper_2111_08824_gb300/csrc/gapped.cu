@@ -50,6 +50,13 @@ __device__ __forceinline__ int64_t key_pslot(const typename Model::Leaf* leaves,
   return (int64_t)slot.template at<Model>(Model::load_leaf(leaves, m.leaf(x)), x);
 }
 
+// The RadixSpline hash needs no leaf record (no RMI lookup).
+template <class Model>
+__device__ __forceinline__ int64_t key_pslot(const typename Model::Leaf*, const Model&,
+                                             uint64_t x, const RsHashSlot& slot) {
+  return (int64_t)slot.at(x);
+}
+
 __device__ __forceinline__ int64_t warp_max(int64_t v) {
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) v = max(v, (int64_t)__shfl_xor_sync(0xffffffffu, v, d));
@@ -281,6 +288,101 @@ __global__ void grmi_tail_kernel(uint64_t* __restrict__ gkeys, uint32_t* __restr
   if (blockIdx.x == 0 && threadIdx.x == 0) gpos[C] = n;
 }
 
+// ------------------------------------------------------------ RadixSpline --
+//
+// RadixSpline over R's distinct keys (Section 2.D), the hash of the
+// RSHASH-INLJ learned hash index (Section 3.C).  CDF points: the distinct
+// keys dk[d] with the position of their first copy dfirst[d].  Spline points
+// are chosen greedily in one pass (the error corridor of Neumann and Michel,
+// 2008, as RadixSpline does): from the last spline point b every further
+// point q narrows a corridor of slopes to [q.y - eps, q.y + eps]; the first
+// point whose own slope from b leaves the corridor makes the point before it
+// a spline point.  Every CDF point then lies within eps positions of the line
+// between its spline points.  One GPU thread runs the pass over a chunk of
+// kRsChunk distinct keys (each chunk starts and ends with a spline point):
+// a counting launch, a scan of the counts, a writing launch.  Slopes are
+// compared exactly (128-bit cross products).  Then the radix table over the
+// top bits of (key - k_0) of the spline points, and 1 / (x_{i+1} - x_i) for
+// the interpolation.
+constexpr uint64_t kRsChunk = 1024;
+
+__device__ __forceinline__ bool slope_lt(__int128 a, __int128 b, __int128 c, __int128 d) {
+  return a * d < c * b;   // a/b < c/d for b, d > 0
+}
+
+template <bool WRITE>
+__global__ void rs_spline_kernel(const uint64_t* __restrict__ dk, const uint32_t* __restrict__ dy,
+                                 uint64_t D, uint32_t eps, int64_t* __restrict__ cnt,
+                                 const int64_t* __restrict__ off, uint64_t* __restrict__ sx,
+                                 uint32_t* __restrict__ sy) {
+  const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t c0 = c * kRsChunk;
+  if (c0 >= D) return;
+  const uint64_t c1 = min(D, c0 + kRsChunk);
+  uint64_t S = 0;
+  const uint64_t o = WRITE ? (uint64_t)off[c] : 0;
+  auto emit = [&](uint64_t d) {
+    if (WRITE) {
+      sx[o + S] = dk[d];
+      sy[o + S] = dy[d];
+    }
+    ++S;
+  };
+  uint64_t base = c0;
+  emit(base);
+  __int128 up_dy = 0, up_dx = 1, lo_dy = 0, lo_dx = 1;
+  bool open = false;
+  for (uint64_t d = c0 + 1; d < c1; ++d) {
+    const __int128 dx = (__int128)(dk[d] - dk[base]);
+    const __int128 y = (__int128)dy[d] - (__int128)dy[base];
+    if (!open) {
+      up_dy = y + eps;
+      up_dx = dx;
+      lo_dy = y - eps;
+      lo_dx = dx;
+      open = true;
+      continue;
+    }
+    if (slope_lt(up_dy, up_dx, y, dx) || slope_lt(y, dx, lo_dy, lo_dx)) {
+      base = d - 1;   // d leaves the corridor: the point before it is a spline point
+      emit(base);
+      const __int128 dx2 = (__int128)(dk[d] - dk[base]);
+      const __int128 y2 = (__int128)dy[d] - (__int128)dy[base];
+      up_dy = y2 + eps;
+      up_dx = dx2;
+      lo_dy = y2 - eps;
+      lo_dx = dx2;
+      continue;
+    }
+    if (slope_lt(y + eps, dx, up_dy, up_dx)) {
+      up_dy = y + eps;
+      up_dx = dx;
+    }
+    if (slope_lt(lo_dy, lo_dx, y - eps, dx)) {
+      lo_dy = y - eps;
+      lo_dx = dx;
+    }
+  }
+  if (c1 - 1 != base) emit(c1 - 1);
+  if (!WRITE) cnt[c] = (int64_t)S;
+}
+
+// Radix table (table[b] = spline points with prefix below b, b = 0..T) and
+// the reciprocal spline-segment widths.
+__global__ void rs_table_kernel(const uint64_t* __restrict__ sx, uint32_t S, uint64_t kmin,
+                                uint32_t shift, uint64_t T, uint32_t* __restrict__ table,
+                                double* __restrict__ rcp) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = (sx[i] - kmin) >> shift;
+    const int64_t pp = i ? (int64_t)((sx[i - 1] - kmin) >> shift) : -1;
+    for (int64_t b = pp + 1; b <= (int64_t)p; ++b) table[b] = (uint32_t)i;
+    if (i + 1 == S)
+      for (uint64_t b = p + 1; b <= T; ++b) table[b] = S;
+    rcp[i] = i + 1 < S ? 1.0 / (double)(sx[i + 1] - sx[i]) : 0.0;
+  }
+}
+
 // Model-based insertion of the n sorted keys src[] into the index's gapped
 // arrays, key i at max(slot(src[i]), slot of key i-1 + 1); payload = i.
 template <class Model, class Slot>
@@ -396,6 +498,16 @@ void grmi_release(lj_index* idx) {
   idx->gpos = nullptr;
   idx->dfirst = nullptr;
   idx->hrange = nullptr;
+  if (idx->rs_x) cudaFree(idx->rs_x);
+  if (idx->rs_y) cudaFree(idx->rs_y);
+  if (idx->rs_rcp) cudaFree(idx->rs_rcp);
+  if (idx->rs_table) cudaFree(idx->rs_table);
+  idx->rs_x = nullptr;
+  idx->rs_y = nullptr;
+  idx->rs_rcp = nullptr;
+  idx->rs_table = nullptr;
+  idx->rs_S = idx->rs_shift = idx->rs_rbits = idx->rs_eps = 0;
+  idx->rs_kmin = idx->rs_kmax = 0;
   idx->gslots = 0;
   idx->gscale = 0;
   idx->gkind = 0;
@@ -515,10 +627,160 @@ extern "C" int lhash_build(lj_index* index, uint32_t spk, lj_stream_t stream) {
   return LJ_OK;
 }
 
+namespace lj {
+namespace {
+
+// The RadixSpline of the index's distinct keys (dkey[D], index->dfirst) into
+// the index's rs_* arrays.
+int build_radix_spline(lj_index* idx, const uint64_t* dkey, uint64_t D, uint32_t eps,
+                       uint32_t rbits, cudaStream_t s) {
+  const uint64_t chunks = std::max<uint64_t>(1, (D + kRsChunk - 1) / kRsChunk);
+  const size_t b_c = (chunks * 8 + 255) / 256 * 256;
+  char* ws = nullptr;
+  LJ_CUDA(scratch_alloc((void**)&ws, 256 + 2 * b_c, s));
+  int64_t* total = (int64_t*)ws;
+  uint64_t* ends = (uint64_t*)(ws + 64);   // dkey[0], dkey[D-1]
+  int64_t* cnt = (int64_t*)(ws + 256);
+  int64_t* off = (int64_t*)(ws + 256 + b_c);
+  int64_t S = 0;
+  uint64_t hends[2] = {0, 0};
+  cudaError_t ce = cudaMemsetAsync(ws, 0, 256, s);
+  const unsigned g = (unsigned)((chunks + 127) / 128);
+  if (ce == cudaSuccess && D > 0) {
+    rs_spline_kernel<false><<<g, 128, 0, s>>>(dkey, idx->dfirst, D, eps, cnt, nullptr, nullptr,
+                                              nullptr);
+    grmi_prefix_kernel<true><<<1, 1024, 0, s>>>(cnt, (uint32_t)chunks, off, total);
+    ce = cudaMemcpyAsync(ends, dkey, 8, cudaMemcpyDeviceToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(ends + 1, dkey + D - 1, 8, cudaMemcpyDeviceToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&S, total, 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hends, ends, 16, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  }
+  const uint64_t T = 1ull << rbits;
+  uint32_t bl = 0;
+  for (uint64_t v = hends[1] - hends[0]; v; v >>= 1) ++bl;
+  const uint32_t shift = bl > rbits ? bl - rbits : 0;
+  if (ce == cudaSuccess) ce = cudaMalloc(&idx->rs_x, std::max<int64_t>(S, 1) * 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&idx->rs_y, std::max<int64_t>(S, 1) * 4);
+  if (ce == cudaSuccess) ce = cudaMalloc(&idx->rs_rcp, std::max<int64_t>(S, 1) * 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&idx->rs_table, (T + 1) * 4);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(idx->rs_table, 0, (T + 1) * 4, s);
+  if (ce == cudaSuccess && D > 0) {
+    rs_spline_kernel<true><<<g, 128, 0, s>>>(dkey, idx->dfirst, D, eps, nullptr, off, idx->rs_x,
+                                             idx->rs_y);
+    const unsigned gt = (unsigned)std::min<uint64_t>(4096, std::max<uint64_t>(1, (S + 255) / 256));
+    rs_table_kernel<<<gt, 256, 0, s>>>(idx->rs_x, (uint32_t)S, hends[0], shift, T, idx->rs_table,
+                                       idx->rs_rcp);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  scratch_free(ws, s);
+  if (ce != cudaSuccess) return fail_cuda(ce, "lhash_build_rs: RadixSpline");
+  idx->rs_S = (uint32_t)S;
+  idx->rs_shift = shift;
+  idx->rs_rbits = rbits;
+  idx->rs_eps = eps;
+  idx->rs_kmin = hends[0];
+  idx->rs_kmax = hends[1];
+  return 0;
+}
+
+}  // namespace
+}  // namespace lj
+
+extern "C" int lhash_build_rs(lj_index* index, uint32_t spk, uint32_t eps, uint32_t radix_bits,
+                              lj_stream_t stream) {
+  using namespace lj;
+  if (!index) return fail(LJ_E_INVAL, "lhash_build_rs: index is NULL");
+  if (spk < 1 || spk > 16) return fail(LJ_E_INVAL, "lhash_build_rs: spk = %u must be in [1, 16]", spk);
+  if (eps > (1u << 20)) return fail(LJ_E_INVAL, "lhash_build_rs: eps = %u above 2^20", eps);
+  if (radix_bits < 1 || radix_bits > 24)
+    return fail(LJ_E_INVAL, "lhash_build_rs: radix_bits = %u must be in [1, 24]", radix_bits);
+  if (current_device() != index->device)
+    return fail(LJ_E_INVAL, "lhash_build_rs: index lives on device %d, current device is %d",
+                index->device, current_device());
+  if ((uint64_t)spk * index->n + 8 >= 0xFFFFFFFFull)
+    return fail(LJ_E_INVAL, "lhash_build_rs: spk * n exceeds the 32-bit slot range");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(LJ_E_CUDA, "lhash_build_rs: cudaEventCreate failed");
+  cudaEventRecord(e0, s);
+  grmi_release(index);
+  uint64_t* dkey = nullptr;
+  uint64_t D = 0;
+  int rc = distinct_keys(index, &dkey, &D, s);
+  if (!rc) rc = build_radix_spline(index, dkey, D, eps, radix_bits, s);
+  if (!rc) {
+    const uint64_t B = std::max<uint64_t>(1, ((uint64_t)spk * D + 3) / 4);
+    const RsHashSlot slot{RsDev{index->rs_x, index->rs_y, index->rs_rcp, index->rs_table,
+                                index->rs_kmin, index->rs_kmax, index->n, index->rs_S,
+                                index->rs_shift},
+                          B, index->n + 1};
+    if (index->precision == LJ_FP64)
+      rc = build_gapped(index, ModelF64::make(index->root_f64[0], index->root_f64[1], index->L),
+                        slot, dkey, D, 4 * B, s);
+    else
+      rc = build_gapped(index, ModelF32::make(index->root_f32[0], index->root_f32[1], index->L),
+                        slot, dkey, D, 4 * B, s);
+    if (!rc) {   // per-slot ranges, as lhash_build
+      const uint64_t C = index->gslots;
+      cudaError_t ce = cudaMalloc(&index->hrange, std::max<uint64_t>(C, 1) * 8);
+      if (ce == cudaSuccess) {
+        const unsigned g = (unsigned)std::min<uint64_t>(8192, std::max<uint64_t>(1, (C + 255) / 256));
+        lhash_range_kernel<<<g, 256, 0, s>>>(index->gpos, index->dfirst, C, (uint32_t)D,
+                                              index->hrange);
+        ce = cudaGetLastError();
+      }
+      if (ce != cudaSuccess) rc = fail_cuda(ce, "lhash_build_rs: slot ranges");
+    }
+    if (!rc) {
+      index->gkind = kRsHash;
+      index->ndistinct = D;
+      index->hbuckets = B;
+      index->gstats.gaps = spk;
+      index->gstats.kind = 2;
+      index->gstats.distinct = D;
+    }
+  }
+  if (dkey) scratch_free(dkey, s);
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc) rc = take_device_errors(index->device, s);
+  if (rc) {
+    grmi_release(index);
+    return rc;
+  }
+  index->gstats.build_ms = ms;
+  return LJ_OK;
+}
+
+extern "C" int rs_export(const lj_index* index, uint64_t* sx_host, uint32_t* sy_host,
+                         uint32_t* table_host, uint32_t* shift_host, uint64_t* count_host) {
+  using namespace lj;
+  if (!index) return fail(LJ_E_INVAL, "rs_export: index is NULL");
+  if (index->gkind != kRsHash || !index->rs_table)
+    return fail(LJ_E_STATE, "rs_export: the index has no RadixSpline (lhash_build_rs)");
+  if (count_host) *count_host = index->rs_S;
+  if (shift_host) *shift_host = index->rs_shift;
+  if (sx_host && index->rs_S)
+    LJ_CUDA(cudaMemcpy(sx_host, index->rs_x, (size_t)index->rs_S * 8, cudaMemcpyDeviceToHost));
+  if (sy_host && index->rs_S)
+    LJ_CUDA(cudaMemcpy(sy_host, index->rs_y, (size_t)index->rs_S * 4, cudaMemcpyDeviceToHost));
+  if (table_host)
+    LJ_CUDA(cudaMemcpy(table_host, index->rs_table, ((1ull << index->rs_rbits) + 1) * 4,
+                       cudaMemcpyDeviceToHost));
+  return LJ_OK;
+}
+
 extern "C" int lhash_export_first(const lj_index* index, uint32_t* first_host) {
   using namespace lj;
   if (!index || !first_host) return fail(LJ_E_INVAL, "lhash_export_first: NULL argument");
-  if (index->gkind != 1 || !index->dfirst)
+  if ((index->gkind != 1 && index->gkind != 2) || !index->dfirst)
     return fail(LJ_E_STATE, "lhash_export_first: the index has no learned hash table");
   LJ_CUDA(cudaMemcpy(first_host, index->dfirst, (index->ndistinct + 1) * 4, cudaMemcpyDeviceToHost));
   return LJ_OK;
@@ -567,12 +829,13 @@ extern "C" int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uin
     index->probe_order = c == LJ_LOOKUP_RMI_BUCKETED ? 1 : c == LJ_LOOKUP_SORTMERGE ? 2 : 0;
     if (c == LJ_LOOKUP_GRMI) return grmi_build(index, 4, stream);
     if (c == LJ_LOOKUP_LHASH) return lhash_build(index, 4, stream);
+    if (c == LJ_LOOKUP_RSHASH) return lhash_build_rs(index, 4, 16, 18, stream);
     grmi_release(index);
     return 0;
   };
   double best = 1e300;
   int best_c = LJ_LOOKUP_RMI, rc = 0;
-  for (int c = LJ_LOOKUP_RMI; c <= LJ_LOOKUP_SORTMERGE && !rc; ++c) {
+  for (int c = LJ_LOOKUP_RMI; c <= LJ_LOOKUP_RSHASH && !rc; ++c) {
     if ((rc = setup(c))) break;
     float ms = 1e30f;
     for (int rep = 0; rep < 4 && !rc; ++rep) {

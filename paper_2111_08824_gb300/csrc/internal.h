@@ -29,11 +29,19 @@ struct lj_index {
   uint32_t* gpos = nullptr;
   uint32_t gslots = 0;           // C
   uint32_t gscale = 0;           // 1 + gaps (gapped RMI)
-  int gkind = 0;                 // 0: gapped RMI over R's keys, 1: learned hash over distinct keys
+  int gkind = 0;                 // 0: gapped RMI over R's keys, 1: learned hash over distinct
+                                 // keys (RMI as the hash), 2: the same with a RadixSpline
   uint32_t* dfirst = nullptr;    // learned hash: first position of each distinct key, D + 1
   uint64_t* hrange = nullptr;    // learned hash: per slot, first | count << 32 of its entry
   uint64_t ndistinct = 0;        // learned hash: D
   uint64_t hbuckets = 0;         // learned hash: B
+  // RadixSpline of the learned hash with a RadixSpline as the hash (gkind 2)
+  uint64_t* rs_x = nullptr;      // spline keys
+  uint32_t* rs_y = nullptr;      // spline positions
+  double* rs_rcp = nullptr;      // 1 / (x_{i+1} - x_i)
+  uint32_t* rs_table = nullptr;  // radix table, 2^rs_rbits + 1 entries
+  uint32_t rs_S = 0, rs_shift = 0, rs_rbits = 0, rs_eps = 0;
+  uint64_t rs_kmin = 0, rs_kmax = 0;
   lj_grmi_stats gstats{};
 };
 

@@ -153,15 +153,21 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(ProbeParams<Model> P) {
   uint64_t off = 0, end = 0;
   if (j < P.m) {
     const uint64_t key = __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j);
-    const typename Model::Leaf lf = Model::load_leaf(P.leaves, P.model.leaf(key));
     uint64_t xk[1] = {key};
-    if constexpr (GAP != 0) {
-      uint32_t q[1] = {gapped_start<Model, GAP == 2>(P, lf, key)};
+    if constexpr (GAP == 3) {                       // RadixSpline hash: no leaf record
+      uint32_t q[1] = {gapped_start<Model, kRsHash>(P, typename Model::Leaf{}, key)};
+      uint64_t v[1];
+      gallop_first<1, false>(P.gkeys, P.gslots, xk, q, v);
+      lb = __ldg(P.dfirst + __ldg(P.gpos + q[0]));  // the distinct-key rank's first position
+    } else if constexpr (GAP != 0) {
+      const typename Model::Leaf lf = Model::load_leaf(P.leaves, P.model.leaf(key));
+      uint32_t q[1] = {gapped_start<Model, GAP == 2 ? kRmiHash : kGappedRmi>(P, lf, key)};
       uint64_t v[1];
       gallop_first<1, false>(P.gkeys, P.gslots, xk, q, v);
       lb = __ldg(P.gpos + q[0]);                    // GAP 2: the distinct-key rank
       if (GAP == 2) lb = __ldg(P.dfirst + lb);      // (rank D: dfirst[D] = n, unused)
     } else {
+      const typename Model::Leaf lf = Model::load_leaf(P.leaves, P.model.leaf(key));
       uint32_t wl, wh;
       window<Model>(lf, key, wl, wh);
       uint32_t b[1] = {wl}, l[1] = {wh - wl};
@@ -307,7 +313,7 @@ __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32
     uint32_t r_idx[2], cnt[2];
     bool valid[2];
     if constexpr (GAP != 0)
-      lookup_gapped<Model, MODE, VEC, GAP == 2>(P, j0, r_idx, cnt, valid);
+      lookup_gapped<Model, MODE, VEC, GAP - 1>(P, j0, r_idx, cnt, valid);
     else
       lookup_probes<Model, MODE, 1, VEC>(P, j0, 0, r_idx, cnt, valid);
     uint32_t w0, w1;
@@ -369,6 +375,14 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     hash_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
                        unsigned long long* __restrict__ tile_counts) {
   search_chunk<Model, MODE, CHUNK, VEC, 2>(P, out, tile_counts);
+}
+
+// The same with the RadixSpline as the hash (the paper's RSHASH-INLJ).
+template <class Model, int MODE, int CHUNK, bool VEC>
+__global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
+    rs_hash_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
+                          unsigned long long* __restrict__ tile_counts) {
+  search_chunk<Model, MODE, CHUNK, VEC, 3>(P, out, tile_counts);
 }
 
 // ---------------------------------------------------------------------------
@@ -820,6 +834,8 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.ndistinct = (uint32_t)idx->ndistinct;
   P.hB = idx->hbuckets;
   P.hn1 = idx->n + 1;
+  P.rs = RsDev{idx->rs_x, idx->rs_y, idx->rs_rcp, idx->rs_table, idx->rs_kmin, idx->rs_kmax,
+               idx->n, idx->rs_S, idx->rs_shift};
   return P;
 }
 
@@ -1004,16 +1020,23 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
       return rc;
     }
   } else {
-    KernelTimer kt(!P.gkeys ? "probe_search_kernel"
-                   : idx->gkind == 1 ? "hash_search_kernel" : "gapped_search_kernel", s);
+    KernelTimer kt(!P.gkeys                  ? "probe_search_kernel"
+                   : idx->gkind == kRmiHash ? "hash_search_kernel"
+                   : idx->gkind == kRsHash  ? "rs_hash_search_kernel"
+                                            : "gapped_search_kernel", s);
 #define LJ_SEARCH(KERNEL, MODE)                                                              \
   (vec ? KERNEL<Model, MODE, kSearchChunk, true><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts) \
        : KERNEL<Model, MODE, kSearchChunk, false><<<grid, kSearchBlock, 0, s>>>(P, words, tile_counts))
-    if (P.gkeys && idx->gkind == 1) {
+    if (P.gkeys && idx->gkind == kRmiHash) {
       if (dup)
         LJ_SEARCH(hash_search_kernel, kDupCount);
       else
         LJ_SEARCH(hash_search_kernel, kUniqueCount);
+    } else if (P.gkeys && idx->gkind == kRsHash) {
+      if (dup)
+        LJ_SEARCH(rs_hash_search_kernel, kDupCount);
+      else
+        LJ_SEARCH(rs_hash_search_kernel, kUniqueCount);
     } else if (P.gkeys) {
       if (dup)
         LJ_SEARCH(gapped_search_kernel, kDupCount);
@@ -1115,7 +1138,9 @@ int launch_emit(const lj_index* idx, Model model, const uint64_t* S, uint64_t m,
   const uint64_t blocks = (m + kBlock - 1) / kBlock;
   {
     KernelTimer kt("emit_kernel", s);
-    if (P.gkeys && idx->gkind == 1)
+    if (P.gkeys && idx->gkind == kRsHash)
+      emit_kernel<Model, 3><<<(unsigned)blocks, kBlock, 0, s>>>(P);
+    else if (P.gkeys && idx->gkind == kRmiHash)
       emit_kernel<Model, 2><<<(unsigned)blocks, kBlock, 0, s>>>(P);
     else if (P.gkeys)
       emit_kernel<Model, 1><<<(unsigned)blocks, kBlock, 0, s>>>(P);

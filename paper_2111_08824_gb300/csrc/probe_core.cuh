@@ -51,6 +51,7 @@ struct ProbeParams {
   uint32_t ndistinct;     // D
   uint64_t hB;            // buckets
   uint64_t hn1;           // n + 1
+  RsDev rs;               // RadixSpline of the learned hash over it (kind kRsHash)
 };
 
 // Tunables (fixed at compile time; the defaults are the measured best).
@@ -297,12 +298,14 @@ __device__ __forceinline__ void gallop_first(const uint64_t* __restrict__ K, uin
 }
 
 // Predicted slot of x, at most C: the gapped RMI's, or the first slot of
-// x's bucket in the learned hash table (HASH).
-template <class Model, bool HASH = false>
+// x's bucket in the learned hash table (RMI or RadixSpline as the hash).
+// The leaf record is not used by the RadixSpline hash.
+template <class Model, int KIND = kGappedRmi>
 __device__ __forceinline__ uint32_t gapped_start(const ProbeParams<Model>& P,
                                                  const typename Model::Leaf& lf, uint64_t x) {
-  const uint64_t q = HASH ? HashSlot{P.hB, P.hn1}.template at<Model>(lf, x)
-                          : gapped_pslot<Model>(lf, x, P.gscale);
+  const uint64_t q = KIND == kRsHash    ? RsHashSlot{P.rs, P.hB, P.hn1}.at(x)
+                     : KIND == kRmiHash ? HashSlot{P.hB, P.hn1}.template at<Model>(lf, x)
+                                        : gapped_pslot<Model>(lf, x, P.gscale);
   return q < P.gslots ? (uint32_t)q : P.gslots;
 }
 
@@ -311,7 +314,7 @@ __device__ __forceinline__ uint32_t gapped_start(const ProbeParams<Model>& P,
 // >= x; its payload is the lower bound of x in R.  With duplicates a second
 // search from there finds the first key > x, and cnt is the difference of
 // the two payloads.
-template <class Model, int MODE, bool VEC, bool HASH = false>
+template <class Model, int MODE, bool VEC, int KIND = kGappedRmi>
 __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint64_t j0,
                                               uint32_t (&r_idx)[2], uint32_t (&cnt)[2],
                                               bool (&valid)[2]) {
@@ -331,15 +334,19 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     pos[p] = P.gslots;
-    if (valid[p])
-      pos[p] = gapped_start<Model, HASH>(P, Model::load_leaf(P.leaves, P.model.leaf(x[p])), x[p]);
+    if (valid[p]) {
+      if (KIND == kRsHash)   // the RadixSpline needs no leaf record
+        pos[p] = gapped_start<Model, KIND>(P, typename Model::Leaf{}, x[p]);
+      else
+        pos[p] = gapped_start<Model, KIND>(P, Model::load_leaf(P.leaves, P.model.leaf(x[p])), x[p]);
+    }
   }
   uint64_t val[2];
   gallop_first<2, false>(P.gkeys, P.gslots, x, pos, val);
   bool hit[2];
 #pragma unroll
   for (int p = 0; p < 2; ++p) hit[p] = valid[p] && pos[p] < P.gslots && val[p] == x[p];
-  if (HASH) {
+  if (KIND != kGappedRmi) {
     // one 8-byte load gives the slot's whole range of matches (the copies
     // after the last key carry count 0: no match)
 #pragma unroll

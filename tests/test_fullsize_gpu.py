@@ -16,8 +16,9 @@ on every host core).
                     join_emit, is checked on the device against the oracle's
                     ranges: the pair at output position q is (lo_s + q -
                     off_s, s) for the one probe s with off_s <= q < off_s+1.
-  gapped RMI and learned hash at full size: their arrays equal the oracle's,
-                    and their joins give the oracle's ranges for every probe.
+  gapped RMI, learned hash and RadixSpline hash at full size: their arrays
+                    equal the oracle's, and their joins give the oracle's
+                    ranges for every probe.
 """
 import numpy as np
 import pytest
@@ -254,3 +255,37 @@ def test_dup_seqh_50m_learned_hash_full(dup):
     pairs = torch.empty((total, 2), dtype=torch.int32, device="cuda")
     assert lj.join_expand(first, offsets, pairs) == total
     _pairs_equal_ranges_on_device(pairs, total, lo, off_o)
+
+
+def test_dup_seqh_50m_rs_hash_full(dup):
+    """RadixSpline hash index (RSHASH-INLJ, eps 16, 18 radix bits, 4 slots per
+    distinct key) on the duplicate workload: spline, radix table and hash
+    table equal the oracle's; the located range of every probe and every
+    emitted pair equal the oracle's."""
+    lj = _lj()
+    w, Rd, Sd = dup.w, dup.Rd, dup.Sd
+    m = w.S.size
+    idx = lj.rmi_build(Rd, w.leaves, w.precision)
+    lj.lhash_build_rs(idx, 4, 16, 18)
+    rs = oracle.rs_build(w.R, eps=16, chunk=1024, rbits=18)
+    got = lj.rs_export(idx)
+    assert np.array_equal(got["sx"], rs.sx) and np.array_equal(got["sy"], rs.sy)
+    assert np.array_equal(lj.rs_export_table(idx, 18), rs.table)
+    want = oracle.rs_lhash_build(w.R, rs, 4)
+    keys, pos = lj.grmi_export(idx)
+    assert np.array_equal(keys, want.keys) and np.array_equal(pos, want.pos)
+    del keys, pos, want
+    lo, hi, total_o = dup.ranges()
+    cnt_o = (hi - lo).astype(np.int64)
+    off_o = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(cnt_o, out=off_o[1:])
+    first = torch.empty(m, dtype=torch.int32, device="cuda")
+    counts = torch.empty(m, dtype=torch.int32, device="cuda")
+    offsets = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    assert lj.join_locate(idx, Sd, first, counts=counts, offsets=offsets) == total_o
+    hit = cnt_o > 0
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), cnt_o)
+    assert np.array_equal(first.cpu().numpy().view(np.uint32)[hit], lo[hit].astype(np.uint32))
+    pairs = torch.empty((total_o, 2), dtype=torch.int32, device="cuda")
+    assert lj.join_expand(first, offsets, pairs) == total_o
+    _pairs_equal_ranges_on_device(pairs, total_o, lo, off_o)
