@@ -396,6 +396,32 @@ int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
               lj_pair* pairs_host, uint64_t capacity, uint64_t* written_host,
               lj_stream_t stream);
 
+/* ------------------------------------------------ learned sort-merge ---- */
+
+/*
+ * lsj_join -- learned sort-merge join (L-SJ, Section 4) of two UNSORTED
+ * relations: J = { (i, j) : R[i] == S[j] }, i and j positions in R and S as
+ * given (no index, no sorted input).
+ *   model      per relation, a CDF model (the RMI of rmi_build) fitted over
+ *              an evenly spaced sample of at most 16,384 keys, sorted on the
+ *              device (Section 4.B);
+ *   partition  both relations range-partitioned with their model into
+ *              partitions of about 2048 keys (histogram, scan, scatter);
+ *   sort       each partition sorted on its own by (key, position) in
+ *              shared memory (Section 4.C); the relations are then sorted;
+ *   join       R's partitions in chunks of up to 4096 keys, each merged with
+ *              the partitions of S its first and last keys map to under S's
+ *              model (Section 4.D).
+ *   pairs_dev, capacity   output (device); pairs beyond capacity are not written
+ *   written_host          |J| (optional)
+ * Pairs are grouped by R chunk (R's key order), then in S's (key, position)
+ * order, then R's; the same for the same input.  Work memory: about 36
+ * bytes per key of R and S (stream-ordered pool).  Synchronises.
+ * Errors: LJ_E_INVAL, LJ_E_NOMEM, LJ_E_CUDA, LJ_E_CAPACITY.
+ */
+int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev, uint64_t m,
+             lj_pair* pairs_dev, uint64_t capacity, uint64_t* written_host, lj_stream_t stream);
+
 /* ----------------------------------------------------------- batches ---- */
 
 typedef struct lj_batch lj_batch;      /* opaque batch plan, owned by the library */

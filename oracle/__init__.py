@@ -28,6 +28,9 @@ Learned In-Memory Joins"):
                              prefixes, interpolation between spline points)
   rs_lhash_build / _join     Section 3.C with a RadixSpline as the hash
                              (the paper's RSHASH-INLJ)
+  join_pairs_unsorted        Section 4 (sort-based join of two unsorted
+                             relations): J = {(i, j) : R[i] == S[j]} with i, j
+                             positions in the relations as given
 """
 from __future__ import annotations
 
@@ -438,3 +441,23 @@ def rs_lhash_join(R, h: RSHash, S) -> tuple[np.ndarray, np.ndarray, int]:
         _ptr(R), R.size, _ptr(rs.sx), _ptr(rs.sy), rs.sx.size, h.B, _ptr(h.keys), _ptr(h.pos),
         h.keys.size, _ptr(h.first), h.D, _ptr(S), S.size, _ptr(lo), _ptr(hi))
     return lo, hi, int(total)
+
+
+def join_pairs_unsorted(R, S) -> np.ndarray:
+    """The join of two unsorted relations (Section 4's learned sort-merge join
+    computes it): all (i, j) with R[i] == S[j], i and j positions in R and S
+    as given, ordered by j then i, as (k, 2) uint32.  R is sorted with its
+    positions (numpy's stable sort: equal keys keep their order), then the
+    sort-merge join above gives each probe's run of R."""
+    R, S = _u64(R), _u64(S)
+    perm = np.argsort(R, kind="stable")
+    lo, hi, total = join_ranges(R[perm], S)
+    out = np.zeros((total, 2), dtype=np.uint32)
+    cnt = (hi - lo).astype(np.int64)
+    j = np.repeat(np.arange(S.size, dtype=np.int64), cnt)
+    first = np.repeat(lo.astype(np.int64), cnt)
+    start = np.repeat(np.cumsum(cnt) - cnt, cnt)
+    r_sorted = first + (np.arange(total, dtype=np.int64) - start)
+    out[:, 0] = perm[r_sorted]
+    out[:, 1] = j
+    return out

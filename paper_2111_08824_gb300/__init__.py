@@ -11,7 +11,7 @@ use; there is no CPU fallback.
 from ._native import (LJ_FP32, LJ_FP64, BatchPlan, Index, LJoinError, Server, grmi_build,
                       grmi_drop, grmi_export, grmi_stats, join_batch, join_expand,
                       join_locate, lhash_build, lhash_build_rs, lhash_export_first, index_autotune,
-                      join_batch_plan, join_count, join_count_noalloc, join_emit, join_host,
+                      join_batch_plan, join_count, join_count_noalloc, join_emit, join_host, lsj_join,
                       rmi_autotune, rmi_autotune_clear,
                       library_path, lj_get_option, lj_last_error, lj_profile_report,
                       lj_set_option,
@@ -22,6 +22,7 @@ __all__ = ["LJ_FP32", "LJ_FP64", "BatchPlan", "Index", "LJoinError", "Server", "
            "grmi_drop", "grmi_export", "grmi_stats", "join_batch", "join_expand",
            "join_locate", "lhash_build", "lhash_build_rs", "lhash_export_first", "index_autotune",
            "join_batch_plan", "join_count", "join_count_noalloc", "join_emit", "join_host",
+           "lsj_join",
            "rmi_autotune", "rmi_autotune_clear",
            "library_path", "lj_get_option", "lj_last_error", "lj_profile_report",
            "lj_set_option", "lj_version", "load", "rmi_build", "rmi_build_batch", "rmi_export",

@@ -82,6 +82,7 @@ SIGNATURES = {
     "lhash_build": ([_P, _U32, _P], _I),
     "lhash_build_rs": ([_P, _U32, _U32, _U32, _P], _I),
     "rs_export": ([_P, _P, _P, _P, _P, _P], _I),
+    "lsj_join": ([_P, _U64, _P, _U64, _P, _U64, _P, _P], _I),
     "lhash_export_first": ([_P, _P], _I),
     "index_autotune": ([_P, _P, _U64, _P, _P, _P], _I),
     "grmi_drop": ([_P], _I),
@@ -289,6 +290,18 @@ def rs_export_table(index: Index, radix_bits: int) -> np.ndarray:
     table = np.zeros((1 << radix_bits) + 1, dtype=np.uint32)
     _check(load().rs_export(index.handle, None, None, _ptr(table), None, None))
     return table
+
+
+def lsj_join(R, S, pairs, stream=None) -> int:
+    """Learned sort-merge join (Section 4) of two unsorted device tensors of
+    uint64 keys into `pairs` (int32 tensor (cap, 2)); returns |J|."""
+    _require_cuda_u64(R, "R")
+    _require_cuda_u64(S, "S")
+    total = ctypes.c_uint64()
+    cap = pairs.shape[0] if pairs is not None else 0
+    _check(load().lsj_join(_ptr(R), R.numel(), _ptr(S), S.numel(), _ptr(pairs), cap,
+                           ctypes.byref(total), _stream_ptr(stream)))
+    return total.value
 
 
 LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge", "rshash")

@@ -1,0 +1,513 @@
+// Learned sort-merge join (L-SJ, Section 4 of Sabek and Kraska, "The Case
+// for Learned In-Memory Joins") of two unsorted relations on the GPU.
+//
+//   model      (Section 4.B, model building) per relation, a sample of up
+//              to kSample keys at evenly spaced positions, sorted in shared
+//              memory by one block, and the two-level linear RMI of this
+//              library fitted over the sorted sample (rmi_build): a CDF
+//              model.  part(x) = min(P - 1, p(x) * P / s), p(x) the model's
+//              predicted position clamped to its leaf (monotone), s the
+//              sample size, P the number of partitions (one per kPartKeys
+//              keys on average).
+//   partition  (Section 4.B, range partitioning) each key's partition
+//              (histogram with warp-aggregated atomics), a scan, and a
+//              scatter of (key, position) into partition order.  The model
+//              is monotone, so the partitions are key ranges in order.
+//   sort       (Section 4.C) every partition sorted on its own, by (key,
+//              position): one block per partition, a bitonic network in
+//              shared memory (up to kSortCap entries; larger partitions,
+//              e.g. many copies of one key, in global memory).  After this
+//              the relation is globally sorted.
+//   join       (Section 4.D, chunked join) R's sorted partitions are cut
+//              into chunks of at most kJoinChunk keys; S's model, queried
+//              with a chunk's first and last key, gives the overlapping
+//              partitions of S; each S key of them is looked up in the chunk
+//              (staged in shared memory): a count pass, a scan of the counts
+//              per chunk, a write pass.
+// Output: the pairs (i, j) with R[i] == S[j], i and j positions in the
+// relations as given, grouped by R chunk, then in S's sorted order, then in
+// R's sorted order (deterministic).
+//
+// Differences from the paper's CPU design: the sample is evenly spaced and
+// at most 16,384 keys (one block sorts it in shared memory); the partitions
+// are sized for a thread block's shared memory rather than for TLB entries;
+// the per-partition sort is a bitonic network in shared memory rather than
+// AVX registers; no software write-combine buffers (the scatter goes
+// through L2).
+#include <algorithm>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace lj {
+namespace {
+
+constexpr uint32_t kSample = 16384;      // largest sample per relation
+constexpr uint32_t kPartKeys = 2048;     // keys per partition on average
+constexpr uint32_t kSortCap = 8192;      // largest partition sorted in shared memory
+constexpr uint32_t kJoinChunk = 4096;    // R keys per join work item
+constexpr int kLBlock = 256;
+
+__device__ __forceinline__ bool kv_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+
+// Ascending sort of (k[i], v[i]), i < cnt, by (key, value): a bitonic
+// network whose merges begin with the mirrored comparison, so every
+// comparison sends the smaller entry to the lower index and the virtual
+// entries past cnt (+infinity) never move.  Called by the whole block.
+__device__ void bitonic_kv(uint64_t* k, uint32_t* v, uint32_t cnt) {
+  uint32_t N = 1;
+  while (N < cnt) N <<= 1;
+  for (uint32_t size = 2; size <= N; size <<= 1) {
+    const uint32_t half = size >> 1;
+    for (uint32_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+      const uint32_t blk = i / half, off = i % half;
+      const uint32_t lo = blk * size + off, hi = blk * size + size - 1 - off;
+      if (hi < cnt && kv_less(k[hi], v[hi], k[lo], v[lo])) {
+        const uint64_t tk = k[lo];
+        k[lo] = k[hi];
+        k[hi] = tk;
+        const uint32_t tv = v[lo];
+        v[lo] = v[hi];
+        v[hi] = tv;
+      }
+    }
+    __syncthreads();
+    for (uint32_t stride = half >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+        const uint32_t lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+        if (hi < cnt && kv_less(k[hi], v[hi], k[lo], v[lo])) {
+          const uint64_t tk = k[lo];
+          k[lo] = k[hi];
+          k[hi] = tk;
+          const uint32_t tv = v[lo];
+          v[lo] = v[hi];
+          v[hi] = tv;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Evenly spaced sample of s keys (position floor((2t + 1) n / (2s))),
+// sorted in shared memory by one block.
+__global__ void __launch_bounds__(1024) lsj_sample_kernel(const uint64_t* __restrict__ X,
+                                                          uint64_t n, uint32_t s,
+                                                          uint64_t* __restrict__ out) {
+  extern __shared__ uint64_t sk[];
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kSample);
+  for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) {
+    sk[t] = X[((2 * (uint64_t)t + 1) * n) / (2 * (uint64_t)s)];
+    sv[t] = t;
+  }
+  __syncthreads();
+  bitonic_kv(sk, sv, s);
+  for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) out[t] = sk[t];
+}
+
+template <class Model>
+__device__ __forceinline__ uint32_t part_of(const Model& m, const typename Model::Leaf* leaves,
+                                            uint64_t x, uint32_t s, uint32_t P) {
+  const uint64_t p = clamped_pos<Model>(Model::load_leaf(leaves, m.leaf(x)), x);   // 0 .. s
+  const uint64_t q = p * P / s;
+  return q < P ? (uint32_t)q : P - 1;
+}
+
+// Partition of every key and the partition sizes.
+template <class Model>
+__global__ void __launch_bounds__(kLBlock)
+    lsj_hist_kernel(const uint64_t* __restrict__ X, uint64_t n, Model m,
+                    const typename Model::Leaf* leaves, uint32_t s, uint32_t P,
+                    uint32_t* __restrict__ pid, unsigned long long* __restrict__ cnt) {
+  const uint64_t i = (uint64_t)blockIdx.x * kLBlock + threadIdx.x;
+  const bool valid = i < n;
+  const uint32_t p = valid ? part_of(m, leaves, __ldg(reinterpret_cast<const unsigned long long*>(X) + i), s, P) : 0;
+  const unsigned mask = __ballot_sync(0xffffffffu, valid);
+  if (valid) {
+    pid[i] = p;
+    const unsigned grp = __match_any_sync(mask, p);
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(cnt + p, (unsigned long long)__popc(grp));
+  }
+}
+
+// Exclusive scan of cnt[0..P) into off[0..P] (off[P] = total), one block.
+__global__ void __launch_bounds__(1024) lsj_scan_kernel(const unsigned long long* __restrict__ cnt,
+                                                        uint32_t P, uint64_t* __restrict__ off) {
+  __shared__ uint64_t s[1024];
+  const uint32_t per = (P + 1023) / 1024;
+  const uint32_t b = threadIdx.x * per, e = min(P, b + per);
+  uint64_t sum = 0;
+  for (uint32_t t = b; t < e; ++t) sum += cnt[t];
+  s[threadIdx.x] = sum;
+  __syncthreads();
+  for (uint32_t d = 1; d < 1024; d <<= 1) {
+    const uint64_t v = threadIdx.x >= d ? s[threadIdx.x - d] : 0;
+    __syncthreads();
+    s[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint64_t run = threadIdx.x ? s[threadIdx.x - 1] : 0;
+  for (uint32_t t = b; t < e; ++t) {
+    off[t] = run;
+    run += cnt[t];
+  }
+  if (threadIdx.x == 1023) off[P] = s[1023];
+}
+
+// (key, position) into its partition's next free slot.
+__global__ void __launch_bounds__(kLBlock)
+    lsj_scatter_kernel(const uint64_t* __restrict__ X, uint64_t n, const uint32_t* __restrict__ pid,
+                       const uint64_t* __restrict__ off, unsigned long long* __restrict__ cursor,
+                       uint64_t* __restrict__ keys, uint32_t* __restrict__ pos) {
+  const uint64_t i = (uint64_t)blockIdx.x * kLBlock + threadIdx.x;
+  const bool valid = i < n;
+  const uint32_t p = valid ? pid[i] : 0;
+  const unsigned mask = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
+  const unsigned grp = __match_any_sync(mask, p);
+  const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(cursor + p, (unsigned long long)__popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  const uint64_t at = off[p] + base + __popc(grp & ((1u << lane) - 1u));
+  keys[at] = X[i];
+  pos[at] = (uint32_t)i;
+}
+
+// One block per partition: sort it by (key, position).
+__global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ keys,
+                                                       uint32_t* __restrict__ pos,
+                                                       const uint64_t* __restrict__ off) {
+  extern __shared__ uint64_t sk[];
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kSortCap);
+  const uint64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+  const uint64_t cnt = b - a;
+  if (cnt <= 1) return;
+  if (cnt <= kSortCap) {
+    for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+      sk[t] = keys[a + t];
+      sv[t] = pos[a + t];
+    }
+    __syncthreads();
+    bitonic_kv(sk, sv, (uint32_t)cnt);
+    for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+      keys[a + t] = sk[t];
+      pos[a + t] = sv[t];
+    }
+  } else {
+    bitonic_kv(keys + a, pos + a, (uint32_t)cnt);   // large partition: in global memory
+  }
+}
+
+// Join work item: R's sorted positions [ra, ra + len) (len <= kJoinChunk, in
+// one partition) and the overlapping range [sa, sb) of S's sorted keys.
+struct JoinItem {
+  uint64_t ra, sa, sb;
+  uint32_t len, pad;
+};
+
+// Items of R's partitions (chunks of kJoinChunk keys) with their S ranges.
+template <class Model>
+__global__ void lsj_items_kernel(const uint64_t* __restrict__ rkeys, const uint64_t* __restrict__ roff,
+                                 uint32_t PR, const uint64_t* __restrict__ item0, Model ms,
+                                 const typename Model::Leaf* sleaves, uint32_t ss, uint32_t PS,
+                                 const uint64_t* __restrict__ soff, JoinItem* __restrict__ items) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < PR; p += gridDim.x * blockDim.x) {
+    const uint64_t a = roff[p], b = roff[p + 1];
+    uint64_t it = item0[p];
+    for (uint64_t c = a; c < b; c += kJoinChunk, ++it) {
+      const uint64_t e = min(b, c + kJoinChunk);
+      JoinItem J;
+      J.ra = c;
+      J.len = (uint32_t)(e - c);
+      J.pad = 0;
+      const uint32_t f = part_of(ms, sleaves, rkeys[c], ss, PS);
+      const uint32_t l = part_of(ms, sleaves, rkeys[e - 1], ss, PS);
+      J.sa = soff[f];
+      J.sb = soff[l + 1];
+      items[it] = J;
+    }
+  }
+}
+
+// Count pass (WRITE = false: per-item match counts) and write pass (WRITE:
+// the pairs at the item's offset).  Block per item; the item's R keys are
+// staged in shared memory and every S key of the range is bounded in them.
+template <bool WRITE>
+__global__ void __launch_bounds__(kLBlock)
+    lsj_join_kernel(const JoinItem* __restrict__ items, const uint64_t* __restrict__ rkeys,
+                    const uint32_t* __restrict__ rpos, const uint64_t* __restrict__ skeys,
+                    const uint32_t* __restrict__ spos, unsigned long long* __restrict__ count,
+                    const uint64_t* __restrict__ ioff, lj_pair* __restrict__ pairs,
+                    uint64_t capacity) {
+  __shared__ uint64_t sr[kJoinChunk];
+  __shared__ uint32_t sw[kLBlock / 32];
+  __shared__ uint64_t s_run;
+  const JoinItem J = items[blockIdx.x];
+  for (uint32_t t = threadIdx.x; t < J.len; t += kLBlock) sr[t] = rkeys[J.ra + t];
+  if (threadIdx.x == 0) s_run = WRITE ? ioff[blockIdx.x] : 0;
+  __syncthreads();
+  const uint64_t lo_key = sr[0], hi_key = sr[J.len - 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long total = 0;
+  for (uint64_t base = J.sa; base < J.sb; base += kLBlock) {
+    const uint64_t q = base + threadIdx.x;
+    uint32_t lb = 0, c = 0;
+    if (q < J.sb) {
+      const uint64_t x = skeys[q];
+      if (x >= lo_key && x <= hi_key) {
+        uint32_t a = 0, len = J.len;   // lower bound of x in the chunk
+        while (len > 0) {
+          const uint32_t h = len >> 1;
+          if (sr[a + h] < x) {
+            a += h + 1;
+            len -= h + 1;
+          } else {
+            len = h;
+          }
+        }
+        uint32_t u = a;
+        len = J.len - a;               // upper bound
+        while (len > 0) {
+          const uint32_t h = len >> 1;
+          if (sr[u + h] <= x) {
+            u += h + 1;
+            len -= h + 1;
+          } else {
+            len = h;
+          }
+        }
+        lb = a;
+        c = u - a;
+      }
+    }
+    if (!WRITE) {
+      total += c;
+      continue;
+    }
+    // block exclusive scan of c: the round's output positions
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += v;
+    }
+    if (lane == 31) sw[warp] = inc;
+    __syncthreads();
+    uint64_t at = s_run + inc - c;
+    uint32_t round = 0;
+    for (int w = 0; w < kLBlock / 32; ++w) {
+      if (w < warp) at += sw[w];
+      round += sw[w];
+    }
+    if (c) {
+      const uint32_t sj = spos[q];
+      for (uint32_t t = 0; t < c; ++t)
+        if (at + t < capacity) pairs[at + t] = lj_pair{rpos[J.ra + lb + t], sj};
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_run += round;
+    __syncthreads();
+  }
+  if (!WRITE) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) total += __shfl_xor_sync(0xffffffffu, total, d);
+    __shared__ unsigned long long s_tot[kLBlock / 32];
+    if (lane == 0) s_tot[warp] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < kLBlock / 32; ++w) t += s_tot[w];
+      count[blockIdx.x] = t;
+    }
+  }
+}
+
+unsigned blocks_for(uint64_t work, unsigned block) {
+  return (unsigned)std::max<uint64_t>(1, (work + block - 1) / block);
+}
+
+// One relation, partitioned and sorted: keys/pos in sorted order, off[P+1]
+// partition starts, and the model that partitioned it.
+struct Sorted {
+  lj_index* model = nullptr;
+  uint32_t s = 0, P = 1;
+  uint64_t* keys = nullptr;
+  uint32_t* pos = nullptr;
+  uint64_t* off = nullptr;
+};
+
+int sort_relation(const uint64_t* X, uint64_t n, Sorted& out, cudaStream_t s,
+                  uint64_t* sample_buf, uint32_t* pid, unsigned long long* cnt,
+                  unsigned long long* cursor) {
+  out.s = (uint32_t)std::min<uint64_t>(n, kSample);
+  out.P = (uint32_t)std::max<uint64_t>(1, (n + kPartKeys - 1) / kPartKeys);
+  // model: sorted sample + RMI over it
+  const size_t smem = (size_t)kSample * 12;
+  lsj_sample_kernel<<<1, 1024, smem, s>>>(X, n, out.s, sample_buf);
+  LJ_CUDA(cudaGetLastError());
+  const uint32_t L = std::max<uint32_t>(1, out.s / 32);
+  if (int rc = rmi_build(sample_buf, out.s, L, LJ_FP32, (lj_stream_t)s, &out.model)) return rc;
+  const ModelF32 m = ModelF32::make(out.model->root_f32[0], out.model->root_f32[1], L);
+  const auto* leaves = (const LeafF32*)out.model->leaves;
+  LJ_CUDA(cudaMemsetAsync(cnt, 0, (size_t)out.P * 8, s));
+  LJ_CUDA(cudaMemsetAsync(cursor, 0, (size_t)out.P * 8, s));
+  {
+    KernelTimer kt("lsj_hist_kernel", s);
+    lsj_hist_kernel<ModelF32><<<blocks_for(n, kLBlock), kLBlock, 0, s>>>(X, n, m, leaves, out.s,
+                                                                         out.P, pid, cnt);
+  }
+  lsj_scan_kernel<<<1, 1024, 0, s>>>(cnt, out.P, out.off);
+  {
+    KernelTimer kt("lsj_scatter_kernel", s);
+    lsj_scatter_kernel<<<blocks_for(n, kLBlock), kLBlock, 0, s>>>(X, n, pid, out.off, cursor,
+                                                                  out.keys, out.pos);
+  }
+  {
+    KernelTimer kt("lsj_sort_kernel", s);
+    lsj_sort_kernel<<<out.P, 512, (size_t)kSortCap * 12, s>>>(out.keys, out.pos, out.off);
+  }
+  LJ_CUDA(cudaGetLastError());
+  return 0;
+}
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace lj
+
+extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev, uint64_t m,
+                        lj_pair* pairs_dev, uint64_t capacity, uint64_t* written_host,
+                        lj_stream_t stream) {
+  using namespace lj;
+  if (n >= (1ull << 32) || m >= (1ull << 32))
+    return fail(LJ_E_INVAL, "lsj_join: n and m must be below 2^32");
+  if ((n && !R_dev) || (m && !S_dev)) return fail(LJ_E_INVAL, "lsj_join: R or S is NULL");
+  if (capacity > 0 && !pairs_dev) return fail(LJ_E_INVAL, "lsj_join: pairs is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0 || m == 0) {
+    if (written_host) {
+      *written_host = 0;
+      LJ_CUDA(cudaStreamSynchronize(s));
+    }
+    return LJ_OK;
+  }
+  // shared memory above 48 KB for the two sorting kernels (on the current device)
+  LJ_CUDA(cudaFuncSetAttribute(lsj_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSample * 12)));
+  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSortCap * 12)));
+  Sorted R, S;
+  const uint64_t nm = std::max(n, m);
+  const uint32_t Pmax = (uint32_t)((nm + kPartKeys - 1) / kPartKeys) + 1;
+  // scratch: sample, pid, counts, cursors, offsets x2, sorted keys/pos x2
+  const size_t b_sample = round256((size_t)kSample * 8);
+  const size_t b_pid = round256(nm * 4);
+  const size_t b_cnt = round256((size_t)Pmax * 8);
+  const size_t total = b_sample + b_pid + 2 * b_cnt + 2 * round256(((size_t)Pmax + 1) * 8) +
+                       round256(n * 8) + round256(n * 4) + round256(m * 8) + round256(m * 4);
+  char* ws = nullptr;
+  LJ_CUDA(scratch_alloc((void**)&ws, total, s));
+  char* p = ws;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += b;
+    return q;
+  };
+  uint64_t* sample = (uint64_t*)take(b_sample);
+  uint32_t* pid = (uint32_t*)take(b_pid);
+  unsigned long long* cnt = (unsigned long long*)take(b_cnt);
+  unsigned long long* cursor = (unsigned long long*)take(b_cnt);
+  R.off = (uint64_t*)take(round256(((size_t)Pmax + 1) * 8));
+  S.off = (uint64_t*)take(round256(((size_t)Pmax + 1) * 8));
+  R.keys = (uint64_t*)take(round256(n * 8));
+  R.pos = (uint32_t*)take(round256(n * 4));
+  S.keys = (uint64_t*)take(round256(m * 8));
+  S.pos = (uint32_t*)take(round256(m * 4));
+  int rc = 0;
+  JoinItem* items = nullptr;
+  char* ws2 = nullptr;
+  do {
+    // S first (its model is queried by the join), then R; the sample buffer
+    // is reused, so each model is built (and the sample copied) before the
+    // next relation's sample is drawn
+    if ((rc = sort_relation(S_dev, m, S, s, sample, pid, cnt, cursor))) break;
+    if ((rc = sort_relation(R_dev, n, R, s, sample, pid, cnt, cursor))) break;
+    // join items: chunks of R's partitions
+    std::vector<uint64_t> roff(R.P + 1);
+    cudaError_t ce = cudaMemcpyAsync(roff.data(), R.off, (R.P + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+      rc = fail_cuda(ce, "lsj_join: partition offsets");
+      break;
+    }
+    std::vector<uint64_t> item0(R.P + 1, 0);
+    for (uint32_t q = 0; q < R.P; ++q)
+      item0[q + 1] = item0[q] + (roff[q + 1] - roff[q] + kJoinChunk - 1) / kJoinChunk;
+    const uint64_t nitems = item0[R.P];
+    if (nitems >= (1ull << 31)) {
+      rc = fail(LJ_E_INVAL, "lsj_join: too many join items");
+      break;
+    }
+    const size_t b_items = round256(std::max<uint64_t>(nitems, 1) * sizeof(JoinItem));
+    const size_t b_i0 = round256(((size_t)R.P + 1) * 8);
+    const size_t b_ic = round256(std::max<uint64_t>(nitems, 1) * 8);
+    const size_t b_io = round256((std::max<uint64_t>(nitems, 1) + 1) * 8);
+    if ((ce = scratch_alloc((void**)&ws2, b_items + b_i0 + b_ic + b_io, s)) != cudaSuccess) {
+      rc = fail_cuda(ce, "lsj_join: item scratch");
+      break;
+    }
+    items = (JoinItem*)ws2;
+    uint64_t* d_item0 = (uint64_t*)(ws2 + b_items);
+    unsigned long long* icnt = (unsigned long long*)(ws2 + b_items + b_i0);
+    uint64_t* ioff = (uint64_t*)(ws2 + b_items + b_i0 + b_ic);
+    ce = cudaMemcpyAsync(d_item0, item0.data(), (R.P + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) {
+      rc = fail_cuda(ce, "lsj_join: item table");
+      break;
+    }
+    const ModelF32 ms = ModelF32::make(S.model->root_f32[0], S.model->root_f32[1], S.model->L);
+    {
+      KernelTimer kt("lsj_items_kernel", s);
+      lsj_items_kernel<ModelF32><<<blocks_for(R.P, 256), 256, 0, s>>>(
+          R.keys, R.off, R.P, d_item0, ms, (const LeafF32*)S.model->leaves, S.s, S.P, S.off, items);
+    }
+    {
+      KernelTimer kt("lsj_join_count_kernel", s);
+      lsj_join_kernel<false><<<(unsigned)nitems, kLBlock, 0, s>>>(items, R.keys, R.pos, S.keys,
+                                                                  S.pos, icnt, nullptr, nullptr, 0);
+    }
+    lsj_scan_kernel<<<1, 1024, 0, s>>>(icnt, (uint32_t)nitems, ioff);
+    {
+      KernelTimer kt("lsj_join_write_kernel", s);
+      lsj_join_kernel<true><<<(unsigned)nitems, kLBlock, 0, s>>>(items, R.keys, R.pos, S.keys,
+                                                                 S.pos, nullptr, ioff, pairs_dev,
+                                                                 capacity);
+    }
+    if ((ce = cudaGetLastError()) != cudaSuccess) {
+      rc = fail_cuda(ce, "lsj_join kernels");
+      break;
+    }
+    uint64_t written = 0;
+    ce = cudaMemcpyAsync(&written, ioff + nitems, 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+      rc = fail_cuda(ce, "lsj_join: total");
+      break;
+    }
+    if (written_host) *written_host = written;
+    if (written > capacity)
+      rc = fail(LJ_E_CAPACITY, "lsj_join: %llu pairs do not fit the capacity of %llu",
+                (unsigned long long)written, (unsigned long long)capacity);
+  } while (0);
+  if (ws2) scratch_free(ws2, s);
+  scratch_free(ws, s);
+  cudaStreamSynchronize(s);
+  rmi_free(R.model);
+  rmi_free(S.model);
+  if (!rc) rc = take_device_errors(current_device(), s);
+  return rc;
+}

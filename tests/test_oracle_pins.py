@@ -300,3 +300,27 @@ def test_rmi_degenerate_inputs():
                     assert q["ub"] == np.searchsorted(R, np.uint64(x), "right")
     with pytest.raises(oracle.OracleError):
         oracle.rmi_fit(np.array([2, 1], np.uint64), 4)
+
+
+def test_unsorted_join_equals_nested_loops_and_histograms():
+    """The sort-based join of two unsorted relations (Section 4): equal to the
+    nested-loop definition on small inputs (duplicates on both sides,
+    extreme keys, empty sides) and to the histogram closed form on larger
+    ones."""
+    rng = np.random.default_rng(77)
+    for t in range(60):
+        n, m = int(rng.integers(0, 120)), int(rng.integers(0, 120))
+        R = rng.integers(0, 25, n).astype(np.uint64)
+        S = rng.integers(0, 25, m).astype(np.uint64)
+        if t % 7 == 0:
+            R[: n // 3] = np.uint64(2**64 - 1)
+        got = oracle.join_pairs_unsorted(R, S)
+        want = sorted((j, i) for i, j in oracle.brute_force_join(R, S))
+        assert [(int(s), int(r)) for r, s in got] == want
+    R = rng.integers(0, 5000, 200000).astype(np.uint64)
+    S = rng.integers(0, 6000, 150000).astype(np.uint64)
+    got = oracle.join_pairs_unsorted(R, S)
+    cr = np.bincount(R.astype(np.int64), minlength=6000)
+    cs = np.bincount(S.astype(np.int64), minlength=6000)
+    assert got.shape[0] == int(np.sum(cr * cs))
+    assert np.all(R[got[:, 0]] == S[got[:, 1]])

@@ -42,7 +42,7 @@ def _relation(kind, n, rng):
         return np.sort(rng.integers(0, max(2, n // 6), n, dtype=np.uint64))
     if kind == "extremes":
         return np.unique(np.concatenate([rng.integers(0, 2**64 - 1, n, dtype=np.uint64,
-                                                      endpoint=True), np.array([0, TOP])]))
+                                                      endpoint=True), np.array([0, TOP], dtype=np.uint64)]))
     holes = np.flatnonzero(rng.random(2 * n) > 0.1).astype(np.uint64)
     return np.sort(np.repeat(holes[: n // 4], rng.integers(1, 8, n // 4)))[:n]
 
