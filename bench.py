@@ -337,6 +337,67 @@ def uniform_1m_record(reps: int = 200) -> dict:
     return out
 
 
+def run_lsj(args, rank, world, dist):
+    """Learned sort-merge join (Section 4) of two unsorted relations: one step
+    = the whole join (sampled models, partitioning and sorting of both
+    relations, chunked merge-join, pairs written)."""
+    import torch
+
+    import paper_2111_08824_gb300 as lj
+    n = args.n or 100_000_000
+    m = args.m or 100_000_000
+    wl = datagen.lsj_uniform_100m(seed=args.seed + 1000 * rank, n=n, m=m)
+    Rd = torch.from_numpy(wl.R.view(np.int64)).cuda()
+    Sd = torch.from_numpy(wl.S.view(np.int64)).cuda()
+    total = wl.meta["expected_pairs"]
+    pairs = torch.empty((max(total, 1), 2), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        assert lj.lsj_join(Rd, Sd, pairs) == total
+    lj.lj_profile_report()
+    lj.lj_set_option("profile", 1)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lj.lsj_join(Rd, Sd, pairs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lj.lj_set_option("profile", 0)
+    kernels = lj.lj_profile_report()
+    clk = clocks.stop()
+    ms = reduce_max(e0.elapsed_time(e1), dist, "cuda") / args.steps
+    peak, peak_kind = _peaks()
+    # the sort kernel reads and writes each partitioned (key, position) once
+    sort_bytes = 2 * 12 * (n + m)
+    sk = kernels.get("lsj_sort_kernel", {"total_ms": float("nan"), "launches": 1})
+    sort_ms = sk["total_ms"] / sk["launches"] * 2          # two launches (R, S) per step
+    pass_bytes = 8 * (n + m) + 8 * total
+    return {
+        "metric": "join_tuples_per_s", "value": world * (n + m) / (ms / 1e3), "unit": "tuples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 keys", "data": "synthetic",
+        "config": {"workload": "lsj_uniform_100m", "n": n, "m": m, "seed": args.seed,
+                   "l2": "inputs larger than L2"},
+        "pairs": total, "pairs_per_s": world * total / (ms / 1e3),
+        "roofline": {"bound": "hbm", "kernel": "lsj_sort_kernel (both relations)",
+                     "alg_bytes_per_launch": sort_bytes // 2,
+                     "achieved": sort_bytes / (sort_ms / 1e3) / 1e9, "peak": peak,
+                     "frac": sort_bytes / (sort_ms / 1e3) / 1e9 / peak, "unit": "GB/s",
+                     "peak_kind": peak_kind + " copy bandwidth (hbm_gbs)", "traffic": None},
+        "roofline_pass": {"alg_bytes": pass_bytes,
+                          "frac": pass_bytes / (ms / 1e3) / 1e9 / peak},
+        "kernels": kernels, "gpu_launches": sum(k["launches"] for k in kernels.values()),
+        "clocks": clk,
+    }
+
+
 def run_batched(args, rank, world, dist):
     """4096 uneven joins: per-join launches of the plain probe vs one batched
     plan run vs the same run replayed from a CUDA graph (same GPU, same data)."""
@@ -568,7 +629,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lognormal_100m",
-                    choices=sorted(WORKLOADS) + ["batched_4096", "served_64"])
+                    choices=sorted(WORKLOADS) + ["batched_4096", "served_64", "lsj_uniform_100m"])
     ap.add_argument("--rate", type=float, default=2000.0, help="served workload: requests/s")
     ap.add_argument("--duration", type=float, default=5.0, help="served workload: seconds")
     ap.add_argument("--joins", type=int, default=4096, help="batched workload: number of joins")
@@ -613,8 +674,9 @@ def main():
 
     import paper_2111_08824_gb300 as lj
     torch.cuda.set_device(local)
-    if args.workload in ("served_64", "batched_4096"):
-        fn = run_served if args.workload == "served_64" else run_batched
+    if args.workload in ("served_64", "batched_4096", "lsj_uniform_100m"):
+        fn = {"served_64": run_served, "batched_4096": run_batched,
+              "lsj_uniform_100m": run_lsj}[args.workload]
         line = fn(args, rank, world, dist)
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -822,9 +884,12 @@ def main():
         torch.cuda.empty_cache()
         sub = argparse.Namespace(**vars(args))
         sub.joins, sub.scale, sub.seed = 4096, 1.0, args.seed
+        sub_lsj = argparse.Namespace(**vars(sub))
+        sub_lsj.steps, sub_lsj.warmup, sub_lsj.n, sub_lsj.m = 5, 3, None, None
         line["configs"] = {"uniform_1m": uniform_1m_record(),
                            "batched_4096": run_batched(sub, rank, world, dist),
-                           "served_64": run_served(sub, rank, world, dist)}
+                           "served_64": run_served(sub, rank, world, dist),
+                           "lsj_uniform_100m": run_lsj(sub_lsj, rank, world, dist)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -24,6 +24,9 @@ parameters of the five workloads this library is measured on:
                     repeated min(Zipf(1.2), 64) times; S = 200M keys uniform
                     over R's distinct keys.
   batched / served  see `batched_workload` and `served_relations`.
+  lsj_uniform_100m  unsorted relations for the sort-based join: R = 100M
+                    distinct uniform keys in random order; S = 100M draws
+                    from R (every probe matches once), in random order.
 """
 from __future__ import annotations
 
@@ -43,6 +46,7 @@ _CHUNK = 1 << 24
 ST_R_KEYS, ST_R_NORM2, ST_S_COIN, ST_S_HIT, ST_S_MISS = 1, 2, 3, 4, 5
 ST_HOLES, ST_MULT, ST_BATCH_SIZES, ST_BATCH_DIST, ST_CLUSTER = 6, 7, 8, 9, 10
 ST_ARRIVAL = 11
+ST_SHUFFLE_R, ST_SHUFFLE_S = 12, 13
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -335,3 +339,13 @@ WORKLOADS = {
     "lognormal_100m": lognormal_100m,
     "dup_seqh_50m": dup_seqh_50m,
 }
+
+
+def lsj_uniform_100m(seed: int = 0, n: int = 100_000_000, m: int = 100_000_000) -> Workload:
+    """Unsorted R (n distinct uniform 63-bit keys, shuffled) and S (m draws
+    from R with replacement, so every key of S matches exactly once).  The
+    shuffle orders the keys by a splitmix64 draw per position."""
+    R = uniform_unique(n, seed)[np.argsort(rand_u64(seed, ST_SHUFFLE_R, 0, n), kind="stable")]
+    S = R[bounded(rand_u64(seed, ST_S_HIT, 0, m), n).astype(np.int64)] if n else \
+        np.zeros(0, np.uint64)
+    return Workload("lsj_uniform_100m", R, S, 0, "fp32", {"expected_pairs": m if n else 0})

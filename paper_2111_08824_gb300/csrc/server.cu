@@ -14,9 +14,10 @@
 //               admitted into the next free slot, so batches overlap on the
 //               device (continuous batching, not a queue in front of a
 //               single worker).
-//   completion  a host callback enqueued behind each batch wakes the
-//               scheduler, which checks the slot's event; a finished batch
-//               releases its scratch and wakes the waiting clients.
+//   completion  one waiter thread per slot waits for its batch's event
+//               (the runtime polls, so completion is seen within
+//               microseconds), releases the batch's scratch, wakes the
+//               waiting clients and the scheduler.
 // Latency of a request = submit to completion detected (host clock).
 #include <algorithm>
 #include <atomic>
@@ -75,8 +76,12 @@ struct lj_server {
   uint64_t resident = 0;             // bytes of the registered relations (R and index)
   uint64_t mem_in_use = 0, mem_peak = 0;
   bool stop = false;
-  std::atomic<bool> wake{false};   // set by the completion callbacks
+  std::atomic<bool> wake{false};   // set by submissions and completions
   std::thread sched;
+  std::condition_variable cv_launch;   // wakes the slot waiters
+  std::vector<std::thread> waiters;    // one per slot: waits for its batch on the GPU
+  std::vector<char> launched;          // per slot: a batch is in flight, its waiter takes it
+  bool stop_waiters = false;
   // statistics
   std::vector<double> lat_us;
   uint64_t submitted = 0, completed = 0, rejected = 0, keys = 0, batches = 0, batched_reqs = 0;
@@ -105,11 +110,26 @@ void complete_slot(lj_server* sv, Slot& sl) {
   sl.busy = false;
 }
 
-// Host callback enqueued after each batch: wakes the scheduler (no CUDA calls).
-void CUDART_CB on_batch_done(void* p) {
-  lj_server* sv = static_cast<lj_server*>(p);
-  sv->wake.store(true);
-  sv->cv_sched.notify_one();
+// Waiter of slot k: when its batch is launched, waits for the batch's event
+// (the runtime's synchronisation polls, so a finished batch is seen within
+// microseconds), then completes the requests and frees the slot.
+void slot_waiter(lj_server* sv, size_t k) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (true) {
+    sv->cv_launch.wait(lk, [&] { return sv->launched[k] || sv->stop_waiters; });
+    if (!sv->launched[k]) return;   // stopping, nothing in flight
+    Slot& sl = sv->slots[k];
+    const cudaEvent_t ev = sl.done;
+    lk.unlock();
+    cudaEventSynchronize(ev);
+    lk.lock();
+    complete_slot(sv, sl);
+    sv->launched[k] = 0;
+    sv->cv_done.notify_all();
+    sv->wake.store(true);
+    sv->cv_sched.notify_one();
+  }
 }
 
 // Launch the admitted requests `batch` on slot `sl` (called with sv->mu held).
@@ -132,8 +152,7 @@ int launch_slot(lj_server* sv, Slot& sl, std::vector<Request*>& batch) {
     return rc;
   if (cudaMemcpyAsync(sl.written_host, sl.written_dev, jobs.size() * 8, cudaMemcpyDeviceToHost,
                       sl.stream) != cudaSuccess ||
-      cudaEventRecord(sl.done, sl.stream) != cudaSuccess ||
-      cudaLaunchHostFunc(sl.stream, on_batch_done, sv) != cudaSuccess)
+      cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
     return lj::fail(LJ_E_CUDA, "server: cannot enqueue the completion of a batch");
   sl.reqs = batch;
   sl.busy = true;
@@ -147,15 +166,10 @@ void scheduler(lj_server* sv) {
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
     bool progressed = false;
-    // 1. completions
-    for (Slot& sl : sv->slots)
-      if (sl.busy && cudaEventQuery(sl.done) == cudaSuccess) {
-        complete_slot(sv, sl);
-        progressed = true;
-      }
-    if (progressed) sv->cv_done.notify_all();
-    // 2. admission into free slots (first come, first served)
-    for (Slot& sl : sv->slots) {
+    // admission into free slots (first come, first served); completions are
+    // taken by the slots' waiters
+    for (size_t k = 0; k < sv->slots.size(); ++k) {
+      Slot& sl = sv->slots[k];
       if (sl.busy || sv->pending.empty()) continue;
       std::vector<Request*> batch;
       while (!sv->pending.empty() && batch.size() < sv->cfg.max_batch) {
@@ -180,6 +194,9 @@ void scheduler(lj_server* sv) {
         sl.reqs.clear();
         sl.busy = false;
         sv->cv_done.notify_all();
+      } else {
+        sv->launched[k] = 1;
+        sv->cv_launch.notify_all();
       }
       progressed = true;
     }
@@ -188,8 +205,8 @@ void scheduler(lj_server* sv) {
       for (Slot& sl : sv->slots) idle = idle && !sl.busy;
       if (idle) break;
     }
-    // sleep until a submission or a batch completion (callback) wakes us;
-    // the timeout only guards against a wake-up lost between check and wait
+    // sleep until a submission or a completion (slot waiter) wakes us; the
+    // timeout only guards against a wake-up lost between check and wait
     if (!progressed)
       sv->cv_sched.wait_for(lk, std::chrono::microseconds(200),
                             [&] { return sv->wake.exchange(false) || sv->stop; });
@@ -226,6 +243,8 @@ int join_server_create(const lj_server_cfg* cfg, lj_server** out) {
   if (cudaStreamCreateWithFlags(&sv->free_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&sv->fetch_done, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(LJ_E_CUDA, "join_server_create: stream"));
+  sv->launched.assign(sv->slots.size(), 0);
+  for (size_t k = 0; k < sv->slots.size(); ++k) sv->waiters.emplace_back(slot_waiter, sv, k);
   sv->sched = std::thread(scheduler, sv);
   *out = sv;
   return LJ_OK;
@@ -401,7 +420,14 @@ void join_server_destroy(lj_server* sv) {
     sv->stop = true;
   }
   sv->cv_sched.notify_all();
-  if (sv->sched.joinable()) sv->sched.join();
+  if (sv->sched.joinable()) sv->sched.join();   // returns once every slot is idle
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop_waiters = true;
+  }
+  sv->cv_launch.notify_all();
+  for (std::thread& t : sv->waiters)
+    if (t.joinable()) t.join();
   for (auto& kv : sv->reqs) {
     if (kv.second->pairs) lj::scratch_free(kv.second->pairs, sv->free_stream);
     delete kv.second;
