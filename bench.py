@@ -272,8 +272,9 @@ def uniform_1m_record(reps: int = 200) -> dict:
     """The 1M x 1M uniform workload (L = 4096) as a latency case: the inputs
     fit in L2, so L2 is flushed before every rep and each rep is timed alone
     (CUDA events around the call on the launch stream; median of `reps`).
-    Both model precisions, the count-scan-compact pipeline and the fused
-    single-pass kernel; roofline on the algorithmic bytes of the pass."""
+    Both model precisions; the default fused cooperative kernel, the
+    search-compaction pipeline and the single-pass look-back kernel;
+    roofline on the algorithmic bytes of the pass."""
     import torch
 
     import paper_2111_08824_gb300 as lj
@@ -303,12 +304,17 @@ def uniform_1m_record(reps: int = 200) -> dict:
                      f"median of {reps} reps, CUDA events around the call"}
     empty = torch.zeros(1, device="cuda")
     out["event_floor_us"] = 1e3 * statistics.median(timed(lambda: empty.add_(1), reps))
-    old = lj.lj_get_option("single_pass_max")
+    names = ("single_pass_max", "fused_max")
+    old = [lj.lj_get_option(k) for k in names]
     for prec in ("fp64", "fp32"):
         idx = lj.rmi_build(Rd, L, prec)
         rec = 64 if prec == "fp64" else 32
-        for name, spm in (("pipeline", 0), ("single_pass", 1 << 40)):
+        # fused: the default path (one cooperative kernel); pipeline: search,
+        # compaction; single_pass: lookups + decoupled look-back in one kernel
+        for name, spm, fmax in (("fused", 0, old[1]), ("pipeline", 0, 0),
+                                ("single_pass", 1 << 40, 0)):
             lj.lj_set_option("single_pass_max", spm)
+            lj.lj_set_option("fused_max", fmax)
 
             def step():
                 lj.join_emit(idx, Sd, pairs, written=written, want_total=False)
@@ -331,7 +337,8 @@ def uniform_1m_record(reps: int = 200) -> dict:
                              "frac": alg / (med / 1e3) / 1e9 / peak, "unit": "GB/s"},
                 "kernels_us": {k: 1e3 * v["total_ms"] / v["launches"] for k, v in kern.items()},
                 "mean_window": idx.stats()["mean_window"]}
-    lj.lj_set_option("single_pass_max", old)
+    for k, v in zip(names, old):
+        lj.lj_set_option(k, v)
     del Rd, Sd, pairs, flush
     torch.cuda.empty_cache()
     return out
@@ -806,6 +813,10 @@ def main():
     alg = {
         # S, R once, leaves, 4-B result (+ 4-B first match when locating duplicates)
         "probe_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
+        # the same join searched by descending R's key levels
+        "levels_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
+        # small unique batches: lookups and pairs in one kernel
+        "probe_fused_kernel": 8 * m + 8 * n + 32 * L + 8 * total,
         "gapped_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m,  # the same join, gapped index
         "hash_search_kernel": 8 * m + 8 * n + 32 * L + 4 * m + (0 if unique else 4 * m),
         "rs_hash_search_kernel": 8 * m + 8 * n + 4 * m + (0 if unique else 4 * m),

@@ -337,10 +337,12 @@ int join_count_noalloc(const lj_index* index, const uint64_t* S_dev, uint64_t m,
  * join_emit -- write the join pairs (Section 2.A; Section 6.B).
  *   offsets_dev   m+1 offsets from join_count (two-pass path), or NULL for
  *                 the direct path, which needs an index whose R has no
- *                 duplicate key (else LJ_E_NOTUNIQUE): a search kernel, a
- *                 scan of per-tile counts and a kernel that writes the
- *                 pairs (or, for batches up to "single_pass_max" keys, one
- *                 fused kernel).
+ *                 duplicate key (else LJ_E_NOTUNIQUE): for batches up to
+ *                 "fused_max" keys one cooperative kernel (lookups, a
+ *                 grid-wide barrier, block prefixes, pairs); for larger ones
+ *                 a search kernel, a scan of per-tile counts and a kernel
+ *                 that writes the pairs (or, for batches up to
+ *                 "single_pass_max" keys, the single-pass look-back kernel).
  *   pairs_dev     capacity pairs; pairs beyond capacity are not written.
  *   written_dev   optional device uint64: |J| (stream-ordered, no sync)
  *   written_host  optional host uint64: |J|; if given the call synchronises
@@ -586,6 +588,22 @@ void join_server_destroy(lj_server* server);
  *                      (search kernel, then a streaming scan).  Default 0: the
  *                      pipeline measured faster at every batch size from
  *                      2^14 to 2^22 keys.  Both paths give identical results.
+ *   "key_levels"       1: rmi_build also stores R's key levels,
+ *                      a static 4-ary tree of fence keys (level k holds
+ *                      R[4^k i]; about n/3 keys, 8 bytes each), and the
+ *                      pipeline's and the fused kernel's bounded searches
+ *                      descend it (one 32-byte node per level, about
+ *                      log4(window) + 1 loads) instead of halving the window
+ *                      (log2).  0 (default): no levels, halving.  Applies to indexes
+ *                      built afterwards; results are the same either way.
+ *   "fused_max"        join_emit's direct path (unique R) runs batches of
+ *                      at most this many keys in one cooperative kernel of
+ *                      resident blocks (0 .. 2^22; default 2^21; a batch
+ *                      that does not fit the resident blocks takes the
+ *                      pipeline).  Same results as the pipeline.
+ *   "fused_groups"     1 (default): that kernel searches the error window by
+ *                      halving over aligned 4-key groups and reads the last
+ *                      group with one 32-byte load; 0: plain bisection.
  *   "host_chunk"       probe keys per chunk of join_host (2^16 .. 2^32-1;
  *                      default 2^25).
  *   "probe_buckets"    1: the pipeline first groups the probes of every
@@ -609,8 +627,10 @@ void join_server_destroy(lj_server* server);
  *                      skips this many leading tiles, which then never publish
  *                      their state, so the look-back waits of the next tiles
  *                      run out and the call reports LJ_E_TIMEOUT (no device
- *                      trap; the context stays usable).  Results of such a
- *                      call are unspecified.
+ *                      trap; the context stays usable); likewise the fused
+ *                      kernel (fused_max) skips this many leading blocks,
+ *                      which never reach its grid-wide barrier.  Results of
+ *                      such a call are unspecified.
  *   "profile"          1: record CUDA events around every kernel the library
  *                      launches (on the launch's stream); lj_profile_report
  *                      returns the per-kernel totals.  0 (default): off.

@@ -148,6 +148,22 @@ int lj_set_option(const char* name, int64_t value) {
     set_single_pass_max((uint64_t)value);
     return LJ_OK;
   }
+  if (!strcmp(name, "key_levels")) {
+    if (value < 0 || value > 1) return fail(LJ_E_INVAL, "key_levels must be 0 or 1");
+    set_key_levels((int)value);
+    return LJ_OK;
+  }
+  if (!strcmp(name, "fused_max")) {
+    if (value < 0 || value > (1ll << 22))
+      return fail(LJ_E_INVAL, "fused_max must be in [0, 2^22]");
+    set_fused_max((uint64_t)value);
+    return LJ_OK;
+  }
+  if (!strcmp(name, "fused_groups")) {
+    if (value < 0 || value > 1) return fail(LJ_E_INVAL, "fused_groups must be 0 or 1");
+    set_fused_groups((int)value);
+    return LJ_OK;
+  }
   if (!strcmp(name, "profile")) {
     set_profiling(value != 0);
     return LJ_OK;
@@ -180,6 +196,9 @@ int lj_set_option(const char* name, int64_t value) {
 int64_t lj_get_option(const char* name) {
   using namespace lj;
   if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
+  if (name && !strcmp(name, "key_levels")) return get_key_levels();
+  if (name && !strcmp(name, "fused_max")) return (int64_t)get_fused_max();
+  if (name && !strcmp(name, "fused_groups")) return get_fused_groups();
   if (name && !strcmp(name, "profile")) return profiling() ? 1 : 0;
   if (name && !strcmp(name, "host_chunk")) return (int64_t)get_host_chunk();
   if (name && !strcmp(name, "probe_buckets")) return get_probe_buckets();
@@ -242,6 +261,7 @@ void rmi_free(lj_index* index) {
   if (!index) return;
   lj::grmi_release(index);
   if (index->leaves && !index->leaves_block) cudaFree(index->leaves);
+  if (index->levels) cudaFree(index->levels);
   delete index;   // the last index of a batch releases the batch's leaf records
 }
 

@@ -31,6 +31,7 @@
 //              per-leaf min / max by warp reduction + integer atomics; then
 //              the leaf records and per-relation window statistics.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <memory>
 #include <vector>
@@ -743,13 +744,74 @@ int build_many(const uint64_t* const* R, const uint64_t* n, const uint32_t* leav
 }  // namespace
 }  // namespace lj
 
+namespace lj {
+
+// Key levels of R for the descent search (search_levels): level k holds
+// R[4^k i] for i < ceil(n / 4^k), padded with 2^64 - 1 to whole nodes of
+// four entries (the probes never pass padding: they check positions).
+namespace {
+std::atomic<int> g_key_levels{0};
+
+__global__ void key_level_kernel(const uint64_t* __restrict__ R, uint64_t n, uint32_t shift,
+                                 uint64_t* __restrict__ out, uint64_t entries) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= entries) return;
+  const uint64_t pos = i << shift;
+  out[i] = pos < n ? __ldg(reinterpret_cast<const unsigned long long*>(R) + pos) : ~0ull;
+}
+}  // namespace
+
+void set_key_levels(int v) { g_key_levels = v; }
+int get_key_levels() { return g_key_levels; }
+
+int build_key_levels(lj_index* idx, cudaStream_t s) {
+  const uint64_t n = idx->n;
+  if (n <= 4) return 0;   // one node of R: no level above it
+  uint64_t off[kMaxLevels + 1] = {};
+  uint32_t nlev = 0;
+  uint64_t total = 0;
+  for (uint32_t k = 1; k <= (uint32_t)kMaxLevels; ++k) {
+    const uint64_t Nk = (n + (1ull << (2 * k)) - 1) >> (2 * k);
+    off[k] = total;
+    total += (Nk + 3) & ~3ull;
+    nlev = k;
+    if (Nk <= 4) break;
+  }
+  uint64_t* lev = nullptr;
+  LJ_CUDA(cudaMalloc((void**)&lev, total * 8));
+  for (uint32_t k = 1; k <= nlev; ++k) {
+    const uint64_t entries = (k < nlev ? off[k + 1] : total) - off[k];
+    key_level_kernel<<<(unsigned)((entries + 255) / 256), 256, 0, s>>>(idx->R, n, 2 * k,
+                                                                      lev + off[k], entries);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFree(lev);
+    return fail_cuda(e, "key_level_kernel");
+  }
+  idx->levels = lev;
+  idx->nlev = nlev;
+  for (int k = 0; k <= kMaxLevels; ++k) idx->lev_off[k] = (uint32_t)off[k];
+  return 0;
+}
+
+}  // namespace lj
+
 extern "C" int rmi_build(const uint64_t* R_dev, uint64_t n, uint32_t leaves, int precision,
                          lj_stream_t stream, lj_index** out) {
   using namespace lj;
   if (!out) return fail(LJ_E_INVAL, "rmi_build: out is NULL");
   *out = nullptr;
   if (int rc = check_build_args(R_dev, n, leaves, precision, "rmi_build")) return rc;
-  return build_many(&R_dev, &n, &leaves, 1, precision, (cudaStream_t)stream, out);
+  if (int rc = build_many(&R_dev, &n, &leaves, 1, precision, (cudaStream_t)stream, out)) return rc;
+  if (get_key_levels()) {
+    if (int rc = build_key_levels(*out, (cudaStream_t)stream)) {
+      rmi_free(*out);
+      *out = nullptr;
+      return rc;
+    }
+  }
+  return LJ_OK;
 }
 
 extern "C" int rmi_build_batch(const uint64_t* const* R_dev, const uint64_t* n,

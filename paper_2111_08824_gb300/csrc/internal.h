@@ -10,6 +10,10 @@
 
 #include "../../include/ljoin.h"
 
+namespace lj {
+constexpr int kMaxLevels = 15;   // key levels of R: 4^16 > 2^32 - 1 positions
+}  // namespace lj
+
 struct lj_index {
   const uint64_t* R = nullptr;   // borrowed, sorted
   uint64_t n = 0;
@@ -43,6 +47,11 @@ struct lj_index {
   uint32_t rs_S = 0, rs_shift = 0, rs_rbits = 0, rs_eps = 0;
   uint64_t rs_kmin = 0, rs_kmax = 0;
   lj_grmi_stats gstats{};
+  // key levels of R (option "key_levels"): level k = 1 .. nlev holds
+  // R[4^k i] (padded to whole 4-entry nodes) at levels + lev_off[k]
+  uint64_t* levels = nullptr;
+  uint32_t nlev = 0;
+  uint32_t lev_off[lj::kMaxLevels + 1] = {};
 };
 
 namespace lj {
@@ -131,7 +140,16 @@ int get_probe_buckets();
 uint32_t lookback_polls();
 uint32_t fault_skip_tiles();
 
+// Key levels built by rmi_build (option "key_levels": 0 off, 1 on).
+void set_key_levels(int v);
+int get_key_levels();
+int build_key_levels(lj_index* idx, cudaStream_t s);
+
 // Probe batches of at most this many keys take the single-pass kernel.
+void set_fused_max(uint64_t v);
+uint64_t get_fused_max();
+void set_fused_groups(int v);
+int get_fused_groups();
 void set_single_pass_max(uint64_t v);
 uint64_t get_single_pass_max();
 

@@ -6,7 +6,10 @@
 // every match in the range is returned.  Output pairs are written s-major,
 // r-ascending.
 //
-// Two execution paths, chosen by the size of the probe batch:
+// Execution paths, chosen by the size of the probe batch:
+//   fused (join_emit against a unique R, m <= fused_max, default 2^21):
+//     probe_fused_kernel: one cooperative launch of resident blocks;
+//     lookups, a grid-wide barrier, block prefixes from group sums, pairs.
 //   single pass (m <= single_pass_max, default 0, i.e. on request only):
 //     probe_single_pass_kernel<Model, MODE, K, VEC>: block tiles of 256
 //     threads x K rounds x 2 probes; lookups, block scan, decoupled look-back
@@ -51,6 +54,16 @@ namespace {
 // 2048 probes leave most SMs idle on small batches and wait in the
 // look-back on large ones.
 std::atomic<uint64_t> g_single_pass_max{0};
+
+// Unique-R batches up to this size take the fused cooperative kernel
+// (option "fused_max"); fused_groups = 1 searches their windows on 4-key
+// groups (option "fused_groups").  Measured with the L2 flushed (uniform
+// 1M-key R, L = 4096, fp64 model): 2^14 probes 17.4 -> 16.5 us, 2^18
+// 23.3 -> 19.1 us, 2^20 40.6 -> 37.0 us, 2^21 71.3 -> 61.5 us against the
+// pipeline; bisection instead of the 4-key groups: 2^20 40.1 us.
+std::atomic<uint64_t> g_fused_max{1ull << 21};
+std::atomic<int> g_fused_groups{1};
+constexpr uint32_t kFusedMaxPerBlock = 4096;   // probes (words in shared memory) per block
 
 // Bucketed probe order in the pipeline (option "probe_buckets"; off by
 // default: it pays where probes spread over an R larger than L2, and costs
@@ -138,6 +151,113 @@ __global__ void __launch_bounds__(kBlock, LJ_MINB) probe_single_pass_kernel(Prob
     write_round<Model, MODE, VEC>(P, j0, tile_prefix + s_wpre[k * kWarps + warp] + lane_excl[k],
                                   cnt[2 * k], cnt[2 * k + 1], r_idx[2 * k], r_idx[2 * k + 1],
                                   valid[2 * k], valid[2 * k + 1]);
+  }
+}
+
+// Fused kernel for small batches against a unique R (join_emit's direct
+// path, m <= fused_max): one cooperative launch of resident blocks.  Block b
+// owns the contiguous probes [b * per_block, (b + 1) * per_block):
+//   1. lookups, two probes per thread and round, one word per probe kept in
+//      shared memory (first match or kNoMatch);
+//   2. the block's match count goes to bcount[b] and to the sum of its group
+//      of 32 blocks; then a grid-wide barrier (bounded wait);
+//   3. exclusive prefix of block b = the sums of the groups before its group
+//      + the counts of the blocks before it in its group (two warp loads);
+//   4. the block writes its pairs in probe order, 256 words per step (warp
+//      ballots, one block scan of 8 warp totals), coalesced 8-byte stores.
+// Compared with the pipeline this saves a launch, the per-probe words'
+// round trip through memory and the compaction's prefix sums; compared with
+// the single-pass kernel no block waits for a predecessor's lookups: the
+// barrier is passed once, when every block has counted.
+constexpr int kFusedBlock = 256;
+constexpr uint32_t kFusedGroup = 32;   // blocks per group sum
+
+struct FusedState {
+  uint32_t* arrive;              // barrier counter, zeroed before the launch
+  unsigned long long* gsum;      // per group of kFusedGroup blocks, zeroed
+  uint32_t* bcount;              // per block (written before the barrier)
+  uint32_t polls;                // bound of the barrier wait (polls)
+};
+
+template <class Model, bool VEC, int SEARCH>
+__global__ void __launch_bounds__(kFusedBlock, LJ_FMINB)
+    probe_fused_kernel(ProbeParams<Model> P, FusedState F, uint32_t per_block) {
+  extern __shared__ uint32_t s_word[];   // per_block words
+  __shared__ uint32_t s_wsum[kFusedBlock / 32];
+  __shared__ unsigned long long s_prefix;
+  if (blockIdx.x < P.tile_skip) return;   // fault-injection hook (0): such blocks never arrive
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t b0 = (uint64_t)blockIdx.x * per_block;
+  const uint32_t nb = b0 < P.m ? (uint32_t)(P.m - b0 < per_block ? P.m - b0 : per_block) : 0u;
+  uint32_t c = 0;
+#pragma unroll 1
+  for (uint32_t o = 2 * threadIdx.x; o < nb; o += 2 * kFusedBlock) {
+    uint32_t r_idx[2], cnt[2];
+    bool valid[2];
+    lookup_probes<Model, kUniqueCount, 1, VEC, SEARCH>(P, b0 + o, 0, r_idx, cnt, valid);
+    s_word[o] = cnt[0] ? r_idx[0] : kNoMatch;
+    if (o + 1 < nb) s_word[o + 1] = cnt[1] ? r_idx[1] : kNoMatch;
+    c += cnt[0] + cnt[1];   // probe o + 1 >= nb only at the end of S: cnt[1] = 0
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if (lane == 0) s_wsum[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kFusedBlock / 32; ++w) tot += s_wsum[w];
+    F.bcount[blockIdx.x] = tot;
+    if (tot) atomicAdd(F.gsum + blockIdx.x / kFusedGroup, (unsigned long long)tot);
+    __threadfence();
+    atomicAdd(F.arrive, 1u);
+    // every block is resident (cooperative launch), so the wait ends; it is
+    // still bounded, and a timeout is reported as an error
+    uint32_t polls = 0;
+    while (ld_acquire_u32(F.arrive) < gridDim.x) {
+      if (++polls > F.polls) {
+        atomicOr(P.err, kErrLookbackTimeout);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t g = blockIdx.x / kFusedGroup, g0 = g * kFusedGroup;
+    unsigned long long pre = 0;
+    for (uint32_t q = lane; q < g; q += 32) pre += __ldcg(F.gsum + q);
+    if (g0 + lane < blockIdx.x) pre += __ldcg(F.bcount + g0 + lane);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, d);
+    if (lane == 0) {
+      s_prefix = pre;
+      if (blockIdx.x + 1 == gridDim.x) last_tile_total<Model, kUniqueEmit>(P, pre + __ldcg(F.bcount + blockIdx.x));
+    }
+  }
+  __syncthreads();
+  unsigned long long run = s_prefix;
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll 1
+  for (uint32_t o = 0; o < nb; o += kFusedBlock) {
+    const uint32_t i = o + threadIdx.x;
+    const uint32_t w = i < nb ? s_word[i] : kNoMatch;
+    const unsigned bal = __ballot_sync(0xffffffffu, w != kNoMatch);
+    if (lane == 0) s_wsum[warp] = __popc(bal);
+    __syncthreads();
+    uint32_t woff = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < kFusedBlock / 32; ++q) {
+      const uint32_t t = s_wsum[q];
+      woff += q < warp ? t : 0u;
+      tot += t;
+    }
+    if (w != kNoMatch) {
+      const unsigned long long pos = run + woff + __popc(bal & below);
+      if (pos < P.capacity) P.pairs[pos] = lj_pair{w, (uint32_t)(b0 + i + P.s_base)};
+    }
+    run += tot;
+    __syncthreads();   // s_wsum is rewritten by the next step
   }
 }
 
@@ -297,7 +417,7 @@ __global__ void __launch_bounds__(kBlock)
 // At the end of the chunk the block adds its probes' match count to the
 // count of their compaction tile (a chunk never straddles two): one barrier
 // and one atomic per chunk (per-warp atomics contended badly).
-template <class Model, int MODE, int CHUNK, bool VEC, int GAP>
+template <class Model, int MODE, int CHUNK, bool VEC, int GAP, int SEARCH = kSearchHalve>
 __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32_t* __restrict__ out,
                                              unsigned long long* __restrict__ tile_counts) {
   constexpr uint64_t kChunkProbes = 2ull * kSearchBlock * CHUNK;
@@ -315,7 +435,7 @@ __device__ __forceinline__ void search_chunk(const ProbeParams<Model>& P, uint32
     if constexpr (GAP != 0)
       lookup_gapped<Model, MODE, VEC, GAP - 1>(P, j0, r_idx, cnt, valid);
     else
-      lookup_probes<Model, MODE, 1, VEC>(P, j0, 0, r_idx, cnt, valid);
+      lookup_probes<Model, MODE, 1, VEC, SEARCH>(P, j0, 0, r_idx, cnt, valid);
     uint32_t w0, w1;
     if (MODE == kDupCount) {
       w0 = cnt[0];
@@ -357,6 +477,15 @@ __global__ void __launch_bounds__(kSearchBlock, LJ_SMINB)
     probe_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
                         unsigned long long* __restrict__ tile_counts) {
   search_chunk<Model, MODE, CHUNK, VEC, 0>(P, out, tile_counts);
+}
+
+// The same with the bounded search as a descent of R's key levels
+// (search_levels), for an index that has them.
+template <class Model, int MODE, int CHUNK, bool VEC>
+__global__ void __launch_bounds__(kSearchBlock, LJ_LMINB)
+    levels_search_kernel(ProbeParams<Model> P, uint32_t* __restrict__ out,
+                         unsigned long long* __restrict__ tile_counts) {
+  search_chunk<Model, MODE, CHUNK, VEC, 0, kSearchLevels>(P, out, tile_counts);
 }
 
 // The same with the GRMI lookup (Section 3.A): exponential search in the
@@ -836,6 +965,9 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.hn1 = idx->n + 1;
   P.rs = RsDev{idx->rs_x, idx->rs_y, idx->rs_rcp, idx->rs_table, idx->rs_kmin, idx->rs_kmax,
                idx->n, idx->rs_S, idx->rs_shift};
+  P.levels = idx->levels;
+  P.nlev = idx->nlev;
+  for (int k = 0; k <= kMaxLevels; ++k) P.lev_off[k] = idx->lev_off[k];
   return P;
 }
 
@@ -969,6 +1101,82 @@ int launch_bucketed(const lj_index* idx, const ProbeParams<Model>& P, bool dup, 
   return 0;
 }
 
+// Fused path (join_emit, unique R, m <= fused_max): one cooperative launch
+// of probe_fused_kernel over at most as many blocks as can be resident.
+template <class Model, bool VEC, int SEARCH>
+int launch_fused_as(const lj_index* idx, ProbeParams<Model> P, uint64_t* total_host,
+                    cudaStream_t s) {
+  const uint64_t m = P.m;
+  static std::atomic<int> per_sm_cache{0};
+  int per_sm = per_sm_cache.load();
+  if (per_sm == 0) {
+    LJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, probe_fused_kernel<Model, VEC, SEARCH>, kFusedBlock, kFusedMaxPerBlock * 4));
+    if (per_sm <= 0) return fail(LJ_E_CUDA, "probe_fused_kernel: no resident block fits an SM");
+    per_sm_cache = per_sm;
+  }
+  int sms = 0;
+  LJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device));
+  const uint64_t cap_blocks = (uint64_t)per_sm * (uint64_t)sms;
+  uint64_t grid = std::min<uint64_t>(cap_blocks, (m + 2 * kFusedBlock - 1) / (2 * kFusedBlock));
+  // probes per block: even (pairs of keys are read with one 16-byte load)
+  uint32_t per_block = (uint32_t)(((m + grid - 1) / grid + 1) & ~1ull);
+  if (per_block > kFusedMaxPerBlock) return 1;   // more than the resident blocks hold: the pipeline
+  grid = (m + per_block - 1) / per_block;   // no empty block
+  // scratch: barrier counter | total | group sums (zeroed) | block counts
+  const size_t b_gsum = ((grid / kFusedGroup + 1) * 8 + 255) / 256 * 256;
+  const size_t b_cnt = (grid * 4 + 255) / 256 * 256;
+  char* ws = nullptr;
+  LJ_CUDA(scratch_alloc((void**)&ws, 256 + b_gsum + b_cnt, s));
+  LJ_CUDA(cudaMemsetAsync(ws, 0, 256 + b_gsum, s));
+  FusedState F;
+  F.arrive = (uint32_t*)ws;
+  F.gsum = (unsigned long long*)(ws + 256);
+  F.bcount = (uint32_t*)(ws + 256 + b_gsum);
+  F.polls = lookback_polls();
+  P.total_ws = (uint64_t*)(ws + 64);
+  P.tile_skip = std::min<uint32_t>(fault_skip_tiles(), (uint32_t)grid - 1);
+  void* args[] = {&P, &F, &per_block};
+  cudaError_t e;
+  {
+    KernelTimer kt("probe_fused_kernel", s);
+    e = cudaLaunchCooperativeKernel((const void*)probe_fused_kernel<Model, VEC, SEARCH>,
+                                    dim3((unsigned)grid), dim3(kFusedBlock), args,
+                                    (size_t)per_block * 4, s);
+  }
+  if (e != cudaSuccess) {
+    scratch_free(ws, s);
+    return fail_cuda(e, "probe_fused_kernel: cooperative launch");
+  }
+  if (total_host) LJ_CUDA(cudaMemcpyAsync(total_host, P.total_ws, 8, cudaMemcpyDeviceToHost, s));
+  LJ_CUDA(scratch_free(ws, s));
+  if (total_host) {
+    LJ_CUDA(cudaStreamSynchronize(s));
+    if (int r2 = take_device_errors(idx->device, s)) return r2;
+  }
+  return 0;
+}
+
+template <class Model>
+int launch_fused(const lj_index* idx, Model model, const uint64_t* S, uint64_t m, lj_pair* pairs,
+                 uint64_t cap, uint64_t* total_dev, uint64_t* total_host, uint32_t s_base,
+                 cudaStream_t s) {
+  ProbeParams<Model> P = make_params(idx, model, S, m, s_base, device_error_word(idx->device));
+  if (!P.err) return fail(LJ_E_NOMEM, "cannot allocate the device error word");
+  P.pairs = pairs;
+  P.capacity = cap;
+  P.total_out = total_dev;
+  const bool vec = aligned(S, 16);
+  if (P.levels)
+    return vec ? launch_fused_as<Model, true, kSearchLevels>(idx, P, total_host, s)
+               : launch_fused_as<Model, false, kSearchLevels>(idx, P, total_host, s);
+  if (g_fused_groups.load() != 0)
+    return vec ? launch_fused_as<Model, true, kSearchGroups>(idx, P, total_host, s)
+               : launch_fused_as<Model, false, kSearchGroups>(idx, P, total_host, s);
+  return vec ? launch_fused_as<Model, true, kSearchHalve>(idx, P, total_host, s)
+             : launch_fused_as<Model, false, kSearchHalve>(idx, P, total_host, s);
+}
+
 // Count-scan-emit path: search kernel (per-probe words + per-tile counts)
 // -> tile_scan_kernel (tile prefixes, total) -> compact_kernel.
 template <class Model>
@@ -1020,7 +1228,7 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
       return rc;
     }
   } else {
-    KernelTimer kt(!P.gkeys                  ? "probe_search_kernel"
+    KernelTimer kt(!P.gkeys                  ? (P.levels ? "levels_search_kernel" : "probe_search_kernel")
                    : idx->gkind == kRmiHash ? "hash_search_kernel"
                    : idx->gkind == kRsHash  ? "rs_hash_search_kernel"
                                             : "gapped_search_kernel", s);
@@ -1042,6 +1250,11 @@ int launch_pipeline(const lj_index* idx, Model model, int mode, const uint64_t* 
         LJ_SEARCH(gapped_search_kernel, kDupCount);
       else
         LJ_SEARCH(gapped_search_kernel, kUniqueCount);
+    } else if (P.levels) {
+      if (dup)
+        LJ_SEARCH(levels_search_kernel, kDupCount);
+      else
+        LJ_SEARCH(levels_search_kernel, kUniqueCount);
     } else {
       if (dup)
         LJ_SEARCH(probe_search_kernel, kDupCount);
@@ -1122,6 +1335,11 @@ int launch_probe(const lj_index* idx, Model model, int mode, const uint64_t* S, 
   if (m <= g_single_pass_max.load() && !idx->gkeys)   // the GRMI lookup runs in the pipeline only
     return launch_single_pass(idx, model, mode, S, m, pairs, cap, counts, offsets, first,
                               total_dev, total_host, s_base, s);
+  const int order = idx->probe_order >= 0 ? idx->probe_order : g_probe_buckets.load();
+  if (mode == kUniqueEmit && m <= g_fused_max.load() && !idx->gkeys && order == 0) {
+    const int rc = launch_fused(idx, model, S, m, pairs, cap, total_dev, total_host, s_base, s);
+    if (rc <= 0) return rc;   // rc > 0: the batch does not fit the resident blocks
+  }
   return launch_pipeline(idx, model, mode, S, m, pairs, cap, counts, offsets, first, total_dev,
                          total_host, s_base, s);
 }
@@ -1221,6 +1439,10 @@ int probe_expand_impl(const uint32_t* first, const uint64_t* offsets, uint64_t m
 
 void set_probe_buckets(int v) { g_probe_buckets = v; }
 int get_probe_buckets() { return g_probe_buckets; }
+void set_fused_max(uint64_t v) { g_fused_max = v; }
+uint64_t get_fused_max() { return g_fused_max; }
+void set_fused_groups(int v) { g_fused_groups = v; }
+int get_fused_groups() { return g_fused_groups; }
 void set_single_pass_max(uint64_t v) { g_single_pass_max = v; }
 uint64_t get_single_pass_max() { return g_single_pass_max; }
 

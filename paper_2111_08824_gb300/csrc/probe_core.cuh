@@ -52,6 +52,11 @@ struct ProbeParams {
   uint64_t hB;            // buckets
   uint64_t hn1;           // n + 1
   RsDev rs;               // RadixSpline of the learned hash over it (kind kRsHash)
+  // key levels of R (search_levels): level k >= 1 holds R[4^k i] at
+  // levels + lev_off[k]; nlev levels (0: none)
+  const uint64_t* levels;
+  uint32_t nlev;
+  uint32_t lev_off[kMaxLevels + 1];
 };
 
 // Tunables (fixed at compile time; the defaults are the measured best).
@@ -70,6 +75,13 @@ struct ProbeParams {
 #ifndef LJ_SMINB
 #define LJ_SMINB 16        // search kernel: 16 blocks of 128 threads per SM (32 registers,
                            // full occupancy): measured 9% faster than the unconstrained build
+#endif
+#ifndef LJ_LMINB
+#define LJ_LMINB 12        // key-level search kernel: 12 blocks of 128 threads per SM
+#endif
+#ifndef LJ_FMINB
+#define LJ_FMINB 4         // fused small-batch kernel: 4 blocks of 256 threads per SM (64
+                           // registers; fewer registers spill its lookup loop)
 #endif
 #ifndef LJ_GROUP4
 #define LJ_GROUP4 true     // duplicates: halving over aligned 4-key groups + one 32-byte load
@@ -212,6 +224,84 @@ __device__ __forceinline__ void search_last_g4(const uint64_t* __restrict__ R, u
     base[p] = res;
     len[p] = start[p];
   }
+}
+
+// Bounded search by descending the key levels of R, a static 4-ary tree of
+// fence keys over the sorted keys: level 0 is R itself, level k holds
+// R[4^k i], so node b of level k (entries 4b .. 4b + 3, one 32-byte load)
+// splits the block of positions [b 4^(k+1), (b + 1) 4^(k+1)) into its four
+// children.  Same contract as search_last: the wanted position (the first
+// key >= x when STRICT, > x otherwise) lies in [base, base + len].  The
+// descent starts at the lowest level whose block holds both the position
+// before the window and the window's last position (so the last passing key
+// is in that block), takes in each node the last child whose first key
+// passes, and ends with one sector of R: about log4 of the window's width
+// plus one loads, against log2 for halving.  Entries at positions >= n
+// never pass.  lev_off[k] = offset of level k in `lev`.
+template <int NP, bool STRICT, class P_>
+__device__ __forceinline__ void search_levels(const P_& P, const uint64_t (&x)[NP],
+                                              uint32_t (&base)[NP], uint32_t (&len)[NP],
+                                              uint64_t (&cv)[NP]) {
+  const uint32_t n = P.n;
+  uint32_t start[NP], blk[NP];
+  int lvl[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    start[p] = base[p];
+    cv[p] = 0;
+    lvl[p] = -1;   // done
+    blk[p] = 0;
+    if (len[p] > 0) {
+      const uint32_t lo = base[p] ? base[p] - 1 : 0, hi = base[p] + len[p] - 1;
+      const uint32_t d = lo ^ hi;
+      lvl[p] = d ? (31 - __clz(d)) >> 1 : 0;
+      blk[p] = (uint32_t)((uint64_t)hi >> (2 * lvl[p] + 2));
+    }
+  }
+  while (true) {
+    bool any = false;
+    uint64_t k[NP][4];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (lvl[p] >= 0) {
+        any = true;
+        const uint64_t e = 4ull * blk[p];   // first entry of the node in its level
+        if (lvl[p] > 0) {
+          ldg_key4(P.levels + P.lev_off[lvl[p]], (uint32_t)e, k[p]);   // levels are padded
+        } else if (P.r32 && e + 4 <= n) {
+          ldg_key4(P.R, (uint32_t)e, k[p]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) k[p][c] = e + c < n ? ldg_key(P.R, (uint32_t)(e + c)) : 0;
+        }
+      }
+    if (!any) break;
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (lvl[p] >= 0) {
+        const uint64_t pos0 = (uint64_t)blk[p] << (2 * lvl[p] + 2);   // position of entry 0
+        const uint64_t step = 1ull << (2 * lvl[p]);
+        uint32_t t = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const bool pass = pos0 + c * step < n && (STRICT ? k[p][c] < x[p] : k[p][c] <= x[p]);
+          t += pass ? 1u : 0u;
+        }
+        if (lvl[p] == 0) {
+          base[p] = (uint32_t)pos0 + t;
+          cv[p] = t == 1 ? k[p][0] : t == 2 ? k[p][1] : t == 3 ? k[p][2] : t == 4 ? k[p][3] : 0;
+          lvl[p] = -1;
+        } else if (t == 0) {   // nothing in the block passes (its start is position 0)
+          base[p] = (uint32_t)pos0;
+          lvl[p] = -1;
+        } else {
+          blk[p] = 4 * blk[p] + t - 1;
+          --lvl[p];
+        }
+      }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) len[p] = start[p];
 }
 
 // Exponential search of a GRMI (Section 3.A), NP probes interleaved: for
@@ -382,8 +472,13 @@ __device__ __forceinline__ void lookup_gapped(const ProbeParams<Model>& P, uint6
 
 // Lookups of NP keys already loaded (x, valid): root -> leaf record ->
 // window, then the interleaved bounded searches; cnt = number of matches,
-// r_idx = first matching position (when cnt > 0).
-template <class Model, int MODE, int NP>
+// r_idx = first matching position (when cnt > 0).  SEARCH selects the
+// bounded search: kSearchHalve (halving; duplicates on 4-key groups when
+// LJ_GROUP4), kSearchGroups (halving over 4-key groups for unique keys too:
+// about two dependent loads fewer on small windows), kSearchLevels (descent
+// of the key levels, when the index has them).
+enum { kSearchHalve = 0, kSearchGroups = 1, kSearchLevels = 2 };
+template <class Model, int MODE, int NP, int SEARCH = kSearchHalve>
 __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const uint64_t (&x)[NP],
                                             const bool (&valid)[NP], uint32_t (&r_idx)[NP],
                                             uint32_t (&cnt)[NP]) {
@@ -409,7 +504,9 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
 #pragma unroll
     for (int p = 0; p < NP; ++p) wh[p] = base[p] + len[p];
     uint64_t cv[NP];
-    if (LJ_GROUP4 && P.r32)
+    if (SEARCH == kSearchLevels)
+      search_levels<NP, true>(P, x, base, len, cv);            // base = lower bound
+    else if (LJ_GROUP4 && P.r32)
       search_last_g4<NP, true>(P.R, P.n, x, base, len, cv);   // base = lower bound
     else
       search_last<NP, true>(P.R, x, base, len, cv);            // base = lower bound
@@ -419,7 +516,9 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
       lb[p] = base[p];
       len[p] = wh[p] - base[p];
     }
-    if (LJ_GROUP4 && P.r32)
+    if (SEARCH == kSearchLevels)
+      search_levels<NP, false>(P, x, base, len, cv);           // base = upper bound
+    else if (LJ_GROUP4 && P.r32)
       search_last_g4<NP, false>(P.R, P.n, x, base, len, cv);  // base = upper bound
     else
       search_last<NP, false>(P.R, x, base, len, cv);           // base = upper bound
@@ -430,7 +529,12 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
     }
   } else {
     uint64_t cv[NP];
-    search_last<NP, false>(P.R, x, base, len, cv);  // base = upper bound, len = start
+    if (SEARCH == kSearchLevels)
+      search_levels<NP, false>(P, x, base, len, cv);          // base = upper bound, len = start
+    else if (SEARCH == kSearchGroups && P.r32)
+      search_last_g4<NP, false>(P.R, P.n, x, base, len, cv);  // base = upper bound, len = start
+    else
+      search_last<NP, false>(P.R, x, base, len, cv);          // base = upper bound, len = start
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       const bool match = valid[p] && base[p] > len[p] && cv[p] == x[p];
@@ -444,7 +548,7 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
 // j0 = first + 2*stride*k + {0, 1} (one 16-byte load of two keys).  Root ->
 // leaf record -> window, then the interleaved bounded searches.  cnt is the
 // number of matches, r_idx the first matching position (when cnt > 0).
-template <class Model, int MODE, int K, bool VEC>
+template <class Model, int MODE, int K, bool VEC, int SEARCH = kSearchHalve>
 __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint64_t first,
                                               uint32_t stride, uint32_t (&r_idx)[2 * K],
                                               uint32_t (&cnt)[2 * K], bool (&valid)[2 * K]) {
@@ -466,7 +570,7 @@ __device__ __forceinline__ void lookup_probes(const ProbeParams<Model>& P, uint6
           valid[2 * k + 1] ? __ldg(reinterpret_cast<const unsigned long long*>(P.S) + j0 + 1) : 0;
     }
   }
-  lookup_keys<Model, MODE, NP>(P, x, valid, r_idx, cnt);
+  lookup_keys<Model, MODE, NP, SEARCH>(P, x, valid, r_idx, cnt);
 }
 
 // Exclusive scan of the per-tile counts: blocks of 256 threads x 16 counts

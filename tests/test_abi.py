@@ -50,7 +50,8 @@ def test_options_are_validated_without_a_gpu():
     state only: no device call is made)."""
     import paper_2111_08824_gb300 as lj
     saved = {k: lj.lj_get_option(k) for k in ("single_pass_max", "host_chunk", "probe_buckets",
-                                              "lookback_polls", "fault_skip_tiles")}
+                                              "lookback_polls", "fault_skip_tiles", "fused_max",
+                                              "fused_groups", "key_levels")}
     try:
         for v in (0, 1, 2):
             lj.lj_set_option("probe_buckets", v)
@@ -59,6 +60,15 @@ def test_options_are_validated_without_a_gpu():
         assert lj.lj_get_option("host_chunk") == 1 << 20
         lj.lj_set_option("single_pass_max", 12345)
         assert lj.lj_get_option("single_pass_max") == 12345
+        assert lj.lj_get_option("fused_max") == 1 << 21          # defaults
+        assert lj.lj_get_option("fused_groups") == 1
+        lj.lj_set_option("fused_max", 0)
+        assert lj.lj_get_option("fused_max") == 0
+        lj.lj_set_option("fused_groups", 0)
+        assert lj.lj_get_option("fused_groups") == 0
+        assert lj.lj_get_option("key_levels") == 0
+        lj.lj_set_option("key_levels", 1)
+        assert lj.lj_get_option("key_levels") == 1
         assert lj.lj_get_option("lookback_polls") == 1 << 20      # default bound
         assert lj.lj_get_option("fault_skip_tiles") == 0          # no fault injected
         lj.lj_set_option("lookback_polls", 256)
@@ -68,7 +78,9 @@ def test_options_are_validated_without_a_gpu():
         for name, bad in (("probe_buckets", 3), ("probe_buckets", -1), ("host_chunk", 100),
                           ("host_chunk", 1 << 33), ("single_pass_max", -1), ("no_such_option", 1),
                           ("lookback_polls", 15), ("lookback_polls", (1 << 20) + 1),
-                          ("fault_skip_tiles", -1), ("fault_skip_tiles", 1025)):
+                          ("fault_skip_tiles", -1), ("fault_skip_tiles", 1025),
+                          ("fused_max", (1 << 22) + 1), ("fused_max", -1), ("fused_groups", 2),
+                          ("key_levels", 2), ("key_levels", -1)):
             with pytest.raises(lj.LJoinError) as e:
                 lj.lj_set_option(name, bad)
             assert e.value.code == -1

@@ -55,6 +55,15 @@ def test_lookback_wait_runs_out_and_reports_timeout():
         # once reported, the error is cleared: the next calls are clean
         assert lj.join_count_noalloc(idx, Sd) == want
         assert lj.join_count(idx, Sd) == want
+        # the fused kernel's grid-wide barrier: a skipped block never arrives,
+        # the other blocks' bounded waits run out
+        lj.lj_set_option("fault_skip_tiles", 1)
+        pairs = torch.empty((S.size, 2), dtype=torch.int32, device="cuda")
+        with pytest.raises(lj.LJoinError) as e:
+            lj.join_emit(idx, Sd, pairs)
+        assert e.value.code == TIMEOUT
+        lj.lj_set_option("fault_skip_tiles", 0)
+        assert lj.join_emit(idx, Sd, pairs) == want
     finally:
         for k, v in old.items():
             lj.lj_set_option(k, v)

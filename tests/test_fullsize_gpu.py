@@ -113,14 +113,20 @@ def test_uniform_1m_full_parity(prec):
     idx = lj.rmi_build(Rd, w.leaves, prec)
     pairs = torch.empty((w.S.size, 2), dtype=torch.int32, device="cuda")
     want = oracle.join_pairs(w.R, w.S)
-    for spm in (0, 1 << 40):       # the pipeline and the fused single-pass kernel
-        old = lj.lj_get_option("single_pass_max")
+    names = ("single_pass_max", "fused_max", "fused_groups")
+    old = [lj.lj_get_option(k) for k in names]
+    # the bench's default (fused cooperative kernel, 4-key groups), the fused
+    # kernel with bisection, the pipeline and the single-pass kernel
+    for spm, fmax, groups in ((0, old[1], 1), (0, old[1], 0), (0, 0, 1), (1 << 40, 0, 1)):
         lj.lj_set_option("single_pass_max", spm)
+        lj.lj_set_option("fused_max", fmax)
+        lj.lj_set_option("fused_groups", groups)
         try:
             pairs.fill_(-1)
             total = lj.join_emit(idx, Sd, pairs)
         finally:
-            lj.lj_set_option("single_pass_max", old)
+            for k, v in zip(names, old):
+                lj.lj_set_option(k, v)
         assert total == w.meta["expected_pairs"] == w.S.size
         assert np.array_equal(pairs[:total].cpu().numpy().view(np.uint32), want)
 

@@ -25,18 +25,34 @@ pytestmark = pytest.mark.gpu
 TOP = np.uint64(2**64 - 1)
 
 
-@pytest.fixture(params=["single_pass", "pipeline", "bucketed", "sortmerge"], autouse=True)
+PATHS = {   # path: (single_pass_max, probe_buckets, fused_max, fused_groups, key_levels)
+    "single_pass": (1 << 40, 0, 0, 1, 0),
+    "pipeline": (0, 0, 0, 1, 1),           # key-level descent (levels_search_kernel)
+    "pipeline_halving": (0, 0, 0, 1, 0),   # halving (probe_search_kernel)
+    "bucketed": (0, 1, 0, 1, 0),
+    "sortmerge": (0, 2, 0, 1, 0),
+    "fused": (0, 0, 1 << 22, 1, 1),        # fused kernel with the key-level descent
+    "fused_g4": (0, 0, 1 << 22, 1, 0),     # ... halving over 4-key groups
+    "fused_halving": (0, 0, 1 << 22, 0, 0),
+}
+_OPTS = ("single_pass_max", "probe_buckets", "fused_max", "fused_groups", "key_levels")
+
+
+@pytest.fixture(params=sorted(PATHS), autouse=True)
 def probe_path(request):
-    """Run every test on each execution path of the probe: the fused kernel,
-    the pipeline in S order, in bucketed probe order and in learned
-    sort-merge order."""
+    """Run every test on each execution path of the probe: the single-pass
+    kernel; the pipeline in S order (key-level descent or halving), in
+    bucketed probe order and in learned sort-merge order; the fused
+    cooperative kernel of small unique batches (key-level descent, halving
+    over 4-key groups, plain halving).  The options apply to the indexes the
+    test builds."""
     import paper_2111_08824_gb300 as lj
-    old = lj.lj_get_option("single_pass_max"), lj.lj_get_option("probe_buckets")
-    lj.lj_set_option("single_pass_max", 1 << 40 if request.param == "single_pass" else 0)
-    lj.lj_set_option("probe_buckets", {"bucketed": 1, "sortmerge": 2}.get(request.param, 0))
+    old = [lj.lj_get_option(k) for k in _OPTS]
+    for k, v in zip(_OPTS, PATHS[request.param]):
+        lj.lj_set_option(k, v)
     yield request.param
-    lj.lj_set_option("single_pass_max", old[0])
-    lj.lj_set_option("probe_buckets", old[1])
+    for k, v in zip(_OPTS, old):
+        lj.lj_set_option(k, v)
 
 
 def _lj():
@@ -122,44 +138,6 @@ def _relation(kind, rng, n):
     raise ValueError(kind)
 
 
-# ------------------------------------------------------------ index build --
-
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("kind", ["uniform", "lognormal", "clusters", "extremes"])
-@pytest.mark.parametrize("L", [1, 7, 4096, 300000])
-def test_rmi_build_parity(kind, L, prec):
-    rng = np.random.default_rng(zlib.crc32(f"{kind}{L}{prec}".encode()))
-    R = _relation(kind, rng, 100000)
-    lj = _lj()
-    idx = lj.rmi_build(dev(R), L, prec)
-    gpu = lj.rmi_export(idx)
-    ora = oracle.rmi_fit(R, L, fp64=(prec == "fp64"))
-    _validate.compare_index(R, gpu, ora, fp64=(prec == "fp64"))
-    st = idx.stats()
-    assert st["unique"] == 1 and st["n"] == R.size and st["leaves"] == L
-
-
-def test_rmi_build_with_duplicates_parity():
-    rng = np.random.default_rng(5)
-    R = np.sort(rng.integers(0, 3000, 200000, dtype=np.uint64))
-    lj = _lj()
-    for prec in ("fp32", "fp64"):
-        idx = lj.rmi_build(dev(R), 1000, prec)
-        assert idx.stats()["unique"] == 0
-        _validate.compare_index(R, lj.rmi_export(idx), oracle.rmi_fit(R, 1000, prec == "fp64"),
-                                prec == "fp64")
-
-
-def test_rmi_build_is_deterministic():
-    rng = np.random.default_rng(6)
-    R = _relation("lognormal", rng, 300000)
-    lj = _lj()
-    a = lj.rmi_export(lj.rmi_build(dev(R), 5000, "fp32"))
-    b = lj.rmi_export(lj.rmi_build(dev(R), 5000, "fp32"))
-    for k in a:
-        assert np.array_equal(a[k], b[k])
-
-
 # ------------------------------------------------------------------ joins --
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -241,6 +219,20 @@ def test_join_many_chunks_ragged():
     check_against_oracle(R, S, 20000, "fp32", "two_pass")
     Ru = np.unique(R)
     check_against_oracle(Ru, S, 20000, "fp32", "fused")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_join_unique_sizes_across_the_grid(prec):
+    """Batch sizes from one probe to 2^22 - 2 against one unique R: one
+    block, several groups of 32 blocks, a full grid of resident blocks with
+    several rounds per thread, odd sizes (a block whose last probe has no
+    partner) -- on every probe path, the fused kernel included."""
+    rng = np.random.default_rng(43)
+    R = np.unique(rng.integers(0, 2**63, 1 << 20, dtype=np.uint64))
+    check_against_oracle(R, R[7:8], 4096, prec, "fused")             # one probe
+    for m in (3, 513, 65537, 1048583, (1 << 22) - 6):                 # + 4 extreme keys
+        S = _probe_mix(rng, R, m)
+        check_against_oracle(R, S, 4096, prec, "fused")
 
 
 def test_join_misaligned_S_uses_scalar_loads():
