@@ -253,8 +253,10 @@ enum {
   LJ_LOOKUP_GRMI = 2,           /* gapped RMI, 4 gaps per key (grmi_build) */
   LJ_LOOKUP_LHASH = 3,          /* learned hash index, 4 slots per key (lhash_build) */
   LJ_LOOKUP_SORTMERGE = 4,      /* bounded search in R, learned sort-merge order (Section 4) */
-  LJ_LOOKUP_RSHASH = 5          /* learned hash with a RadixSpline as the hash, 4 slots per key,
+  LJ_LOOKUP_RSHASH = 5,         /* learned hash with a RadixSpline as the hash, 4 slots per key,
                                    eps 16, 18 radix bits (lhash_build_rs) */
+  LJ_LOOKUP_RMI_LEVELS = 6      /* bounded search in R as a descent of R's key levels
+                                   (option "key_levels"), probes in S order */
 };
 
 /*
@@ -267,7 +269,7 @@ enum {
  * "probe_buckets" option for this index).  The RMI itself is unchanged, so
  * results are the same whatever the choice (Sections 2.D, 3.A, 3.B, 3.C).
  *   choice       receives LJ_LOOKUP_*
- *   ns_per_key   optional: receives the six timings (ns per probe, by LJ_LOOKUP_*)
+ *   ns_per_key   optional: receives the seven timings (ns per probe, by LJ_LOOKUP_*)
  * Synchronises.  Errors: those of grmi_build, lhash_build and join_count.
  */
 int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uint64_t m_sample,
@@ -594,8 +596,12 @@ void join_server_destroy(lj_server* server);
  *                      pipeline's and the fused kernel's bounded searches
  *                      descend it (one 32-byte node per level, about
  *                      log4(window) + 1 loads) instead of halving the window
- *                      (log2).  0 (default): no levels, halving.  Applies to indexes
- *                      built afterwards; results are the same either way.
+ *                      (log2).  2 (default): only for an R with duplicate
+ *                      keys (measured faster there; on unique keys halving
+ *                      shares more of its pivots across a warp).  0: never.
+ *                      Applies to indexes built afterwards (index_autotune
+ *                      also tries the descent, LJ_LOOKUP_RMI_LEVELS);
+ *                      results are the same either way.
  *   "fused_max"        join_emit's direct path (unique R) runs batches of
  *                      at most this many keys in one cooperative kernel of
  *                      resident blocks (0 .. 2^22; default 2^21; a batch

@@ -304,11 +304,11 @@ def lsj_join(R, S, pairs, stream=None) -> int:
     return total.value
 
 
-LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge", "rshash")
+LOOKUPS = ("rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge", "rshash", "rmi_levels")
 
 
 def index_autotune(index: Index, S_sample, stream=None) -> tuple[str, dict]:
-    """Time the six lookup structures on a probe sample and keep the fastest;
+    """Time the seven lookup structures on a probe sample and keep the fastest;
     returns its name and every candidate's ns per probe."""
     _require_cuda_u64(S_sample, "S_sample")
     choice = ctypes.c_int()

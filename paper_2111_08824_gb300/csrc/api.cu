@@ -149,7 +149,7 @@ int lj_set_option(const char* name, int64_t value) {
     return LJ_OK;
   }
   if (!strcmp(name, "key_levels")) {
-    if (value < 0 || value > 1) return fail(LJ_E_INVAL, "key_levels must be 0 or 1");
+    if (value < 0 || value > 2) return fail(LJ_E_INVAL, "key_levels must be 0, 1 or 2");
     set_key_levels((int)value);
     return LJ_OK;
   }

@@ -827,6 +827,11 @@ extern "C" int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uin
   LJ_CUDA(cudaEventCreate(&e1));
   auto setup = [&](int c) -> int {
     index->probe_order = c == LJ_LOOKUP_RMI_BUCKETED ? 1 : c == LJ_LOOKUP_SORTMERGE ? 2 : 0;
+    index->use_levels = 0;
+    if (c == LJ_LOOKUP_RMI_LEVELS) {
+      grmi_release(index);
+      return build_key_levels(index, s);
+    }
     if (c == LJ_LOOKUP_GRMI) return grmi_build(index, 4, stream);
     if (c == LJ_LOOKUP_LHASH) return lhash_build(index, 4, stream);
     if (c == LJ_LOOKUP_RSHASH) return lhash_build_rs(index, 4, 16, 18, stream);
@@ -835,7 +840,7 @@ extern "C" int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uin
   };
   double best = 1e300;
   int best_c = LJ_LOOKUP_RMI, rc = 0;
-  for (int c = LJ_LOOKUP_RMI; c <= LJ_LOOKUP_RSHASH && !rc; ++c) {
+  for (int c = LJ_LOOKUP_RMI; c <= LJ_LOOKUP_RMI_LEVELS && !rc; ++c) {
     if ((rc = setup(c))) break;
     float ms = 1e30f;
     for (int rep = 0; rep < 4 && !rc; ++rep) {
@@ -859,6 +864,12 @@ extern "C" int index_autotune(lj_index* index, const uint64_t* S_sample_dev, uin
   cudaEventDestroy(e1);
   if (!rc) rc = take_device_errors(index->device, s);
   if (!rc) rc = setup(best_c);
+  if (!rc && !index->use_levels && index->levels) {   // levels not chosen: release them
+    cudaStreamSynchronize(s);
+    cudaFree(index->levels);
+    index->levels = nullptr;
+    index->nlev = 0;
+  }
   if (rc) {
     grmi_release(index);
     index->probe_order = -1;

@@ -51,6 +51,7 @@ struct lj_index {
   // R[4^k i] (padded to whole 4-entry nodes) at levels + lev_off[k]
   uint64_t* levels = nullptr;
   uint32_t nlev = 0;
+  int use_levels = 0;            // the pipeline's search descends the levels
   uint32_t lev_off[lj::kMaxLevels + 1] = {};
 };
 
@@ -140,7 +141,8 @@ int get_probe_buckets();
 uint32_t lookback_polls();
 uint32_t fault_skip_tiles();
 
-// Key levels built by rmi_build (option "key_levels": 0 off, 1 on).
+// Key levels built by rmi_build (option "key_levels": 0 never, 1 always,
+// 2 for an R with duplicate keys).
 void set_key_levels(int v);
 int get_key_levels();
 int build_key_levels(lj_index* idx, cudaStream_t s);

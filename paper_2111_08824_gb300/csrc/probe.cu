@@ -965,7 +965,7 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.hn1 = idx->n + 1;
   P.rs = RsDev{idx->rs_x, idx->rs_y, idx->rs_rcp, idx->rs_table, idx->rs_kmin, idx->rs_kmax,
                idx->n, idx->rs_S, idx->rs_shift};
-  P.levels = idx->levels;
+  P.levels = idx->use_levels ? idx->levels : nullptr;
   P.nlev = idx->nlev;
   for (int k = 0; k <= kMaxLevels; ++k) P.lev_off[k] = idx->lev_off[k];
   return P;

@@ -77,7 +77,8 @@ struct ProbeParams {
                            // full occupancy): measured 9% faster than the unconstrained build
 #endif
 #ifndef LJ_LMINB
-#define LJ_LMINB 12        // key-level search kernel: 12 blocks of 128 threads per SM
+#define LJ_LMINB 10        // key-level search kernel: 10 blocks of 128 threads per SM (51
+                           // registers: measured best against 12 and 16 on dup_seqh_50m)
 #endif
 #ifndef LJ_FMINB
 #define LJ_FMINB 4         // fused small-batch kernel: 4 blocks of 256 threads per SM (64

@@ -66,9 +66,10 @@ def test_options_are_validated_without_a_gpu():
         assert lj.lj_get_option("fused_max") == 0
         lj.lj_set_option("fused_groups", 0)
         assert lj.lj_get_option("fused_groups") == 0
-        assert lj.lj_get_option("key_levels") == 0
-        lj.lj_set_option("key_levels", 1)
-        assert lj.lj_get_option("key_levels") == 1
+        assert lj.lj_get_option("key_levels") == 2               # default: R with duplicates
+        for v in (0, 1, 2):
+            lj.lj_set_option("key_levels", v)
+            assert lj.lj_get_option("key_levels") == v
         assert lj.lj_get_option("lookback_polls") == 1 << 20      # default bound
         assert lj.lj_get_option("fault_skip_tiles") == 0          # no fault injected
         lj.lj_set_option("lookback_polls", 256)
@@ -80,7 +81,7 @@ def test_options_are_validated_without_a_gpu():
                           ("lookback_polls", 15), ("lookback_polls", (1 << 20) + 1),
                           ("fault_skip_tiles", -1), ("fault_skip_tiles", 1025),
                           ("fused_max", (1 << 22) + 1), ("fused_max", -1), ("fused_groups", 2),
-                          ("key_levels", 2), ("key_levels", -1)):
+                          ("key_levels", 3), ("key_levels", -1)):
             with pytest.raises(lj.LJoinError) as e:
                 lj.lj_set_option(name, bad)
             assert e.value.code == -1

@@ -149,7 +149,8 @@ def test_autotuner_can_choose_it_and_stays_exact():
     S = _probes(R, 1 << 18, rng)
     idx = lj.rmi_build(dev(R), 4096, "fp32")
     choice, ns = lj.index_autotune(idx, dev(S))
-    assert set(ns) == {"rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge", "rshash"}
+    assert set(ns) == {"rmi", "rmi_bucketed", "grmi", "lhash", "rmi_sortmerge", "rshash",
+                       "rmi_levels"}
     assert all(v > 0 for v in ns.values())
     off = torch.empty(S.size + 1, dtype=torch.int64, device="cuda")
     t = lj.join_count(idx, dev(S), offsets=off)

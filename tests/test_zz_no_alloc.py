@@ -5,8 +5,9 @@ a serving loop with a hard latency budget cannot afford cudaMalloc (which
 can synchronise the device), and a host that hands all device memory to its
 own allocator has none left to give.  join_count_noalloc serves them with
 scratch memory compiled into the library.  This test checks, through the C
-ABI, that two calls in a row give exactly what join_count gives (counts,
-offsets and total are integers, so the comparison is exact), that the
+ABI, that two calls in a row give exactly what join_count gives and what
+the CPU oracle gives (counts, offsets and total are integers, so the
+comparisons are exact), that the
 second call is not disturbed by what the first left in the shared scratch,
 and that batches beyond the scratch's limit are refused.
 
@@ -15,6 +16,8 @@ already run every other test; it also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
+
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,6 +55,13 @@ def test_noalloc_matches_join_count_twice(dups):
         assert got[0] == want[0]
         assert np.array_equal(got[1], want[1])
         assert np.array_equal(got[2], want[2])
+        # and the oracle's (CPU sort-merge join): counts hi - lo, offsets
+        # their exclusive prefix sums, total |J|
+        lo, hi, total = oracle.join_ranges(R, S)
+        cnt = (hi - lo).astype(np.int64)
+        assert got[0] == total
+        assert np.array_equal(got[1].astype(np.int64), cnt)
+        assert got[2][0] == 0 and np.array_equal(np.diff(got[2]), cnt)
 
 
 def test_noalloc_rejects_batches_beyond_its_limit():
