@@ -124,6 +124,12 @@ size_t dyn_batch_scratch_bytes(const BatchJob* jobs, uint32_t k);
 int enqueue_dyn_batch(const BatchJob* jobs, uint32_t k, DynBatchBuffers& buf, char* scratch,
                       uint64_t* written_dev, cudaStream_t s);
 
+// join_emit's direct or two-pass path on stream s (no synchronisation when
+// total_host is NULL); total_dev receives |J|.
+int probe_emit_impl(const lj_index* idx, const uint64_t* S, uint64_t m, const uint64_t* offsets,
+                    lj_pair* pairs, uint64_t cap, uint64_t* total_dev, uint64_t* total_host,
+                    uint32_t s_base, cudaStream_t s);
+
 // Release the gapped arrays of an index (no-op without them).
 void grmi_release(lj_index* idx);
 
@@ -146,6 +152,8 @@ uint32_t fault_skip_tiles();
 void set_key_levels(int v);
 int get_key_levels();
 int build_key_levels(lj_index* idx, cudaStream_t s);
+void set_lev_min_window(uint32_t v);
+uint32_t get_lev_min_window();
 
 // Probe batches of at most this many keys take the single-pass kernel.
 void set_fused_max(uint64_t v);

@@ -10,7 +10,8 @@
 //               (LJ_E_BUDGET); admission is first come, first served.
 //   batching    all requests admitted together form one dynamic batch (one
 //               persistent search launch, one scan, one compaction) on the
-//               slot's stream; requests arriving while batches run are
+//               slot's stream -- a batch of one request takes join_emit's
+//               own kernels instead; requests arriving while batches run are
 //               admitted into the next free slot, so batches overlap on the
 //               device (continuous batching, not a queue in front of a
 //               single worker).
@@ -104,7 +105,7 @@ void complete_slot(lj_server* sv, Slot& sl) {
     sv->keys += r->m;
     sv->t_last = now;
   }
-  lj::scratch_free(sl.scratch, sl.stream);
+  if (sl.scratch) lj::scratch_free(sl.scratch, sl.stream);
   sl.scratch = nullptr;
   sl.reqs.clear();
   sl.busy = false;
@@ -144,12 +145,26 @@ int launch_slot(lj_server* sv, Slot& sl, std::vector<Request*>& batch) {
     r->status = 2;
     r->t_start = Clock::now();
   }
-  const size_t bytes = lj::dyn_batch_scratch_bytes(jobs.data(), (uint32_t)jobs.size());
-  if (lj::scratch_alloc((void**)&sl.scratch, bytes, sl.stream) != cudaSuccess)
-    return lj::fail(LJ_E_NOMEM, "server: no room for a batch's scratch");
-  if (int rc = lj::enqueue_dyn_batch(jobs.data(), (uint32_t)jobs.size(), sl.buf, sl.scratch,
-                                     sl.written_dev, sl.stream))
-    return rc;
+  if (batch.size() == 1) {
+    // a batch of one request: the plain probe's own path (the fused kernel
+    // for small batches, else the search-compaction pipeline), so a request
+    // alone costs what join_emit costs and the slots add the overlap
+    Request* r = batch[0];
+    if (r->m == 0) {
+      if (cudaMemsetAsync(sl.written_dev, 0, 8, sl.stream) != cudaSuccess)
+        return lj::fail(LJ_E_CUDA, "server: cannot enqueue a request");
+    } else if (int rc = lj::probe_emit_impl(jobs[0].idx, r->S, r->m, nullptr, r->pairs, r->m,
+                                            sl.written_dev, nullptr, 0, sl.stream)) {
+      return rc;
+    }
+  } else {
+    const size_t bytes = lj::dyn_batch_scratch_bytes(jobs.data(), (uint32_t)jobs.size());
+    if (lj::scratch_alloc((void**)&sl.scratch, bytes, sl.stream) != cudaSuccess)
+      return lj::fail(LJ_E_NOMEM, "server: no room for a batch's scratch");
+    if (int rc = lj::enqueue_dyn_batch(jobs.data(), (uint32_t)jobs.size(), sl.buf, sl.scratch,
+                                       sl.written_dev, sl.stream))
+      return rc;
+  }
   if (cudaMemcpyAsync(sl.written_host, sl.written_dev, jobs.size() * 8, cudaMemcpyDeviceToHost,
                       sl.stream) != cudaSuccess ||
       cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
