@@ -153,12 +153,6 @@ int lj_set_option(const char* name, int64_t value) {
     set_key_levels((int)value);
     return LJ_OK;
   }
-  if (!strcmp(name, "levels_min_window")) {
-    if (value < 0 || value >= (1ll << 32))
-      return fail(LJ_E_INVAL, "levels_min_window must be in [0, 2^32)");
-    set_lev_min_window((uint32_t)value);
-    return LJ_OK;
-  }
   if (!strcmp(name, "fused_max")) {
     if (value < 0 || value > (1ll << 22))
       return fail(LJ_E_INVAL, "fused_max must be in [0, 2^22]");
@@ -203,7 +197,6 @@ int64_t lj_get_option(const char* name) {
   using namespace lj;
   if (name && !strcmp(name, "single_pass_max")) return (int64_t)get_single_pass_max();
   if (name && !strcmp(name, "key_levels")) return get_key_levels();
-  if (name && !strcmp(name, "levels_min_window")) return get_lev_min_window();
   if (name && !strcmp(name, "fused_max")) return (int64_t)get_fused_max();
   if (name && !strcmp(name, "fused_groups")) return get_fused_groups();
   if (name && !strcmp(name, "profile")) return profiling() ? 1 : 0;

@@ -152,8 +152,6 @@ uint32_t fault_skip_tiles();
 void set_key_levels(int v);
 int get_key_levels();
 int build_key_levels(lj_index* idx, cudaStream_t s);
-void set_lev_min_window(uint32_t v);
-uint32_t get_lev_min_window();
 
 // Probe batches of at most this many keys take the single-pass kernel.
 void set_fused_max(uint64_t v);

@@ -14,10 +14,14 @@
 //              scatter of (key, position) into partition order.  The model
 //              is monotone, so the partitions are key ranges in order.
 //   sort       (Section 4.C) every partition sorted on its own, by (key,
-//              position): one block per partition, a bitonic network in
-//              shared memory (up to kSortCap entries; larger partitions,
-//              e.g. many copies of one key, in global memory).  After this
-//              the relation is globally sorted.
+//              position): one block per partition; in shared memory (up to
+//              kSortCap entries) the partition is split once more, into
+//              buckets by the top bits of its keys' offsets from its smallest
+//              key, and each entry is placed by its rank inside its bucket
+//              (a bitonic network when a bucket is crowded); larger
+//              partitions, e.g. many copies of one key, take a bitonic
+//              network in global memory.  After this the relation is
+//              globally sorted.
 //   join       (Section 4.D, chunked join) R's sorted partitions are cut
 //              into chunks of at most kJoinChunk keys; S's model, queried
 //              with a chunk's first and last key, gives the overlapping
@@ -31,9 +35,11 @@
 // Differences from the paper's CPU design: the sample is evenly spaced and
 // at most 16,384 keys (one block sorts it in shared memory); the partitions
 // are sized for a thread block's shared memory rather than for TLB entries;
-// the per-partition sort is a bitonic network in shared memory rather than
-// AVX registers; no software write-combine buffers (the scatter goes
-// through L2).
+// inside a partition the keys are split further (the paper's idea of
+// sub-partitioning before sorting, taken one level down: by key offset
+// rather than by the model) and ranked in shared memory, with a bitonic
+// network in shared memory (not AVX registers) only for crowded buckets; no
+// software write-combine buffers (the scatter goes through L2).
 #include <algorithm>
 #include <vector>
 
@@ -177,28 +183,134 @@ __global__ void __launch_bounds__(kLBlock)
   pos[at] = (uint32_t)i;
 }
 
-// One block per partition: sort it by (key, position).
+// One block per partition: sort it by (key, position).  Launched twice:
+// CAP = kSortSmall for the partitions of at most kSortSmall entries (48 KB of
+// shared memory, four blocks per SM), CAP = kSortCap for the larger ones
+// (and, above kSortCap, a bitonic network in global memory).  In shared
+// memory the partition is bucketed by the top bits of (key - its smallest
+// key), about 8 entries per bucket, and every entry's rank inside its bucket
+// by (key, position) -- the pairs are all distinct -- gives its final place
+// directly: a handful of barriers instead of the O(log^2) stages of a
+// bitonic network.  A partition with a bucket above kRankMax entries (many
+// equal or clustered keys) goes through the bitonic network instead.
+constexpr uint32_t kSortSmall = 4096;
+constexpr uint32_t kRankMax = 64;
+
+__device__ __forceinline__ uint32_t bitlen64(uint64_t v) { return v ? 64u - __clzll(v) : 0u; }
+
+template <uint32_t CAP>
 __global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ keys,
                                                        uint32_t* __restrict__ pos,
                                                        const uint64_t* __restrict__ off) {
+  constexpr uint32_t kBuckets = CAP / 8;
   extern __shared__ uint64_t sk[];
-  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kSortCap);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + CAP);
+  __shared__ uint32_t s_cur[kBuckets];
+  __shared__ uint32_t s_start[kBuckets + 1];
+  __shared__ uint64_t s_min[16], s_max[16];
+  __shared__ uint32_t s_big;
   const uint64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
   const uint64_t cnt = b - a;
   if (cnt <= 1) return;
-  if (cnt <= kSortCap) {
-    for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+  constexpr uint64_t kLow = CAP == kSortSmall ? 0 : kSortSmall;   // this launch's sizes: (kLow, CAP]
+  if (cnt <= kLow) return;
+  if (cnt > CAP) {
+    if (CAP == kSortSmall) return;                  // the second launch takes it
+    bitonic_kv(keys + a, pos + a, (uint32_t)cnt);   // large partition: in global memory
+    return;
+  }
+  const uint32_t n = (uint32_t)cnt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // smallest and largest key
+  uint64_t lo = ~0ull, hi = 0;
+  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+    const uint64_t x = keys[a + t];
+    lo = x < lo ? x : lo;
+    hi = x > hi ? x : hi;
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const uint64_t l2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)lo, d);
+    const uint64_t h2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)hi, d);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  if (lane == 0) {
+    s_min[warp] = lo;
+    s_max[warp] = hi;
+  }
+  const uint32_t nbits = min(31u - __clz(max(n / 8, 1u)) + 1u, 31u - __clz(kBuckets));
+  const uint32_t nb = 1u << nbits;   // buckets: about 8 entries each, at most kBuckets
+  for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) s_cur[t] = 0;
+  if (threadIdx.x == 0) s_big = 0;
+  __syncthreads();
+  lo = s_min[0];
+  hi = s_max[0];
+  for (uint32_t w = 1; w < blockDim.x / 32; ++w) {
+    lo = s_min[w] < lo ? s_min[w] : lo;
+    hi = s_max[w] > hi ? s_max[w] : hi;
+  }
+  const uint32_t rb = bitlen64(hi - lo);
+  const uint32_t shift = rb > nbits ? rb - nbits : 0u;   // (hi - lo) >> shift < nb
+  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x)
+    atomicAdd(&s_cur[(uint32_t)((keys[a + t] - lo) >> shift)], 1u);
+  __syncthreads();
+  // bucket starts (exclusive scan by warp 0) and the largest bucket
+  if (warp == 0) {
+    uint32_t run = 0, big = 0;
+    for (uint32_t c0 = 0; c0 < nb; c0 += 32) {
+      const uint32_t v = c0 + lane < nb ? s_cur[c0 + lane] : 0u;
+      big = v > big ? v : big;
+      uint32_t inc = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += u;
+      }
+      if (c0 + lane < nb) s_start[c0 + lane] = run + inc - v;
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) big = max(big, __shfl_xor_sync(0xffffffffu, big, d));
+    if (lane == 0) {
+      s_start[nb] = run;
+      s_big = big > kRankMax ? 1u : 0u;
+    }
+  }
+  __syncthreads();
+  if (s_big) {   // a crowded bucket: the bitonic network on the whole partition
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
       sk[t] = keys[a + t];
       sv[t] = pos[a + t];
     }
     __syncthreads();
-    bitonic_kv(sk, sv, (uint32_t)cnt);
-    for (uint32_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+    bitonic_kv(sk, sv, n);
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
       keys[a + t] = sk[t];
       pos[a + t] = sv[t];
     }
-  } else {
-    bitonic_kv(keys + a, pos + a, (uint32_t)cnt);   // large partition: in global memory
+    return;
+  }
+  // scatter into bucket order (any order inside a bucket)
+  for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) s_cur[t] = s_start[t];
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+    const uint64_t x = keys[a + t];
+    const uint32_t q = atomicAdd(&s_cur[(uint32_t)((x - lo) >> shift)], 1u);
+    sk[q] = x;
+    sv[q] = pos[a + t];
+  }
+  __syncthreads();
+  // final place of each entry: its bucket's start + its rank in the bucket
+  for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) {
+    const uint64_t x = sk[q];
+    const uint32_t v = sv[q];
+    const uint32_t bk = (uint32_t)((x - lo) >> shift);
+    const uint32_t s0 = s_start[bk], s1 = s_start[bk + 1];
+    uint32_t r = 0;
+    for (uint32_t j = s0; j < s1; ++j) r += kv_less(sk[j], sv[j], x, v) ? 1u : 0u;
+    keys[a + s0 + r] = x;
+    pos[a + s0 + r] = v;
   }
 }
 
@@ -368,7 +480,10 @@ int sort_relation(const uint64_t* X, uint64_t n, Sorted& out, cudaStream_t s,
   }
   {
     KernelTimer kt("lsj_sort_kernel", s);
-    lsj_sort_kernel<<<out.P, 512, (size_t)kSortCap * 12, s>>>(out.keys, out.pos, out.off);
+    lsj_sort_kernel<kSortSmall><<<out.P, 512, (size_t)kSortSmall * 12, s>>>(out.keys, out.pos,
+                                                                            out.off);
+    lsj_sort_kernel<kSortCap><<<out.P, 512, (size_t)kSortCap * 12, s>>>(out.keys, out.pos,
+                                                                        out.off);
   }
   LJ_CUDA(cudaGetLastError());
   return 0;
@@ -398,8 +513,10 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   // shared memory above 48 KB for the two sorting kernels (on the current device)
   LJ_CUDA(cudaFuncSetAttribute(lsj_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(kSample * 12)));
-  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kSortCap * 12)));
+  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_kernel<kSortSmall>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSortSmall * 12)));
+  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_kernel<kSortCap>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSortCap * 12)));
   Sorted R, S;
   const uint64_t nm = std::max(n, m);
   const uint32_t Pmax = (uint32_t)((nm + kPartKeys - 1) / kPartKeys) + 1;

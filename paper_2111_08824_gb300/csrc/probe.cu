@@ -65,10 +65,6 @@ std::atomic<uint64_t> g_fused_max{1ull << 21};
 std::atomic<int> g_fused_groups{1};
 constexpr uint32_t kFusedMaxPerBlock = 4096;   // probes (words in shared memory) per block
 
-// Windows up to this width are halved even when the index has key levels
-// (option "levels_min_window").
-std::atomic<uint32_t> g_lev_min_window{0};
-
 // Bucketed probe order in the pipeline (option "probe_buckets"; off by
 // default: it pays where probes spread over an R larger than L2, and costs
 // where they concentrate on a few hot regions).
@@ -970,7 +966,6 @@ ProbeParams<Model> make_params(const lj_index* idx, Model model, const uint64_t*
   P.rs = RsDev{idx->rs_x, idx->rs_y, idx->rs_rcp, idx->rs_table, idx->rs_kmin, idx->rs_kmax,
                idx->n, idx->rs_S, idx->rs_shift};
   P.levels = idx->use_levels ? idx->levels : nullptr;
-  P.lev_min_window = g_lev_min_window.load();
   P.nlev = idx->nlev;
   for (int k = 0; k <= kMaxLevels; ++k) P.lev_off[k] = idx->lev_off[k];
   return P;
@@ -1444,8 +1439,6 @@ int probe_expand_impl(const uint32_t* first, const uint64_t* offsets, uint64_t m
 
 void set_probe_buckets(int v) { g_probe_buckets = v; }
 int get_probe_buckets() { return g_probe_buckets; }
-void set_lev_min_window(uint32_t v) { g_lev_min_window = v; }
-uint32_t get_lev_min_window() { return g_lev_min_window; }
 void set_fused_max(uint64_t v) { g_fused_max = v; }
 uint64_t get_fused_max() { return g_fused_max; }
 void set_fused_groups(int v) { g_fused_groups = v; }

@@ -56,7 +56,6 @@ struct ProbeParams {
   // levels + lev_off[k]; nlev levels (0: none)
   const uint64_t* levels;
   uint32_t nlev;
-  uint32_t lev_min_window;   // windows up to this width are halved instead (0: none)
   uint32_t lev_off[kMaxLevels + 1];
 };
 
@@ -306,33 +305,6 @@ __device__ __forceinline__ void search_levels(const P_& P, const uint64_t (&x)[N
   for (int p = 0; p < NP; ++p) len[p] = start[p];
 }
 
-// The key-level descent for windows wider than P.lev_min_window, halving
-// for the others (same contract as search_last).
-template <int NP, bool STRICT, class P_>
-__device__ __forceinline__ void search_levels_wide(const P_& P, const uint64_t (&x)[NP],
-                                                   uint32_t (&base)[NP], uint32_t (&len)[NP],
-                                                   uint64_t (&cv)[NP]) {
-  uint32_t b2[NP], l2[NP];
-  uint64_t c2[NP];
-  bool wide[NP];
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    wide[p] = len[p] > P.lev_min_window;
-    b2[p] = base[p];
-    l2[p] = wide[p] ? len[p] : 0u;
-    if (wide[p]) len[p] = 0;
-  }
-  search_last<NP, STRICT>(P.R, x, base, len, cv);
-  search_levels<NP, STRICT>(P, x, b2, l2, c2);
-#pragma unroll
-  for (int p = 0; p < NP; ++p)
-    if (wide[p]) {
-      base[p] = b2[p];
-      len[p] = l2[p];
-      cv[p] = c2[p];
-    }
-}
-
 // Exponential search of a GRMI (Section 3.A), NP probes interleaved: for
 // each probe p the first slot s >= pos[p] of the sorted gapped key array K
 // (C slots) with K[s] >= x[p] (STRICT: K[s] > x[p]), or C.  Keys at pos,
@@ -534,7 +506,7 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
     for (int p = 0; p < NP; ++p) wh[p] = base[p] + len[p];
     uint64_t cv[NP];
     if (SEARCH == kSearchLevels)
-      search_levels_wide<NP, true>(P, x, base, len, cv);       // base = lower bound
+      search_levels<NP, true>(P, x, base, len, cv);            // base = lower bound
     else if (LJ_GROUP4 && P.r32)
       search_last_g4<NP, true>(P.R, P.n, x, base, len, cv);   // base = lower bound
     else
@@ -546,7 +518,7 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
       len[p] = wh[p] - base[p];
     }
     if (SEARCH == kSearchLevels)
-      search_levels_wide<NP, false>(P, x, base, len, cv);      // base = upper bound
+      search_levels<NP, false>(P, x, base, len, cv);           // base = upper bound
     else if (LJ_GROUP4 && P.r32)
       search_last_g4<NP, false>(P.R, P.n, x, base, len, cv);  // base = upper bound
     else
@@ -559,7 +531,7 @@ __device__ __forceinline__ void lookup_keys(const ProbeParams<Model>& P, const u
   } else {
     uint64_t cv[NP];
     if (SEARCH == kSearchLevels)
-      search_levels_wide<NP, false>(P, x, base, len, cv);     // base = upper bound, len = start
+      search_levels<NP, false>(P, x, base, len, cv);          // base = upper bound, len = start
     else if (SEARCH == kSearchGroups && P.r32)
       search_last_g4<NP, false>(P.R, P.n, x, base, len, cv);  // base = upper bound, len = start
     else
