@@ -3,10 +3,11 @@
 //
 //   model      (Section 4.B, model building) per relation, a sample of up
 //              to kSample keys at evenly spaced positions, sorted in shared
-//              memory by one block, and the two-level linear RMI of this
-//              library fitted over the sorted sample (rmi_build): a CDF
-//              model.  part(x) = min(P - 1, p(x) * P / s), p(x) the model's
-//              predicted position clamped to its leaf (monotone), s the
+//              memory by one block; the CDF model is the piecewise-linear
+//              function through every kKnotGap-th key of the sorted sample
+//              (the empirical CDF of the sample, smoothed).
+//              part(x) = min(P - 1, floor(p(x) * P / s)), p(x) the spline's
+//              position of x in the sample (a real number, monotone), s the
 //              sample size, P the number of partitions (one per kPartKeys
 //              keys on average).
 //   partition  (Section 4.B, range partitioning) each key's partition
@@ -114,23 +115,60 @@ __global__ void __launch_bounds__(1024) lsj_sample_kernel(const uint64_t* __rest
   for (uint32_t t = threadIdx.x; t < s; t += blockDim.x) out[t] = sk[t];
 }
 
-template <class Model>
-__device__ __forceinline__ uint32_t part_of(const Model& m, const typename Model::Leaf* leaves,
-                                            uint64_t x, uint32_t s, uint32_t P) {
-  const uint64_t p = clamped_pos<Model>(Model::load_leaf(leaves, m.leaf(x)), x);   // 0 .. s
-  const uint64_t q = p * P / s;
-  return q < P ? (uint32_t)q : P - 1;
+// CDF model of a relation (Section 4.B): the piecewise-linear function
+// through every kKnotGap-th key of its sorted sample (knot k = sample[k G],
+// the last knot the largest sample key), i.e. the sample's empirical CDF
+// smoothed over kKnotGap sample gaps.  Unlike the clamped prediction of a
+// model with separately fitted pieces it is continuous, so no partition
+// collects the keys of a gap between two pieces.
+struct Spline {
+  const uint64_t* knot;   // K + 1 knot keys, non-decreasing
+  uint32_t K;             // segments
+  uint32_t s;             // sample size (positions 0 .. s - 1)
+};
+constexpr uint32_t kKnotGap = 32;
+
+__device__ __forceinline__ uint32_t knot_pos(const Spline& m, uint32_t k) {
+  return min(k * kKnotGap, m.s - 1);
+}
+
+// Partition of key x: its position in the sample by the spline (a real
+// number in [0, s - 1]), scaled to the P partitions.  Monotone in x (the
+// interpolation within a segment is, and segments meet at the knots), so
+// the partitions are key ranges in key order.
+__device__ __forceinline__ uint32_t part_of(const Spline& m, uint64_t x, uint32_t P) {
+  const uint64_t* kn = m.knot;
+  if (x <= __ldg(reinterpret_cast<const unsigned long long*>(kn))) return 0;
+  if (x >= __ldg(reinterpret_cast<const unsigned long long*>(kn) + m.K)) return P - 1;
+  uint32_t lo = 0, len = m.K;   // last knot <= x: in [0, K)
+  while (len > 1) {
+    const uint32_t h = len >> 1;
+    if (__ldg(reinterpret_cast<const unsigned long long*>(kn) + lo + h) <= x) lo += h;
+    len -= h;
+  }
+  const uint64_t k0 = __ldg(reinterpret_cast<const unsigned long long*>(kn) + lo);
+  const uint64_t k1 = __ldg(reinterpret_cast<const unsigned long long*>(kn) + lo + 1);
+  const float y0 = (float)knot_pos(m, lo), y1 = (float)knot_pos(m, lo + 1);
+  const float f = __fdiv_rn(__ull2float_rn(x - k0), __ull2float_rn(k1 - k0));   // in [0, 1]
+  const float q = __fmul_rn(__fmaf_rn(y1 - y0, f, y0), (float)P / (float)m.s);
+  return q < (float)P ? (uint32_t)q : P - 1;
+}
+
+// Knots of the spline from the sorted sample.
+__global__ void lsj_knots_kernel(const uint64_t* __restrict__ sample, uint32_t s, uint32_t K,
+                                 uint64_t* __restrict__ knot) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x)
+    knot[k] = sample[min(k * kKnotGap, s - 1)];
 }
 
 // Partition of every key and the partition sizes.
-template <class Model>
 __global__ void __launch_bounds__(kLBlock)
-    lsj_hist_kernel(const uint64_t* __restrict__ X, uint64_t n, Model m,
-                    const typename Model::Leaf* leaves, uint32_t s, uint32_t P,
+    lsj_hist_kernel(const uint64_t* __restrict__ X, uint64_t n, Spline m, uint32_t P,
                     uint32_t* __restrict__ pid, unsigned long long* __restrict__ cnt) {
   const uint64_t i = (uint64_t)blockIdx.x * kLBlock + threadIdx.x;
   const bool valid = i < n;
-  const uint32_t p = valid ? part_of(m, leaves, __ldg(reinterpret_cast<const unsigned long long*>(X) + i), s, P) : 0;
+  const uint32_t p =
+      valid ? part_of(m, __ldg(reinterpret_cast<const unsigned long long*>(X) + i), P) : 0;
   const unsigned mask = __ballot_sync(0xffffffffu, valid);
   if (valid) {
     pid[i] = p;
@@ -194,39 +232,50 @@ __global__ void __launch_bounds__(kLBlock)
 // bitonic network.  A partition with a bucket above kRankMax entries (many
 // equal or clustered keys) goes through the bitonic network instead.
 constexpr uint32_t kSortSmall = 4096;
+#ifndef LJ_SORT_THREADS
+#define LJ_SORT_THREADS 512    // threads of the first sort launch: 512 x 3 blocks per SM
+#endif                         // (1.63 ms per 100M keys; 1024 x 2 blocks: 2.33 ms)
+#ifndef LJ_SORT_MINB
+#define LJ_SORT_MINB 3
+#endif
+constexpr uint32_t kSortThreads = LJ_SORT_THREADS;
 constexpr uint32_t kRankMax = 64;
 
 __device__ __forceinline__ uint32_t bitlen64(uint64_t v) { return v ? 64u - __clzll(v) : 0u; }
 
-template <uint32_t CAP>
-__global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ keys,
-                                                       uint32_t* __restrict__ pos,
-                                                       const uint64_t* __restrict__ off) {
+// Sort of one partition [a, a + n) in shared memory (2 <= n <= CAP), by the
+// whole block.  ITEMS > 0: each thread keeps its ITEMS entries (t,
+// t + blockDim.x, ...) in registers, so the partition is read from global
+// memory once.
+template <uint32_t CAP, int ITEMS>
+__device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict__ pos,
+                               uint64_t a, uint32_t n, uint64_t* sk, uint32_t* sv,
+                               uint32_t* s_cur, uint32_t* s_start, uint64_t* s_min,
+                               uint64_t* s_max, uint32_t* s_big) {
   constexpr uint32_t kBuckets = CAP / 8;
-  extern __shared__ uint64_t sk[];
-  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + CAP);
-  __shared__ uint32_t s_cur[kBuckets];
-  __shared__ uint32_t s_start[kBuckets + 1];
-  __shared__ uint64_t s_min[16], s_max[16];
-  __shared__ uint32_t s_big;
-  const uint64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
-  const uint64_t cnt = b - a;
-  if (cnt <= 1) return;
-  constexpr uint64_t kLow = CAP == kSortSmall ? 0 : kSortSmall;   // this launch's sizes: (kLow, CAP]
-  if (cnt <= kLow) return;
-  if (cnt > CAP) {
-    if (CAP == kSortSmall) return;                  // the second launch takes it
-    bitonic_kv(keys + a, pos + a, (uint32_t)cnt);   // large partition: in global memory
-    return;
-  }
-  const uint32_t n = (uint32_t)cnt;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kR = ITEMS > 0 ? ITEMS : 1;
+  uint64_t rk[kR];
+  uint32_t rv[kR];
   // smallest and largest key
   uint64_t lo = ~0ull, hi = 0;
-  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-    const uint64_t x = keys[a + t];
-    lo = x < lo ? x : lo;
-    hi = x > hi ? x : hi;
+  if (ITEMS > 0) {
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      const uint32_t t = threadIdx.x + i * blockDim.x;
+      rk[i] = t < n ? keys[a + t] : 0;
+      rv[i] = t < n ? pos[a + t] : 0;
+      if (t < n) {
+        lo = rk[i] < lo ? rk[i] : lo;
+        hi = rk[i] > hi ? rk[i] : hi;
+      }
+    }
+  } else {
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+      const uint64_t x = keys[a + t];
+      lo = x < lo ? x : lo;
+      hi = x > hi ? x : hi;
+    }
   }
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) {
@@ -240,9 +289,9 @@ __global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ ke
     s_max[warp] = hi;
   }
   const uint32_t nbits = min(31u - __clz(max(n / 8, 1u)) + 1u, 31u - __clz(kBuckets));
-  const uint32_t nb = 1u << nbits;   // buckets: about 8 entries each, at most kBuckets
+  const uint32_t nb = 1u << nbits;   // buckets: about 4 to 8 entries each, at most kBuckets
   for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) s_cur[t] = 0;
-  if (threadIdx.x == 0) s_big = 0;
+  if (threadIdx.x == 0) *s_big = 0;
   __syncthreads();
   lo = s_min[0];
   hi = s_max[0];
@@ -252,8 +301,14 @@ __global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ ke
   }
   const uint32_t rb = bitlen64(hi - lo);
   const uint32_t shift = rb > nbits ? rb - nbits : 0u;   // (hi - lo) >> shift < nb
-  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x)
-    atomicAdd(&s_cur[(uint32_t)((keys[a + t] - lo) >> shift)], 1u);
+  if (ITEMS > 0) {
+#pragma unroll
+    for (int i = 0; i < kR; ++i)
+      if (threadIdx.x + i * blockDim.x < n) atomicAdd(&s_cur[(uint32_t)((rk[i] - lo) >> shift)], 1u);
+  } else {
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x)
+      atomicAdd(&s_cur[(uint32_t)((keys[a + t] - lo) >> shift)], 1u);
+  }
   __syncthreads();
   // bucket starts (exclusive scan by warp 0) and the largest bucket
   if (warp == 0) {
@@ -274,14 +329,25 @@ __global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ ke
     for (int d = 16; d >= 1; d >>= 1) big = max(big, __shfl_xor_sync(0xffffffffu, big, d));
     if (lane == 0) {
       s_start[nb] = run;
-      s_big = big > kRankMax ? 1u : 0u;
+      *s_big = big > kRankMax ? 1u : 0u;
     }
   }
   __syncthreads();
-  if (s_big) {   // a crowded bucket: the bitonic network on the whole partition
-    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-      sk[t] = keys[a + t];
-      sv[t] = pos[a + t];
+  if (*s_big) {   // a crowded bucket: the bitonic network on the whole partition
+    if (ITEMS > 0) {
+#pragma unroll
+      for (int i = 0; i < kR; ++i) {
+        const uint32_t t = threadIdx.x + i * blockDim.x;
+        if (t < n) {
+          sk[t] = rk[i];
+          sv[t] = rv[i];
+        }
+      }
+    } else {
+      for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+        sk[t] = keys[a + t];
+        sv[t] = pos[a + t];
+      }
     }
     __syncthreads();
     bitonic_kv(sk, sv, n);
@@ -289,16 +355,27 @@ __global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ ke
       keys[a + t] = sk[t];
       pos[a + t] = sv[t];
     }
+    __syncthreads();   // shared memory is reused by the block's next partition
     return;
   }
   // scatter into bucket order (any order inside a bucket)
   for (uint32_t t = threadIdx.x; t < nb; t += blockDim.x) s_cur[t] = s_start[t];
   __syncthreads();
-  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-    const uint64_t x = keys[a + t];
-    const uint32_t q = atomicAdd(&s_cur[(uint32_t)((x - lo) >> shift)], 1u);
-    sk[q] = x;
-    sv[q] = pos[a + t];
+  if (ITEMS > 0) {
+#pragma unroll
+    for (int i = 0; i < kR; ++i)
+      if (threadIdx.x + i * blockDim.x < n) {
+        const uint32_t q = atomicAdd(&s_cur[(uint32_t)((rk[i] - lo) >> shift)], 1u);
+        sk[q] = rk[i];
+        sv[q] = rv[i];
+      }
+  } else {
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+      const uint64_t x = keys[a + t];
+      const uint32_t q = atomicAdd(&s_cur[(uint32_t)((x - lo) >> shift)], 1u);
+      sk[q] = x;
+      sv[q] = pos[a + t];
+    }
   }
   __syncthreads();
   // final place of each entry: its bucket's start + its rank in the bucket
@@ -312,6 +389,59 @@ __global__ void __launch_bounds__(512) lsj_sort_kernel(uint64_t* __restrict__ ke
     keys[a + s0 + r] = x;
     pos[a + s0 + r] = v;
   }
+  __syncthreads();   // shared memory is reused by the block's next partition
+}
+
+// First sort launch, one block per partition: partitions of at most
+// kSortSmall entries are sorted here (48 KB of shared memory, entries kept in
+// registers); larger ones are appended to `big` for lsj_sort_big_kernel.
+__global__ void __launch_bounds__(kSortThreads, LJ_SORT_MINB) lsj_sort_kernel(uint64_t* __restrict__ keys,
+                                                           uint32_t* __restrict__ pos,
+                                                           const uint64_t* __restrict__ off,
+                                                           uint32_t* __restrict__ big) {
+  extern __shared__ uint64_t sk[];
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kSortSmall);
+  __shared__ uint32_t s_cur[kSortSmall / 8];
+  __shared__ uint32_t s_start[kSortSmall / 8 + 1];
+  __shared__ uint64_t s_min[32], s_max[32];
+  __shared__ uint32_t s_big;
+  const uint64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+  const uint64_t cnt = b - a;
+  if (cnt <= 1) return;
+  if (cnt > kSortSmall) {
+    if (threadIdx.x == 0) big[1 + atomicAdd(big, 1u)] = blockIdx.x;   // big[0] = count
+    return;
+  }
+  sort_partition<kSortSmall, kSortSmall / kSortThreads>(keys, pos, a, (uint32_t)cnt, sk, sv,
+                                                        s_cur, s_start, s_min, s_max, &s_big);
+}
+
+// Second sort launch: the partitions listed in `big` (more than kSortSmall
+// entries), a few blocks striding over the list; up to kSortCap entries in
+// shared memory, larger ones (e.g. many copies of one key) through a bitonic
+// network in global memory.
+__global__ void __launch_bounds__(512) lsj_sort_big_kernel(uint64_t* __restrict__ keys,
+                                                           uint32_t* __restrict__ pos,
+                                                           const uint64_t* __restrict__ off,
+                                                           const uint32_t* __restrict__ big) {
+  extern __shared__ uint64_t sk[];
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kSortCap);
+  __shared__ uint32_t s_cur[kSortCap / 8];
+  __shared__ uint32_t s_start[kSortCap / 8 + 1];
+  __shared__ uint64_t s_min[16], s_max[16];
+  __shared__ uint32_t s_big;
+  const uint32_t count = big[0];
+  for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const uint32_t part = big[1 + i];
+    const uint64_t a = off[part], cnt = off[part + 1] - a;
+    if (cnt > kSortCap) {
+      bitonic_kv(keys + a, pos + a, (uint32_t)cnt);   // large partition: in global memory
+      __syncthreads();
+    } else {
+      sort_partition<kSortCap, 0>(keys, pos, a, (uint32_t)cnt, sk, sv, s_cur, s_start, s_min,
+                                  s_max, &s_big);
+    }
+  }
 }
 
 // Join work item: R's sorted positions [ra, ra + len) (len <= kJoinChunk, in
@@ -322,11 +452,10 @@ struct JoinItem {
 };
 
 // Items of R's partitions (chunks of kJoinChunk keys) with their S ranges.
-template <class Model>
 __global__ void lsj_items_kernel(const uint64_t* __restrict__ rkeys, const uint64_t* __restrict__ roff,
-                                 uint32_t PR, const uint64_t* __restrict__ item0, Model ms,
-                                 const typename Model::Leaf* sleaves, uint32_t ss, uint32_t PS,
-                                 const uint64_t* __restrict__ soff, JoinItem* __restrict__ items) {
+                                 uint32_t PR, const uint64_t* __restrict__ item0, Spline ms,
+                                 uint32_t PS, const uint64_t* __restrict__ soff,
+                                 JoinItem* __restrict__ items) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < PR; p += gridDim.x * blockDim.x) {
     const uint64_t a = roff[p], b = roff[p + 1];
     uint64_t it = item0[p];
@@ -336,8 +465,8 @@ __global__ void lsj_items_kernel(const uint64_t* __restrict__ rkeys, const uint6
       J.ra = c;
       J.len = (uint32_t)(e - c);
       J.pad = 0;
-      const uint32_t f = part_of(ms, sleaves, rkeys[c], ss, PS);
-      const uint32_t l = part_of(ms, sleaves, rkeys[e - 1], ss, PS);
+      const uint32_t f = part_of(ms, rkeys[c], PS);
+      const uint32_t l = part_of(ms, rkeys[e - 1], PS);
       J.sa = soff[f];
       J.sb = soff[l + 1];
       items[it] = J;
@@ -445,7 +574,8 @@ unsigned blocks_for(uint64_t work, unsigned block) {
 // One relation, partitioned and sorted: keys/pos in sorted order, off[P+1]
 // partition starts, and the model that partitioned it.
 struct Sorted {
-  lj_index* model = nullptr;
+  uint64_t* knot = nullptr;   // the spline's knots (kSample / kKnotGap + 1 at most)
+  uint32_t K = 0;
   uint32_t s = 0, P = 1;
   uint64_t* keys = nullptr;
   uint32_t* pos = nullptr;
@@ -454,23 +584,22 @@ struct Sorted {
 
 int sort_relation(const uint64_t* X, uint64_t n, Sorted& out, cudaStream_t s,
                   uint64_t* sample_buf, uint32_t* pid, unsigned long long* cnt,
-                  unsigned long long* cursor) {
+                  unsigned long long* cursor, uint32_t* big) {
   out.s = (uint32_t)std::min<uint64_t>(n, kSample);
   out.P = (uint32_t)std::max<uint64_t>(1, (n + kPartKeys - 1) / kPartKeys);
-  // model: sorted sample + RMI over it
+  // model: sorted sample, knots of its spline
   const size_t smem = (size_t)kSample * 12;
   lsj_sample_kernel<<<1, 1024, smem, s>>>(X, n, out.s, sample_buf);
   LJ_CUDA(cudaGetLastError());
-  const uint32_t L = std::max<uint32_t>(1, out.s / 32);
-  if (int rc = rmi_build(sample_buf, out.s, L, LJ_FP32, (lj_stream_t)s, &out.model)) return rc;
-  const ModelF32 m = ModelF32::make(out.model->root_f32[0], out.model->root_f32[1], L);
-  const auto* leaves = (const LeafF32*)out.model->leaves;
+  out.K = std::max<uint32_t>(1, (out.s - 1 + kKnotGap - 1) / kKnotGap);
+  lsj_knots_kernel<<<1, 256, 0, s>>>(sample_buf, out.s, out.K, out.knot);
+  LJ_CUDA(cudaGetLastError());
+  const Spline m{out.knot, out.K, out.s};
   LJ_CUDA(cudaMemsetAsync(cnt, 0, (size_t)out.P * 8, s));
   LJ_CUDA(cudaMemsetAsync(cursor, 0, (size_t)out.P * 8, s));
   {
     KernelTimer kt("lsj_hist_kernel", s);
-    lsj_hist_kernel<ModelF32><<<blocks_for(n, kLBlock), kLBlock, 0, s>>>(X, n, m, leaves, out.s,
-                                                                         out.P, pid, cnt);
+    lsj_hist_kernel<<<blocks_for(n, kLBlock), kLBlock, 0, s>>>(X, n, m, out.P, pid, cnt);
   }
   lsj_scan_kernel<<<1, 1024, 0, s>>>(cnt, out.P, out.off);
   {
@@ -478,12 +607,16 @@ int sort_relation(const uint64_t* X, uint64_t n, Sorted& out, cudaStream_t s,
     lsj_scatter_kernel<<<blocks_for(n, kLBlock), kLBlock, 0, s>>>(X, n, pid, out.off, cursor,
                                                                   out.keys, out.pos);
   }
+  LJ_CUDA(cudaMemsetAsync(big, 0, 4, s));
   {
     KernelTimer kt("lsj_sort_kernel", s);
-    lsj_sort_kernel<kSortSmall><<<out.P, 512, (size_t)kSortSmall * 12, s>>>(out.keys, out.pos,
-                                                                            out.off);
-    lsj_sort_kernel<kSortCap><<<out.P, 512, (size_t)kSortCap * 12, s>>>(out.keys, out.pos,
-                                                                        out.off);
+    lsj_sort_kernel<<<out.P, kSortThreads, (size_t)kSortSmall * 12, s>>>(out.keys, out.pos,
+                                                                        out.off, big);
+  }
+  {
+    KernelTimer kt("lsj_sort_big_kernel", s);
+    lsj_sort_big_kernel<<<std::min<uint32_t>(out.P, 304), 512, (size_t)kSortCap * 12, s>>>(
+        out.keys, out.pos, out.off, big);
   }
   LJ_CUDA(cudaGetLastError());
   return 0;
@@ -513,10 +646,10 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   // shared memory above 48 KB for the two sorting kernels (on the current device)
   LJ_CUDA(cudaFuncSetAttribute(lsj_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(kSample * 12)));
-  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_kernel<kSortSmall>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSortSmall * 12)));
-  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_kernel<kSortCap>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kSortCap * 12)));
+  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSortSmall * 12)));
+  LJ_CUDA(cudaFuncSetAttribute(lsj_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSortCap * 12)));
   Sorted R, S;
   const uint64_t nm = std::max(n, m);
   const uint32_t Pmax = (uint32_t)((nm + kPartKeys - 1) / kPartKeys) + 1;
@@ -524,7 +657,10 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   const size_t b_sample = round256((size_t)kSample * 8);
   const size_t b_pid = round256(nm * 4);
   const size_t b_cnt = round256((size_t)Pmax * 8);
-  const size_t total = b_sample + b_pid + 2 * b_cnt + 2 * round256(((size_t)Pmax + 1) * 8) +
+  const size_t b_big = round256(((size_t)Pmax + 1) * 4);
+  const size_t b_knot = round256(((size_t)kSample / kKnotGap + 2) * 8);
+  const size_t total = b_sample + b_pid + 2 * b_cnt + b_big + 2 * b_knot +
+                       2 * round256(((size_t)Pmax + 1) * 8) +
                        round256(n * 8) + round256(n * 4) + round256(m * 8) + round256(m * 4);
   char* ws = nullptr;
   LJ_CUDA(scratch_alloc((void**)&ws, total, s));
@@ -538,6 +674,9 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   uint32_t* pid = (uint32_t*)take(b_pid);
   unsigned long long* cnt = (unsigned long long*)take(b_cnt);
   unsigned long long* cursor = (unsigned long long*)take(b_cnt);
+  uint32_t* big = (uint32_t*)take(b_big);   // [0] count, then partition ids
+  R.knot = (uint64_t*)take(b_knot);
+  S.knot = (uint64_t*)take(b_knot);
   R.off = (uint64_t*)take(round256(((size_t)Pmax + 1) * 8));
   S.off = (uint64_t*)take(round256(((size_t)Pmax + 1) * 8));
   R.keys = (uint64_t*)take(round256(n * 8));
@@ -549,10 +688,10 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   char* ws2 = nullptr;
   do {
     // S first (its model is queried by the join), then R; the sample buffer
-    // is reused, so each model is built (and the sample copied) before the
+    // is reused, so each model's knots are taken (copied) before the
     // next relation's sample is drawn
-    if ((rc = sort_relation(S_dev, m, S, s, sample, pid, cnt, cursor))) break;
-    if ((rc = sort_relation(R_dev, n, R, s, sample, pid, cnt, cursor))) break;
+    if ((rc = sort_relation(S_dev, m, S, s, sample, pid, cnt, cursor, big))) break;
+    if ((rc = sort_relation(R_dev, n, R, s, sample, pid, cnt, cursor, big))) break;
     // join items: chunks of R's partitions
     std::vector<uint64_t> roff(R.P + 1);
     cudaError_t ce = cudaMemcpyAsync(roff.data(), R.off, (R.P + 1) * 8, cudaMemcpyDeviceToHost, s);
@@ -586,11 +725,11 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
       rc = fail_cuda(ce, "lsj_join: item table");
       break;
     }
-    const ModelF32 ms = ModelF32::make(S.model->root_f32[0], S.model->root_f32[1], S.model->L);
+    const Spline ms{S.knot, S.K, S.s};
     {
       KernelTimer kt("lsj_items_kernel", s);
-      lsj_items_kernel<ModelF32><<<blocks_for(R.P, 256), 256, 0, s>>>(
-          R.keys, R.off, R.P, d_item0, ms, (const LeafF32*)S.model->leaves, S.s, S.P, S.off, items);
+      lsj_items_kernel<<<blocks_for(R.P, 256), 256, 0, s>>>(R.keys, R.off, R.P, d_item0, ms,
+                                                            S.P, S.off, items);
     }
     {
       KernelTimer kt("lsj_join_count_kernel", s);
@@ -623,8 +762,6 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   if (ws2) scratch_free(ws2, s);
   scratch_free(ws, s);
   cudaStreamSynchronize(s);
-  rmi_free(R.model);
-  rmi_free(S.model);
   if (!rc) rc = take_device_errors(current_device(), s);
   return rc;
 }
