@@ -173,8 +173,9 @@ typedef struct {
  * From then on join_count, join_emit and join_host on this index look keys
  * up by exponential search from the predicted slot (keys at q, q+1, q+3,
  * q+7, ... then a binary search); results are identical to the plain RMI's.
- * The batched and serving paths and join_count_noalloc reject a gapped index
- * (LJ_E_INVAL).  Rebuilding replaces the arrays.  Not safe while a join on
+ * The batched path and join_count_noalloc reject a gapped index
+ * (LJ_E_INVAL); the serving path runs each request to such a relation alone,
+ * with join_emit's kernels.  Rebuilding replaces the arrays.  Not safe while a join on
  * the index is in flight.  Synchronises `stream`.
  * Errors: LJ_E_INVAL (NULL index, gaps > 16, C too large), LJ_E_NOMEM,
  * LJ_E_CUDA.
@@ -542,18 +543,21 @@ typedef struct {
  * batching.  Each request is one join (Section 2.A probe of its keys against
  * a resident relation's index, Section 2.D), answered exactly as join_emit
  * would answer it alone.  The budget covers the registered relations (their
- * keys and leaf records, charged when added) and the requests in flight.  A
- * scheduler thread admits pending requests first come, first served, when an
- * in-flight slot is free and the memory they need (12 bytes per probe: 8 for
- * pairs, 4 for search words) fits what the budget has left;
- * every admitted group runs as one batched launch on its slot's stream, so
- * batches admitted while others run overlap on the device.
+ * keys, leaf records and any gapped or hash arrays, charged when added) and
+ * the requests in flight.  A scheduler thread admits pending requests first
+ * come, first served, when an in-flight slot is free and the memory they
+ * need (12 bytes per probe: 8 for pairs, 4 for search words) fits what the
+ * budget has left; every admitted group runs as one batched launch on its
+ * slot's stream -- a group of one request, and every request to a relation
+ * with gapped or hash arrays (which always runs alone), with join_emit's own
+ * kernels -- so batches admitted while others run overlap on the device.
  *
  * join_server_create   start a server on the current device.
  * join_server_add_relation  register a built index (unique R, one precision
- *                      for all relations; borrowed); returns its id.
- *                      LJ_E_BUDGET if its keys and leaf records do not fit
- *                      the budget left.
+ *                      for all relations; borrowed; gapped or hash arrays
+ *                      allowed, not to be rebuilt or dropped while
+ *                      registered); returns its id.  LJ_E_BUDGET if its keys,
+ *                      leaf records and arrays do not fit the budget left.
  * join_submit          queue a request: m probe keys at S (device or
  *                      page-locked host memory, valid until the request
  *                      completes).  Returns at once.  LJ_E_BUDGET if the

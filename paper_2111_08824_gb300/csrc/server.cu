@@ -11,7 +11,10 @@
 //   batching    all requests admitted together form one dynamic batch (one
 //               persistent search launch, one scan, one compaction) on the
 //               slot's stream -- a batch of one request takes join_emit's
-//               own kernels instead; requests arriving while batches run are
+//               own kernels instead, and so does every request to a
+//               relation with gapped or hash arrays (grmi_build,
+//               lhash_build, lhash_build_rs), always alone; requests
+//               arriving while batches run are
 //               admitted into the next free slot, so batches overlap on the
 //               device (continuous batching, not a queue in front of a
 //               single worker).
@@ -189,11 +192,16 @@ void scheduler(lj_server* sv) {
       std::vector<Request*> batch;
       while (!sv->pending.empty() && batch.size() < sv->cfg.max_batch) {
         Request* r = sv->pending.front();
+        // a relation with gapped or hash arrays is probed by join_emit's own
+        // kernels: its requests run as batches of one
+        const bool alone = sv->rels[r->rel]->gkeys != nullptr;
+        if (alone && !batch.empty()) break;
         if (sv->mem_in_use + r->need > sv->cfg.hbm_budget_bytes) break;
         sv->pending.pop_front();
         sv->mem_in_use += r->need;
         sv->mem_peak = std::max(sv->mem_peak, sv->mem_in_use);
         batch.push_back(r);
+        if (alone) break;
       }
       if (batch.empty()) break;
       if (int rc = launch_slot(sv, sl, batch)) {
@@ -269,14 +277,21 @@ int join_server_add_relation(lj_server* sv, const lj_index* index, uint32_t* rel
   using namespace lj;
   if (!sv || !index || !rel_id) return fail(LJ_E_INVAL, "join_server_add_relation: NULL argument");
   if (!index->unique) return fail(LJ_E_NOTUNIQUE, "served relations need an R without duplicates");
-  if (index->gkeys) return fail(LJ_E_INVAL, "served relations cannot have gapped arrays (grmi_build)");
   if (index->device != sv->device) return fail(LJ_E_INVAL, "relation on another device");
   std::lock_guard<std::mutex> lk(sv->mu);
   if (!sv->rels.empty() && sv->rels[0]->precision != index->precision)
     return fail(LJ_E_INVAL, "served relations must share one precision");
-  // the resident relation (its keys and its leaf records) counts against the budget
+  // the resident relation (its keys, its leaf records and any gapped or
+  // hash arrays) counts against the budget
   const uint64_t rec = index->precision == LJ_FP64 ? sizeof(lj::LeafF64) : sizeof(lj::LeafF32);
-  const uint64_t bytes = index->n * 8 + (uint64_t)index->L * rec;
+  uint64_t bytes = index->n * 8 + (uint64_t)index->L * rec;
+  if (index->gkeys) {
+    bytes += (uint64_t)index->gslots * 8;                                   // keys
+    bytes += index->gkind == 0 ? ((uint64_t)index->gslots + 1) * 4          // GRMI payloads
+                               : (uint64_t)index->gslots * 8 + (index->ndistinct + 1) * 4;
+    if (index->gkind == 2)   // RadixSpline: points, reciprocals, radix table
+      bytes += (uint64_t)index->rs_S * 20 + ((1ull << index->rs_rbits) + 1) * 4;
+  }
   if (sv->mem_in_use + bytes > sv->cfg.hbm_budget_bytes)
     return fail(LJ_E_BUDGET, "join_server_add_relation: %llu resident bytes exceed the HBM budget",
                 (unsigned long long)bytes);

@@ -129,3 +129,49 @@ def test_budget_admission_rejection_and_timeout():
         assert st["rejected"] == 1 and st["completed"] == 2 and st["mem_peak"] <= budget
     finally:
         srv.close()
+
+
+def test_gapped_and_hash_relations_are_served_alone_and_exactly():
+    """Relations with a gapped RMI, a learned hash (RMI or RadixSpline as the
+    hash) and none, served together: requests to the first three run alone
+    with join_emit's kernels, the others in batches; every result equals
+    join_emit's for the request alone and the oracle's, and the arrays are
+    charged to the budget while the relations are registered."""
+    lj = _lj()
+    rels, idx = _relations(lj, k=4, seed=19)
+    lj.grmi_build(idx[0], 4)
+    lj.lhash_build(idx[1], 4)
+    lj.lhash_build_rs(idx[2], 4, 16, 18)
+    srv = lj.Server(hbm_budget_bytes=8 << 30, streams=3, max_batch=32)
+    try:
+        rids = [srv.add_relation(ix) for ix in idx]
+        plain = rels[3].numel() * 8 + idx[3].leaves * 32
+        st = srv.stats()
+        # the gapped and hash arrays are part of the resident bytes
+        assert st["resident"] > sum(R.numel() * 8 + ix.leaves * 32 for R, ix in zip(rels, idx))
+        assert st["resident"] > plain
+        rng = np.random.default_rng(23)
+        reqs = []
+        for q in range(64):
+            r = int(rng.integers(0, len(rels)))
+            m = int(np.exp(rng.uniform(np.log(500), np.log(100_000))))
+            reqs.append((r, _request(rels[r], m, 700 + q)))
+        torch.cuda.synchronize()
+        tickets = [srv.submit(rids[r], S) for r, S in reqs]
+        for q, (r, S) in enumerate(reqs):
+            res = srv.wait(tickets[q], timeout_us=30_000_000)
+            assert res["status"] == 0
+            out = torch.empty((max(res["pairs"], 1), 2), dtype=torch.int32, device="cuda")
+            srv.fetch(tickets[q], out)
+            torch.cuda.synchronize()
+            got = out[: res["pairs"]].cpu()
+            assert torch.equal(got, _alone(lj, idx[r], S))
+            want = oracle.join_pairs(rels[r].cpu().numpy().view(np.uint64),
+                                     S.cpu().numpy().view(np.uint64))
+            assert np.array_equal(got.numpy().view(np.uint32), want)
+            srv.release(tickets[q])
+        st = srv.stats()
+        assert st["completed"] == len(reqs)
+        assert st["mem_in_use"] == st["resident"]
+    finally:
+        srv.close()
