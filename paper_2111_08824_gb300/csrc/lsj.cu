@@ -201,11 +201,12 @@ __global__ void __launch_bounds__(1024) lsj_scan_kernel(const unsigned long long
   if (threadIdx.x == 1023) off[P] = s[1023];
 }
 
-// (key, position) into its partition's next free slot.
+// (key, position) into its partition's next free slot, as one 16-byte
+// record (one scattered store per key instead of two).
 __global__ void __launch_bounds__(kLBlock)
     lsj_scatter_kernel(const uint64_t* __restrict__ X, uint64_t n, const uint32_t* __restrict__ pid,
                        const uint64_t* __restrict__ off, unsigned long long* __restrict__ cursor,
-                       uint64_t* __restrict__ keys, uint32_t* __restrict__ pos) {
+                       ulonglong2* __restrict__ rec) {
   const uint64_t i = (uint64_t)blockIdx.x * kLBlock + threadIdx.x;
   const bool valid = i < n;
   const uint32_t p = valid ? pid[i] : 0;
@@ -217,8 +218,7 @@ __global__ void __launch_bounds__(kLBlock)
   if (lane == leader) base = atomicAdd(cursor + p, (unsigned long long)__popc(grp));
   base = __shfl_sync(grp, base, leader);
   const uint64_t at = off[p] + base + __popc(grp & ((1u << lane) - 1u));
-  keys[at] = X[i];
-  pos[at] = (uint32_t)i;
+  rec[at] = make_ulonglong2(X[i], i);   // one 16-byte store per key
 }
 
 // One block per partition: sort it by (key, position).  Launched twice:
@@ -248,8 +248,9 @@ __device__ __forceinline__ uint32_t bitlen64(uint64_t v) { return v ? 64u - __cl
 // t + blockDim.x, ...) in registers, so the partition is read from global
 // memory once.
 template <uint32_t CAP, int ITEMS>
-__device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict__ pos,
-                               uint64_t a, uint32_t n, uint64_t* sk, uint32_t* sv,
+__device__ void sort_partition(const ulonglong2* __restrict__ rec, uint64_t* __restrict__ keys,
+                               uint32_t* __restrict__ pos, uint64_t a, uint32_t n, uint64_t* sk,
+                               uint32_t* sv,
                                uint32_t* s_cur, uint32_t* s_start, uint64_t* s_min,
                                uint64_t* s_max, uint32_t* s_big) {
   constexpr uint32_t kBuckets = CAP / 8;
@@ -263,8 +264,9 @@ __device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict
 #pragma unroll
     for (int i = 0; i < kR; ++i) {
       const uint32_t t = threadIdx.x + i * blockDim.x;
-      rk[i] = t < n ? keys[a + t] : 0;
-      rv[i] = t < n ? pos[a + t] : 0;
+      const ulonglong2 e = t < n ? rec[a + t] : make_ulonglong2(0, 0);
+      rk[i] = e.x;
+      rv[i] = (uint32_t)e.y;
       if (t < n) {
         lo = rk[i] < lo ? rk[i] : lo;
         hi = rk[i] > hi ? rk[i] : hi;
@@ -272,7 +274,7 @@ __device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict
     }
   } else {
     for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-      const uint64_t x = keys[a + t];
+      const uint64_t x = rec[a + t].x;
       lo = x < lo ? x : lo;
       hi = x > hi ? x : hi;
     }
@@ -307,7 +309,7 @@ __device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict
       if (threadIdx.x + i * blockDim.x < n) atomicAdd(&s_cur[(uint32_t)((rk[i] - lo) >> shift)], 1u);
   } else {
     for (uint32_t t = threadIdx.x; t < n; t += blockDim.x)
-      atomicAdd(&s_cur[(uint32_t)((keys[a + t] - lo) >> shift)], 1u);
+      atomicAdd(&s_cur[(uint32_t)((rec[a + t].x - lo) >> shift)], 1u);
   }
   __syncthreads();
   // bucket starts (exclusive scan by warp 0) and the largest bucket
@@ -345,8 +347,9 @@ __device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict
       }
     } else {
       for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-        sk[t] = keys[a + t];
-        sv[t] = pos[a + t];
+        const ulonglong2 e = rec[a + t];
+        sk[t] = e.x;
+        sv[t] = (uint32_t)e.y;
       }
     }
     __syncthreads();
@@ -371,10 +374,10 @@ __device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict
       }
   } else {
     for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-      const uint64_t x = keys[a + t];
-      const uint32_t q = atomicAdd(&s_cur[(uint32_t)((x - lo) >> shift)], 1u);
-      sk[q] = x;
-      sv[q] = pos[a + t];
+      const ulonglong2 e = rec[a + t];
+      const uint32_t q = atomicAdd(&s_cur[(uint32_t)((e.x - lo) >> shift)], 1u);
+      sk[q] = e.x;
+      sv[q] = (uint32_t)e.y;
     }
   }
   __syncthreads();
@@ -395,10 +398,10 @@ __device__ void sort_partition(uint64_t* __restrict__ keys, uint32_t* __restrict
 // First sort launch, one block per partition: partitions of at most
 // kSortSmall entries are sorted here (48 KB of shared memory, entries kept in
 // registers); larger ones are appended to `big` for lsj_sort_big_kernel.
-__global__ void __launch_bounds__(kSortThreads, LJ_SORT_MINB) lsj_sort_kernel(uint64_t* __restrict__ keys,
-                                                           uint32_t* __restrict__ pos,
-                                                           const uint64_t* __restrict__ off,
-                                                           uint32_t* __restrict__ big) {
+__global__ void __launch_bounds__(kSortThreads, LJ_SORT_MINB)
+    lsj_sort_kernel(const ulonglong2* __restrict__ rec, uint64_t* __restrict__ keys,
+                    uint32_t* __restrict__ pos, const uint64_t* __restrict__ off,
+                    uint32_t* __restrict__ big) {
   extern __shared__ uint64_t sk[];
   uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kSortSmall);
   __shared__ uint32_t s_cur[kSortSmall / 8];
@@ -407,12 +410,19 @@ __global__ void __launch_bounds__(kSortThreads, LJ_SORT_MINB) lsj_sort_kernel(ui
   __shared__ uint32_t s_big;
   const uint64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
   const uint64_t cnt = b - a;
-  if (cnt <= 1) return;
+  if (cnt <= 1) {   // nothing to sort; a lone record is copied out
+    if (cnt == 1 && threadIdx.x == 0) {
+      const ulonglong2 e = rec[a];
+      keys[a] = e.x;
+      pos[a] = (uint32_t)e.y;
+    }
+    return;
+  }
   if (cnt > kSortSmall) {
     if (threadIdx.x == 0) big[1 + atomicAdd(big, 1u)] = blockIdx.x;   // big[0] = count
     return;
   }
-  sort_partition<kSortSmall, kSortSmall / kSortThreads>(keys, pos, a, (uint32_t)cnt, sk, sv,
+  sort_partition<kSortSmall, kSortSmall / kSortThreads>(rec, keys, pos, a, (uint32_t)cnt, sk, sv,
                                                         s_cur, s_start, s_min, s_max, &s_big);
 }
 
@@ -420,10 +430,10 @@ __global__ void __launch_bounds__(kSortThreads, LJ_SORT_MINB) lsj_sort_kernel(ui
 // entries), a few blocks striding over the list; up to kSortCap entries in
 // shared memory, larger ones (e.g. many copies of one key) through a bitonic
 // network in global memory.
-__global__ void __launch_bounds__(512) lsj_sort_big_kernel(uint64_t* __restrict__ keys,
-                                                           uint32_t* __restrict__ pos,
-                                                           const uint64_t* __restrict__ off,
-                                                           const uint32_t* __restrict__ big) {
+__global__ void __launch_bounds__(512)
+    lsj_sort_big_kernel(const ulonglong2* __restrict__ rec, uint64_t* __restrict__ keys,
+                        uint32_t* __restrict__ pos, const uint64_t* __restrict__ off,
+                        const uint32_t* __restrict__ big) {
   extern __shared__ uint64_t sk[];
   uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kSortCap);
   __shared__ uint32_t s_cur[kSortCap / 8];
@@ -434,11 +444,17 @@ __global__ void __launch_bounds__(512) lsj_sort_big_kernel(uint64_t* __restrict_
   for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
     const uint32_t part = big[1 + i];
     const uint64_t a = off[part], cnt = off[part + 1] - a;
-    if (cnt > kSortCap) {
-      bitonic_kv(keys + a, pos + a, (uint32_t)cnt);   // large partition: in global memory
+    if (cnt > kSortCap) {   // large partition: a bitonic network in global memory
+      for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const ulonglong2 e = rec[a + t];
+        keys[a + t] = e.x;
+        pos[a + t] = (uint32_t)e.y;
+      }
+      __syncthreads();
+      bitonic_kv(keys + a, pos + a, (uint32_t)cnt);
       __syncthreads();
     } else {
-      sort_partition<kSortCap, 0>(keys, pos, a, (uint32_t)cnt, sk, sv, s_cur, s_start, s_min,
+      sort_partition<kSortCap, 0>(rec, keys, pos, a, (uint32_t)cnt, sk, sv, s_cur, s_start, s_min,
                                   s_max, &s_big);
     }
   }
@@ -584,7 +600,7 @@ struct Sorted {
 
 int sort_relation(const uint64_t* X, uint64_t n, Sorted& out, cudaStream_t s,
                   uint64_t* sample_buf, uint32_t* pid, unsigned long long* cnt,
-                  unsigned long long* cursor, uint32_t* big) {
+                  unsigned long long* cursor, uint32_t* big, ulonglong2* rec) {
   out.s = (uint32_t)std::min<uint64_t>(n, kSample);
   out.P = (uint32_t)std::max<uint64_t>(1, (n + kPartKeys - 1) / kPartKeys);
   // model: sorted sample, knots of its spline
@@ -605,18 +621,18 @@ int sort_relation(const uint64_t* X, uint64_t n, Sorted& out, cudaStream_t s,
   {
     KernelTimer kt("lsj_scatter_kernel", s);
     lsj_scatter_kernel<<<blocks_for(n, kLBlock), kLBlock, 0, s>>>(X, n, pid, out.off, cursor,
-                                                                  out.keys, out.pos);
+                                                                  rec);
   }
   LJ_CUDA(cudaMemsetAsync(big, 0, 4, s));
   {
     KernelTimer kt("lsj_sort_kernel", s);
-    lsj_sort_kernel<<<out.P, kSortThreads, (size_t)kSortSmall * 12, s>>>(out.keys, out.pos,
+    lsj_sort_kernel<<<out.P, kSortThreads, (size_t)kSortSmall * 12, s>>>(rec, out.keys, out.pos,
                                                                         out.off, big);
   }
   {
     KernelTimer kt("lsj_sort_big_kernel", s);
     lsj_sort_big_kernel<<<std::min<uint32_t>(out.P, 304), 512, (size_t)kSortCap * 12, s>>>(
-        out.keys, out.pos, out.off, big);
+        rec, out.keys, out.pos, out.off, big);
   }
   LJ_CUDA(cudaGetLastError());
   return 0;
@@ -659,7 +675,8 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   const size_t b_cnt = round256((size_t)Pmax * 8);
   const size_t b_big = round256(((size_t)Pmax + 1) * 4);
   const size_t b_knot = round256(((size_t)kSample / kKnotGap + 2) * 8);
-  const size_t total = b_sample + b_pid + 2 * b_cnt + b_big + 2 * b_knot +
+  const size_t b_rec = round256(nm * 16);
+  const size_t total = b_sample + b_pid + 2 * b_cnt + b_big + 2 * b_knot + b_rec +
                        2 * round256(((size_t)Pmax + 1) * 8) +
                        round256(n * 8) + round256(n * 4) + round256(m * 8) + round256(m * 4);
   char* ws = nullptr;
@@ -677,6 +694,7 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   uint32_t* big = (uint32_t*)take(b_big);   // [0] count, then partition ids
   R.knot = (uint64_t*)take(b_knot);
   S.knot = (uint64_t*)take(b_knot);
+  ulonglong2* rec = (ulonglong2*)take(b_rec);   // partitioned (key, position) records
   R.off = (uint64_t*)take(round256(((size_t)Pmax + 1) * 8));
   S.off = (uint64_t*)take(round256(((size_t)Pmax + 1) * 8));
   R.keys = (uint64_t*)take(round256(n * 8));
@@ -690,8 +708,8 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
     // S first (its model is queried by the join), then R; the sample buffer
     // is reused, so each model's knots are taken (copied) before the
     // next relation's sample is drawn
-    if ((rc = sort_relation(S_dev, m, S, s, sample, pid, cnt, cursor, big))) break;
-    if ((rc = sort_relation(R_dev, n, R, s, sample, pid, cnt, cursor, big))) break;
+    if ((rc = sort_relation(S_dev, m, S, s, sample, pid, cnt, cursor, big, rec))) break;
+    if ((rc = sort_relation(R_dev, n, R, s, sample, pid, cnt, cursor, big, rec))) break;
     // join items: chunks of R's partitions
     std::vector<uint64_t> roff(R.P + 1);
     cudaError_t ce = cudaMemcpyAsync(roff.data(), R.off, (R.P + 1) * 8, cudaMemcpyDeviceToHost, s);
