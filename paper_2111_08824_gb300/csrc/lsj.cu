@@ -123,10 +123,13 @@ __global__ void __launch_bounds__(1024) lsj_sample_kernel(const uint64_t* __rest
 // collects the keys of a gap between two pieces.
 struct Spline {
   const uint64_t* knot;   // K + 1 knot keys, non-decreasing
+  const uint32_t* table;  // radix table: 2^kRadixBits + 1 entries
   uint32_t K;             // segments
   uint32_t s;             // sample size (positions 0 .. s - 1)
+  uint32_t shift;         // prefix of x = (x - knot[0]) >> shift
 };
 constexpr uint32_t kKnotGap = 32;
+constexpr uint32_t kRadixBits = 12;
 
 __device__ __forceinline__ uint32_t knot_pos(const Spline& m, uint32_t k) {
   return min(k * kKnotGap, m.s - 1);
@@ -140,7 +143,10 @@ __device__ __forceinline__ uint32_t part_of(const Spline& m, uint64_t x, uint32_
   const uint64_t* kn = m.knot;
   if (x <= __ldg(reinterpret_cast<const unsigned long long*>(kn))) return 0;
   if (x >= __ldg(reinterpret_cast<const unsigned long long*>(kn) + m.K)) return P - 1;
-  uint32_t lo = 0, len = m.K;   // last knot <= x: in [0, K)
+  // last knot <= x: the knots with x's prefix (table) and the one before them
+  const uint32_t b = (uint32_t)((x - __ldg(reinterpret_cast<const unsigned long long*>(kn))) >> m.shift);
+  const uint32_t t0 = __ldg(m.table + b), t1 = __ldg(m.table + b + 1);
+  uint32_t lo = t0 ? t0 - 1 : 0, len = min(t1, m.K) - lo;
   while (len > 1) {
     const uint32_t h = len >> 1;
     if (__ldg(reinterpret_cast<const unsigned long long*>(kn) + lo + h) <= x) lo += h;
@@ -154,11 +160,24 @@ __device__ __forceinline__ uint32_t part_of(const Spline& m, uint64_t x, uint32_
   return q < (float)P ? (uint32_t)q : P - 1;
 }
 
-// Knots of the spline from the sorted sample.
+// Knots of the spline from the sorted sample, and the radix table over their
+// prefixes: table[b] = the number of knots whose prefix is below b, for
+// b = 0 .. 2^kRadixBits (knot k fills the entries after its predecessor's
+// prefix up to its own).  One block.
 __global__ void lsj_knots_kernel(const uint64_t* __restrict__ sample, uint32_t s, uint32_t K,
-                                 uint64_t* __restrict__ knot) {
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x)
-    knot[k] = sample[min(k * kKnotGap, s - 1)];
+                                 uint32_t shift, uint64_t* __restrict__ knot,
+                                 uint32_t* __restrict__ table) {
+  for (uint32_t k = threadIdx.x; k <= K; k += blockDim.x) knot[k] = sample[min(k * kKnotGap, s - 1)];
+  __syncthreads();
+  const uint64_t k0 = knot[0];
+  constexpr uint32_t T = 1u << kRadixBits;
+  for (uint32_t k = threadIdx.x; k <= K; k += blockDim.x) {
+    const int64_t p = (int64_t)((knot[k] - k0) >> shift);   // < T
+    const int64_t q = k ? (int64_t)((knot[k - 1] - k0) >> shift) : -1;
+    for (int64_t b = q + 1; b <= p; ++b) table[b] = k;
+    if (k == K)
+      for (uint32_t b = (uint32_t)p + 1; b <= T; ++b) table[b] = K + 1;
+  }
 }
 
 // Partition of every key and the partition sizes.
@@ -591,7 +610,8 @@ unsigned blocks_for(uint64_t work, unsigned block) {
 // partition starts, and the model that partitioned it.
 struct Sorted {
   uint64_t* knot = nullptr;   // the spline's knots (kSample / kKnotGap + 1 at most)
-  uint32_t K = 0;
+  uint32_t* table = nullptr;  // its radix table, after the knots
+  uint32_t K = 0, shift = 0;
   uint32_t s = 0, P = 1;
   uint64_t* keys = nullptr;
   uint32_t* pos = nullptr;
@@ -608,9 +628,19 @@ int sort_relation(const uint64_t* X, uint64_t n, Sorted& out, cudaStream_t s,
   lsj_sample_kernel<<<1, 1024, smem, s>>>(X, n, out.s, sample_buf);
   LJ_CUDA(cudaGetLastError());
   out.K = std::max<uint32_t>(1, (out.s - 1 + kKnotGap - 1) / kKnotGap);
-  lsj_knots_kernel<<<1, 256, 0, s>>>(sample_buf, out.s, out.K, out.knot);
+  // the radix table's shift needs the key range of the knots: the sample's
+  // smallest and largest keys, read back (one small copy, synchronising)
+  uint64_t ends[2];
+  LJ_CUDA(cudaMemcpyAsync(&ends[0], sample_buf, 8, cudaMemcpyDeviceToHost, s));
+  LJ_CUDA(cudaMemcpyAsync(&ends[1], sample_buf + out.s - 1, 8, cudaMemcpyDeviceToHost, s));
+  LJ_CUDA(cudaStreamSynchronize(s));
+  uint32_t bits = 0;
+  for (uint64_t r = ends[1] - ends[0]; r; r >>= 1) ++bits;
+  out.shift = bits > kRadixBits ? bits - kRadixBits : 0;
+  out.table = (uint32_t*)(out.knot + kSample / kKnotGap + 2);
+  lsj_knots_kernel<<<1, 256, 0, s>>>(sample_buf, out.s, out.K, out.shift, out.knot, out.table);
   LJ_CUDA(cudaGetLastError());
-  const Spline m{out.knot, out.K, out.s};
+  const Spline m{out.knot, out.table, out.K, out.s, out.shift};
   LJ_CUDA(cudaMemsetAsync(cnt, 0, (size_t)out.P * 8, s));
   LJ_CUDA(cudaMemsetAsync(cursor, 0, (size_t)out.P * 8, s));
   {
@@ -674,7 +704,8 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
   const size_t b_pid = round256(nm * 4);
   const size_t b_cnt = round256((size_t)Pmax * 8);
   const size_t b_big = round256(((size_t)Pmax + 1) * 4);
-  const size_t b_knot = round256(((size_t)kSample / kKnotGap + 2) * 8);
+  const size_t b_knot =
+      round256(((size_t)kSample / kKnotGap + 2) * 8 + (((size_t)1 << kRadixBits) + 1) * 4);
   const size_t b_rec = round256(nm * 16);
   const size_t total = b_sample + b_pid + 2 * b_cnt + b_big + 2 * b_knot + b_rec +
                        2 * round256(((size_t)Pmax + 1) * 8) +
@@ -743,7 +774,7 @@ extern "C" int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev
       rc = fail_cuda(ce, "lsj_join: item table");
       break;
     }
-    const Spline ms{S.knot, S.K, S.s};
+    const Spline ms{S.knot, S.table, S.K, S.s, S.shift};
     {
       KernelTimer kt("lsj_items_kernel", s);
       lsj_items_kernel<<<blocks_for(R.P, 256), 256, 0, s>>>(R.keys, R.off, R.P, d_item0, ms,
