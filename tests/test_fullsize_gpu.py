@@ -19,6 +19,8 @@ on every host core).
   gapped RMI, learned hash and RadixSpline hash at full size: their arrays
                     equal the oracle's, and their joins give the oracle's
                     ranges for every probe.
+  lsj_uniform_100m  the learned sort-merge join of two unsorted 100M-key
+                    relations: every pair equals the oracle's.
 """
 import numpy as np
 import pytest
@@ -295,3 +297,31 @@ def test_dup_seqh_50m_rs_hash_full(dup):
     pairs = torch.empty((total_o, 2), dtype=torch.int32, device="cuda")
     assert lj.join_expand(first, offsets, pairs) == total_o
     _pairs_equal_ranges_on_device(pairs, total_o, lo, off_o)
+
+
+def test_lsj_uniform_100m_full_parity():
+    """The learned sort-merge join (Section 4) of the bench's two unsorted
+    100M-key relations: every pair equals the oracle's (the sort-based join
+    of unsorted relations).  S is drawn from the unique R, so each probe j
+    has exactly one match: the pairs are compared probe by probe."""
+    lj = _lj()
+    w = datagen.lsj_uniform_100m(seed=0)
+    n, m = w.R.size, w.S.size
+    # the oracle's unsorted join (oracle.join_pairs_unsorted), with the
+    # sort-merge ranges taken on every host core: R sorted with its
+    # positions, each probe's range in it, mapped back to R's positions
+    perm = np.argsort(w.R, kind="stable")
+    lo, hi, total = oracle.join_ranges_mt(w.R[perm], w.S)
+    assert total == m == w.meta["expected_pairs"] and np.all(hi - lo == 1)
+    want_r = perm[lo.astype(np.int64)].astype(np.uint32)
+    Rd, Sd = _dev(w.R), _dev(w.S)
+    pairs = torch.full((m, 2), -1, dtype=torch.int32, device="cuda")
+    assert lj.lsj_join(Rd, Sd, pairs) == m
+    got = pairs.cpu().numpy().view(np.uint32)
+    s_idx = got[:, 1].astype(np.int64)
+    assert np.array_equal(np.bincount(s_idx, minlength=m), np.ones(m, np.int64))
+    r_of_s = np.empty(m, np.uint32)
+    r_of_s[s_idx] = got[:, 0]
+    assert np.array_equal(r_of_s, want_r)
+    del Rd, Sd, pairs
+    torch.cuda.empty_cache()
