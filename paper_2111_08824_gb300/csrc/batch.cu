@@ -158,6 +158,61 @@ __global__ void __launch_bounds__(BLOCK) batch_search_kernel(const JoinDesc* __r
   }
 }
 
+// Work item of 2*BLOCK probes (the shape's CHUNK = 1), one block per item and
+// no ticket: without the persistent loop the lookups fit in 32 registers, so
+// 2048 threads are resident per SM (the persistent kernel needs 78-94
+// registers).
+template <class Model, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK)
+    batch_item_kernel(const JoinDesc* __restrict__ desc, const uint64_t* __restrict__ item0,
+                      uint32_t k, uint64_t total_items, const uint64_t* __restrict__ comp0,
+                      unsigned long long* comp_counts, uint32_t* __restrict__ words) {
+  constexpr uint64_t kItem = 2ull * BLOCK;
+  static_assert(kCompactTile % kItem == 0, "a work item must lie in one compaction tile");
+  __shared__ unsigned long long s_count[BLOCK / 32];
+  const uint64_t item = blockIdx.x;
+  if (item >= total_items) return;
+  const uint32_t j = find_join(item0, k, item);
+  const JoinDesc d = desc[j];
+  const uint64_t first = (item - item0[j]) * kItem;   // first probe of the item in join j
+  ProbeParams<Model> P{};
+  P.R = d.R;
+  P.n = d.n;
+  P.r32 = d.r32 != 0;
+  P.leaves = (const typename Model::Leaf*)d.leaves;
+  P.model = model_of<Model>(d);
+  P.S = d.S;
+  P.m = d.m;
+  uint32_t* w = words + d.words_off;
+  const uint64_t j0 = first + 2 * threadIdx.x;
+  unsigned long long c = 0;
+  if (!__all_sync(0xffffffffu, j0 >= d.m)) {   // warp-uniform: lookups run as a warp
+    uint32_t r_idx[2], cnt[2];
+    bool valid[2];
+    if ((reinterpret_cast<uintptr_t>(d.S) & 15) == 0)
+      lookup_probes<Model, kUniqueCount, 1, true>(P, j0, 0, r_idx, cnt, valid);
+    else
+      lookup_probes<Model, kUniqueCount, 1, false>(P, j0, 0, r_idx, cnt, valid);
+    const uint32_t w0 = cnt[0] ? r_idx[0] : kNoMatch, w1 = cnt[1] ? r_idx[1] : kNoMatch;
+    if (valid[1]) {
+      *reinterpret_cast<uint2*>(w + j0) = make_uint2(w0, w1);   // words_off % 4 == 0
+    } else if (valid[0]) {
+      w[j0] = w0;
+    }
+    c = (unsigned long long)cnt[0] + cnt[1];
+  }
+#pragma unroll
+  for (int dd = 16; dd >= 1; dd >>= 1) c += __shfl_xor_sync(0xffffffffu, c, dd);
+  if ((threadIdx.x & 31) == 0) s_count[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+#pragma unroll
+    for (int q = 0; q < BLOCK / 32; ++q) tot += s_count[q];
+    if (tot) atomicAdd(comp_counts + comp0[j] + first / kCompactTile, tot);
+  }
+}
+
 template <bool VEC>
 __global__ void __launch_bounds__(kBlock) batch_compact_kernel(const JoinDesc* __restrict__ desc,
                                                                const uint64_t* __restrict__ comp0,
@@ -265,15 +320,18 @@ int enqueue_run(lj_batch* b, cudaStream_t s) {
   batch_search_kernel<MODEL, BLK, CH><<<b->search_grid, BLK, 0, s>>>(                          \
       desc, b->search_tile0, b->k, b->search_tiles, b->comp_tile0, b->comp_counts, b->words,   \
       ticket)
+#define LJ_BI(MODEL, BLK)                                                                      \
+  batch_item_kernel<MODEL, BLK><<<(unsigned)b->search_tiles, BLK, 0, s>>>(                     \
+      desc, b->search_tile0, b->k, b->search_tiles, b->comp_tile0, b->comp_counts, b->words)
 #define LJ_BS_SHAPE(MODEL)                                         \
   if (b->block == 256) {                                           \
     if (b->chunk == 8) LJ_BS(MODEL, 256, 8);                       \
     else if (b->chunk == 4) LJ_BS(MODEL, 256, 4);                  \
-    else LJ_BS(MODEL, 256, 1);                                     \
+    else LJ_BI(MODEL, 256);                                        \
   } else {                                                         \
     if (b->chunk == 8) LJ_BS(MODEL, 128, 8);                       \
     else if (b->chunk == 4) LJ_BS(MODEL, 128, 4);                  \
-    else LJ_BS(MODEL, 128, 1);                                     \
+    else LJ_BI(MODEL, 128);                                        \
   }
     if (b->precision == LJ_FP64) {
       LJ_BS_SHAPE(ModelF64)
@@ -281,6 +339,7 @@ int enqueue_run(lj_batch* b, cudaStream_t s) {
       LJ_BS_SHAPE(ModelF32)
     }
 #undef LJ_BS
+#undef LJ_BI
 #undef LJ_BS_SHAPE
   }
   LJ_CUDA(cudaGetLastError());
