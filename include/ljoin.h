@@ -407,13 +407,17 @@ int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
  * lsj_join -- learned sort-merge join (L-SJ, Section 4) of two UNSORTED
  * relations: J = { (i, j) : R[i] == S[j] }, i and j positions in R and S as
  * given (no index, no sorted input).
- *   model      per relation, a CDF model (the RMI of rmi_build) fitted over
- *              an evenly spaced sample of at most 16,384 keys, sorted on the
- *              device (Section 4.B);
+ *   model      per relation, a CDF model built from an evenly spaced sample
+ *              of at most 16,384 keys, sorted on the device: the
+ *              piecewise-linear function through every 32nd sample key,
+ *              looked up through a radix table (Section 4.B);
  *   partition  both relations range-partitioned with their model into
- *              partitions of about 2048 keys (histogram, scan, scatter);
+ *              partitions of about 2048 keys (histogram, scan, scatter of
+ *              one 16-byte (key, position) record per key);
  *   sort       each partition sorted on its own by (key, position) in
- *              shared memory (Section 4.C); the relations are then sorted;
+ *              shared memory: split into buckets by the top bits of the key
+ *              offsets, each entry placed by its rank in its bucket (Section
+ *              4.C); the relations are then sorted;
  *   join       R's partitions in chunks of up to 4096 keys, each merged with
  *              the partitions of S its first and last keys map to under S's
  *              model (Section 4.D).
@@ -421,7 +425,8 @@ int join_host(const lj_index* index, const uint64_t* S_host, uint64_t m,
  *   written_host          |J| (optional)
  * Pairs are grouped by R chunk (R's key order), then in S's (key, position)
  * order, then R's; the same for the same input.  Work memory: about 36
- * bytes per key of R and S (stream-ordered pool).  Synchronises.
+ * bytes per key of R and S, plus 16 bytes per key of the larger relation
+ * (stream-ordered pool).  Synchronises.
  * Errors: LJ_E_INVAL, LJ_E_NOMEM, LJ_E_CUDA, LJ_E_CAPACITY.
  */
 int lsj_join(const uint64_t* R_dev, uint64_t n, const uint64_t* S_dev, uint64_t m,
